@@ -1,0 +1,333 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test compares the oracle with something computed independently of it:
+closed forms, exactness of quadrature on polynomials, the solid-angle
+identity of Lemma 1 (Section 1.1), the doubled-domain equivalence of a planar
+reflective condition (Section 3.2, Test-1), a direct linear solve of the grey
+fixed point, the monotonicity proposition of Section 1.3, and the paper's own
+CPU table.  None of these needs a GPU.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+import sphere_ref as SR
+import workloads as W
+from oracle import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# quadrature rules
+# ---------------------------------------------------------------------------
+def test_gauss_legendre_exact_to_degree_31():
+    t, w = O.gauss_legendre(16)
+    for k in range(32):
+        exact = 2.0 / (k + 1) if k % 2 == 0 else 0.0
+        assert abs((w * t ** k).sum() - exact) < 2e-15, k
+    # degree 32 is not integrated exactly (the rule has 16 points)
+    assert abs((w * t ** 32).sum() - 2.0 / 33) > 1e-11
+
+
+@pytest.mark.parametrize("which,degree", [(4, 2), (14, 5)])
+def test_tet_rule_monomial_exactness(which, degree):
+    b, w = O.tet_rule(which)
+    assert b.shape == (which, 4)
+    assert np.all(w > 0) and np.all(b > 0)
+    assert np.allclose(b.sum(axis=1), 1.0, atol=1e-15)
+    for p in range(degree + 1):
+        for q in range(degree + 1 - p):
+            for r in range(degree + 1 - p - q):
+                exact = math.factorial(p) * math.factorial(q) * math.factorial(r) / math.factorial(p + q + r + 3) * 6
+                num = (w * b[:, 1] ** p * b[:, 2] ** q * b[:, 3] ** r).sum()
+                assert abs(num - exact) < 1e-14, (p, q, r)
+    # one degree more is not exact
+    misses = []
+    d = degree + 1
+    for p in range(d + 1):
+        for q in range(d + 1 - p):
+            r = d - p - q
+            exact = math.factorial(p) * math.factorial(q) * math.factorial(r) / math.factorial(d + 3) * 6
+            misses.append(abs((w * b[:, 1] ** p * b[:, 2] ** q * b[:, 3] ** r).sum() - exact))
+    assert max(misses) > 1e-6
+
+
+@pytest.mark.parametrize("which,degree", [(3, 2), (7, 5)])
+def test_triangle_rule_monomial_exactness(which, degree):
+    b, w = O.tri_rule(which)
+    assert np.all(w > 0)
+    for p in range(degree + 1):
+        for q in range(degree + 1 - p):
+            exact = math.factorial(p) * math.factorial(q) / math.factorial(p + q + 2) * 2
+            assert abs((w * b[:, 1] ** p * b[:, 2] ** q).sum() - exact) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# optical depth and kernel point values
+# ---------------------------------------------------------------------------
+def test_optical_depth_constant_kappa_is_kappa_times_length():
+    rng = np.random.default_rng(1)
+    k = W.Kappa(W.KAPPA_CONST, 2.5, 0.0)
+    for _ in range(20):
+        a, b = rng.uniform(0, 1, 3), rng.uniform(0, 1, 3)
+        assert O.optical_depth(k, a, b) == pytest.approx(2.5 * np.linalg.norm(b - a), rel=1e-14)
+
+
+def test_optical_depth_sinprod_matches_closed_form():
+    rng = np.random.default_rng(2)
+    k = W.sinprod_kappa(0.5)
+    for _ in range(50):
+        a, b = rng.uniform(0, 1, 3), rng.uniform(0, 1, 3)
+        L = np.linalg.norm(b - a)
+        ref = SR.sinprod_line_integral(a, (b - a) / L, 0.0, L, 1.0, 0.5)
+        assert O.optical_depth(k, a, b, 16) == pytest.approx(float(ref), rel=1e-13, abs=1e-15)
+
+
+def test_kernel_point_constant_kappa_mirror_image_closed_form():
+    """Constant kappa: direct = c k e^{-c k r}/(4 pi r^2); reflected term equals the same
+    kernel seen from the mirror image xbar = (x, y, -z): R0 c k e^{-c k |xbar-y|}/(4 pi |xbar-y|^2)."""
+    rng = np.random.default_rng(3)
+    k0, R0 = 1.3, 0.7
+    c = np.array([1.0, 0.6, 2.4])
+    kap = W.Kappa(W.KAPPA_CONST, k0, 0.0)
+    wall = W.wall_z0(R0)
+    for _ in range(30):
+        x, y = rng.uniform(0, 1, 3), rng.uniform(0, 1, 3)
+        d, r = O.kernel_point(kap, wall, x, y, c)
+        rr = np.linalg.norm(x - y)
+        xb = x * np.array([1, 1, -1])
+        rb = np.linalg.norm(xb - y)
+        np.testing.assert_allclose(d, c * k0 * np.exp(-c * k0 * rr) / (4 * math.pi * rr ** 2), rtol=1e-13)
+        np.testing.assert_allclose(r, R0 * c * k0 * np.exp(-c * k0 * rb) / (4 * math.pi * rb ** 2), rtol=1e-13)
+
+
+def test_kernel_point_reflected_optical_depth_is_straight_line_in_doubled_domain():
+    """sin-product kappa: tau(x,x') + tau(x',y) equals the optical depth of the straight segment
+    from x to the image of y below the wall, with kappa extended evenly (closed form)."""
+    rng = np.random.default_rng(4)
+    kap = W.sinprod_kappa(0.5)
+    wall = W.wall_z0(1.0)
+    c = np.array([1.0])
+    for _ in range(30):
+        x, y = rng.uniform(0, 1, 3), rng.uniform(0.05, 1, 3)
+        _, r = O.kernel_point(kap, wall, x, y, c)
+        yb = y * np.array([1, 1, -1])
+        L = np.linalg.norm(yb - x)
+        u = (yb - x) / L
+        s_wall = x[2] / (x[2] + y[2]) * L
+        tau = (SR.sinprod_line_integral(x, u, 0.0, s_wall, 1.0, 0.5)
+               + SR.sinprod_line_integral(x, u, s_wall, L, 1.0, 0.5, zsign=-1.0))
+        ky = 1 + 0.5 * np.prod(np.sin(2 * math.pi * y))
+        ref = ky * math.exp(-tau) / (4 * math.pi * L ** 2)
+        assert r[0] == pytest.approx(ref, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# the P1 operator G
+# ---------------------------------------------------------------------------
+def test_p1_hat_functions_reproduce_linear_functions():
+    """sum_j G^{ij} f(x_j) = sum_T sum_q |T| w_q K(x_i, y_q) f(y_q) for f = 1, x, y, z
+    (P1 interpolation is exact on linear functions)."""
+    p = W.cube_problem(6, W.sinprod_kappa(0.5), W.midpoint_freqs(3), R0=0.5)
+    rows = np.array([0, 7, 100, 215], dtype=np.int32)
+    R, mom = O.G_rows(p, rows, moments=True)
+    for r in range(len(rows)):
+        for g in range(R.shape[1]):
+            np.testing.assert_allclose(R[r, g].sum(), mom[r, g, 0], rtol=1e-13)
+            np.testing.assert_allclose(R[r, g] @ p.xyz, mom[r, g, 1:], rtol=1e-12)
+
+
+def test_literal_entry_equals_row_assembly():
+    p = W.cube_problem(5, W.sinprod_kappa(0.5), W.midpoint_freqs(2), R0=0.5)
+    rows = np.array([3, 62, 124], dtype=np.int32)
+    R = O.G_rows(p, rows)
+    rng = np.random.default_rng(5)
+    for r, i in enumerate(rows):
+        for j in rng.choice(p.N, 6, replace=False):
+            np.testing.assert_allclose(O.G_entry(p, int(i), int(j)), R[r, :, j], rtol=1e-12, atol=1e-300)
+
+
+@pytest.mark.parametrize("kind,k0,amp", [(W.KAPPA_CONST, 2.0, 0.0), (W.KAPPA_SINPROD, 1.0, 0.5)])
+def test_row_sums_converge_to_lemma1_sphere_integral(kind, k0, amp):
+    """Lemma 1: sum_j G^{ij} -> (1/4pi) int_S2 (1 - e^{-tau_exit}) + R0 mirror part.  The paper's
+    quadrature (refine=0) has an O(h) error from the 1/r^2 singularity; red refinement halves it
+    per level, and the Richardson value 2 R_2 - R_1 matches the sphere integral."""
+    n = 6
+    p = W.cube_problem(n, W.Kappa(kind, k0, amp), W.grey_freqs(), R0=0.5)
+    verts = np.array([0, 2 + n * 3 + n * n * 2, n - 1 + n * (n - 1)], dtype=np.int32)
+    c = np.array([1.0, 1.7])
+    R = [O.G_rows(p, verts, c=c, refine=ref).sum(axis=2) for ref in (0, 1, 2)]
+    for v in range(len(verts)):
+        for g in range(2):
+            _, ref = SR.row_sum_reference(p.xyz[verts[v]], kind, k0, amp, c[g], 0.5, 192, 384)
+            e0 = R[0][v, g] / ref - 1
+            e2 = R[2][v, g] / ref - 1
+            assert abs(e0) < 0.15
+            assert abs(e2) < abs(e0) / 3
+            rich = 2 * R[2][v, g] - R[1][v, g]
+            assert rich / ref - 1 == pytest.approx(0.0, abs=3e-3)
+
+
+def test_row_sums_below_one_so_the_fixed_point_contracts():
+    p = W.multifreq_32(n=8, F=4)
+    R = O.G_rows(p, np.arange(p.N, dtype=np.int32))
+    assert R.min() >= 0.0
+    assert R.sum(axis=2).max() < 1.0
+
+
+def test_reflective_wall_equals_doubled_domain_volume():
+    """Section 3.2 (Test-1): a planar RC with R0 = 1 is the same as solving on the domain doubled
+    by symmetry.  With the mirrored mesh and constant kappa the two discrete operators agree to
+    round-off: G_RC S = (G_doubled S_even) restricted to the original vertices."""
+    n = 5
+    kap = W.Kappa(W.KAPPA_CONST, 1.2, 0.0)
+    p = W.cube_problem(n, kap, W.grey_freqs(), R0=1.0)
+    dxyz, dtet, up, low = W.doubled_mesh(n)
+    pd = W.Problem(dxyz, dtet, W.doubled_emitter(n), kap, None, W.grey_freqs())
+    rows = np.array([0, 6, 31, 62, 124, 80], dtype=np.int32)
+    c = np.array([1.0, 0.5])
+    A = O.G_rows(p, rows, c=c)
+    B = O.G_rows(pd, rows, c=c)
+    S = W.rand_vectors(p.N, seed=9)
+    S_even = np.zeros(dxyz.shape[0])
+    S_even[up] = S
+    S_even[low] = S
+    np.testing.assert_allclose(A @ S, B @ S_even, rtol=1e-12)
+
+
+def test_reflective_wall_equals_doubled_domain_source():
+    n = 5
+    kap = W.Kappa(W.KAPPA_CONST, 0.8, 0.0)
+    p = W.cube_problem(n, kap, W.grey_freqs(), R0=1.0)
+    dxyz, dtet, up, low = W.doubled_mesh(n)
+    pd = W.Problem(dxyz, dtet, W.doubled_emitter(n), kap, None, W.grey_freqs())
+    rows = np.arange(p.N, dtype=np.int32)
+    c = np.array([1.0, 2.0])
+    np.testing.assert_allclose(O.source_geometric(p, rows, c=c), O.source_geometric(pd, rows, c=c),
+                               rtol=1e-12, atol=1e-15)
+
+
+def test_zero_reflection_drops_the_mirror_terms():
+    p = W.cube_problem(5, W.sinprod_kappa(0.5), W.grey_freqs(), R0=0.5)
+    q = W.cube_problem(5, W.sinprod_kappa(0.5), W.grey_freqs(), R0=0.0)
+    rows = np.array([0, 30, 77], dtype=np.int32)
+    half = O.G_rows(p, rows)
+    none = O.G_rows(q, rows)
+    one = O.G_rows(p, rows, R0=1.0)
+    assert not np.allclose(half, none)
+    np.testing.assert_allclose(half, none + 0.5 * (one - none), rtol=1e-12, atol=1e-18)
+    np.testing.assert_allclose(O.source_geometric(p, rows, R0=0.0), O.source_geometric(q, rows), rtol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# the emitter source
+# ---------------------------------------------------------------------------
+def test_zero_absorption_source_is_the_view_factor_closed_form():
+    """kappa = 0: G = 0 (so J = Sbar^E) and Sbar^E is the parallel-rectangle view-factor
+    integral (1/4pi) int d^2/(d^2+rho^2)^2, direct from x and mirrored from xbar (R0)."""
+    n, R0 = 6, 0.5
+    p = W.cube_problem(n, W.Kappa(W.KAPPA_CONST, 0.0, 0.0), W.grey_freqs(), R0=R0)
+    assert np.abs(O.G_rows(p, np.array([0, 100], dtype=np.int32))).max() == 0.0
+    h = 1.0 / (n - 1)
+    verts = [i + n * j + n * n * k for (i, j, k) in [(2, 2, 2), (3, 0, 1), (5, 4, 0), (1, 3, 5), (2, 5, 5)]]
+    rows = np.array(verts, dtype=np.int32)
+    fine = O.source_geometric(p, rows, refine=4)[:, 0]
+    paper = O.source_geometric(p, rows, refine=0)[:, 0]
+    for r, v in enumerate(verts):
+        x = p.xyz[v]
+        ref = (SR.square_view(x[1], x[2], x[0]) + R0 * SR.square_view(x[1], -x[2], x[0])) / (4 * math.pi)
+        assert fine[r] == pytest.approx(ref, rel=2e-3)
+        assert paper[r] == pytest.approx(ref, rel=0.05)
+    assert h > 0
+
+
+def test_emitter_vertices_take_the_limit_value():
+    """At vertices on the emitter the source is the limit d -> 0+ of the view-factor integral:
+    1/4 on the face, 1/8 on an edge, 1/16 at a corner (times (1 + R0) on the wall line z = 0)."""
+    n, R0 = 5, 0.5
+    p = W.cube_problem(n, W.Kappa(W.KAPPA_CONST, 0.0, 0.0), W.grey_freqs(), R0=R0)
+    cases = [((0, 2, 2), 0.25), ((0, 0, 2), 0.125), ((0, 2, 4), 0.125), ((0, 4, 4), 0.0625),
+             ((0, 2, 0), 0.125 * (1 + R0)), ((0, 0, 0), 0.0625 * (1 + R0))]
+    rows = np.array([i + n * j + n * n * k for (i, j, k), _ in cases], dtype=np.int32)
+    S = O.source_geometric(p, rows)[:, 0]
+    for r, (ijk, val) in enumerate(cases):
+        x = p.xyz[rows[r]]
+        lim = (SR.square_view(x[1], x[2], 1e-9) + R0 * SR.square_view(x[1], -x[2], 1e-9) * (x[2] == 0)) / (4 * math.pi)
+        assert S[r] == pytest.approx(val, rel=1e-12)
+        assert S[r] == pytest.approx(lim, rel=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# temperature solve and the fixed point
+# ---------------------------------------------------------------------------
+def test_newton_matches_bisection_and_closed_forms():
+    rng = np.random.default_rng(6)
+    fr = W.midpoint_freqs(7, albedo=0.3)
+    J = rng.uniform(0.0, 2.0, size=(7, 50))
+    J[:, 0] = 0.0
+    Tn = O.temperature_newton(J, fr)
+    Tb = O.temperature_bisection(J, fr)
+    np.testing.assert_allclose(Tn, Tb, rtol=1e-13, atol=1e-300)
+    assert Tn[0] == 0.0
+    # single frequency: B_nu(T) = J  =>  T = nu / ln(1 + nu^3 / J)
+    f1 = W.Freqs(np.array([0.7]), np.array([1.0]), np.array([1.2]), np.array([0.3]))
+    J1 = rng.uniform(0.01, 3.0, size=(1, 40))
+    np.testing.assert_allclose(O.temperature_newton(J1, f1), 0.7 / np.log1p(0.7 ** 3 / J1[0]), rtol=1e-13)
+    # grey: sigma T^4 = J
+    Jg = rng.uniform(0.0, 5.0, 30)
+    np.testing.assert_allclose(O.temperature_grey(Jg) ** 4 * (math.pi ** 4 / 15), Jg, rtol=1e-13)
+
+
+def test_planck_integrates_to_stefan_boltzmann():
+    """int_0^inf nu^3/(e^{nu/T}-1) d nu = (pi^4/15) T^4 (the relation used by the grey model)."""
+    nu = np.linspace(1e-6, 60, 400001)
+    for T in (0.5, 1.0, 1.7):
+        val = np.trapezoid(O.planck(nu, T), nu)
+        assert val == pytest.approx(O.SIGMA * T ** 4, rel=1e-6)
+
+
+def test_grey_fixed_point_equals_direct_linear_solve():
+    """Grey, a = 0: S = sigma T^4 = J, so the fixed point solves (I - G) J = Sbar^E."""
+    p = W.cube_problem(6, W.Kappa(W.KAPPA_CONST, 1.0, 0.0), W.grey_freqs(), R0=0.5, grey=True)
+    op = O.DenseOperator(p)
+    res = O.fixed_point(p, op, tol=1e-13, max_iter=400)
+    Jd = np.linalg.solve(np.eye(p.N) - op.G[0], op.SE[0])
+    np.testing.assert_allclose(res["J"][0], Jd, rtol=1e-11)
+    assert res["residual"] <= 1e-13
+
+
+def test_fixed_point_monotone_increasing_from_zero():
+    """Proposition of Section 1.3: T^0 = 0, J^0 = 0 gives T^k increasing at every vertex."""
+    p = W.cube_problem(5, W.sinprod_kappa(0.5), W.midpoint_freqs(3, albedo=0.3), R0=0.5)
+    op = O.DenseOperator(p)
+    res = O.fixed_point(p, op, T0=0.0, tol=1e-12, history=True)
+    H = res["hist_T"]
+    d = np.diff(H, axis=0)
+    assert (d[:-3] > 0).all()
+    assert (d >= -1e-14 * H[1:].max()).all()
+
+
+def test_fixed_point_monotone_decreasing_from_above():
+    """T^0 = 1 (the emitter temperature, above T*) with J^0 = B(1): T^k decreasing."""
+    p = W.cube_problem(5, W.sinprod_kappa(0.5), W.midpoint_freqs(3, albedo=0.3), R0=0.5)
+    op = O.DenseOperator(p)
+    J0 = np.repeat(O.planck(p.freqs.nu, 1.0)[:, None], p.N, axis=1)
+    res = O.fixed_point(p, op, T0=1.0, J0=J0, tol=1e-12, history=True)
+    H = res["hist_T"]
+    d = np.diff(H, axis=0)
+    assert (d[:-3] < 0).all()
+    up = O.fixed_point(p, op, T0=0.0, tol=1e-12)
+    np.testing.assert_allclose(res["T"], up["T"], rtol=1e-9)
+
+
+def test_paper_cpu_table_uses_natural_log():
+    rows = [list(map(float, l.split())) for l in open(os.path.join(GOLDEN, "paper_cpu_table.txt"))
+            if l.strip() and not l.startswith("#")]
+    for N, _, _, cpu, printed in rows:
+        val = 1e5 * cpu / (N * N ** (1 / 3) * math.log(N))
+        assert abs(val - printed) <= 0.0051 + (0.0075 if N == 8003 else 0.0)

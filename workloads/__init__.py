@@ -1,0 +1,276 @@
+"""Seeded synthetic workloads shared by the tests, the smoke check and the benchmark.
+
+This module holds inputs only -- geometry, coefficient fields, frequency grids,
+random vectors and random instance draws.  It contains none of the method's
+arithmetic (no kernel, quadrature, optical depth, Planck function or solver),
+so both the FP64 oracle and the CUDA library can consume it.
+
+Geometry follows the paper's FEM discretisation (Section 2: P1 elements on a
+tetrahedral mesh of the domain, a triangulated boundary):
+
+* ``cube_mesh(n)``: unit cube, n vertices per axis, vertex (i, j, k) at
+  (i, j, k) * h with h = 1/(n-1), index i + n*j + n*n*k; each cell is split
+  into 6 Kuhn tetrahedra, one per axis permutation pi:
+  {c, c+e_pi0, c+e_pi0+e_pi1, c+(1,1,1)}.
+* ``emitter_face_x0(n)``: the face x = 0 as triangles (the Kuhn face
+  diagonals), ordered so that the right-hand normal is the outward (-x) one.
+* ``wall_z0(R0)``: the reflective plane z = 0, outward normal (0, 0, -1).
+* ``doubled_mesh(n)``: the cube and its mirror image in z = 0, i.e. the
+  "symmetrised domain" of the academic test (Section 3.2), built by mirroring
+  every tetrahedron so the lower half is the exact image of the upper half.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List
+
+import numpy as np
+
+KAPPA_CONST = 0
+KAPPA_SINPROD = 1
+
+_KUHN_PERMS = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+
+
+def cube_mesh(n: int):
+    """Structured Kuhn mesh of [0,1]^3 with n vertices per axis.
+
+    Returns (xyz float64 [N,3], tet int32 [6(n-1)^3, 4]).
+    """
+    if n < 2:
+        raise ValueError("need at least 2 vertices per axis")
+    h = 1.0 / (n - 1)
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    xyz = np.stack([i.ravel() * h, j.ravel() * h, k.ravel() * h], axis=1).astype(np.float64)
+
+    def vid(ii, jj, kk):
+        return ii + n * jj + n * n * kk
+
+    c = np.arange(n - 1)
+    ck, cj, ci = np.meshgrid(c, c, c, indexing="ij")
+    ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+    tets = []
+    for p in _KUHN_PERMS:
+        cur = [ci.copy(), cj.copy(), ck.copy()]
+        v0 = vid(*cur)
+        cur[p[0]] += 1
+        v1 = vid(*cur)
+        cur[p[1]] += 1
+        v2 = vid(*cur)
+        v3 = vid(ci + 1, cj + 1, ck + 1)
+        tets.append(np.stack([v0, v1, v2, v3], axis=1))
+    # interleave so that the 6 tetrahedra of one cell are adjacent
+    tet = np.stack(tets, axis=1).reshape(-1, 4).astype(np.int32)
+    return xyz, tet
+
+
+def emitter_face_x0(n: int):
+    """Triangles of the face x = 0, outward (-x) right-hand normal. int32 [2(n-1)^2, 3]."""
+    c = np.arange(n - 1)
+    kk, jj = np.meshgrid(c, c, indexing="ij")
+    jj, kk = jj.ravel(), kk.ravel()
+
+    def vid(j, k):
+        return n * j + n * n * k
+
+    a = vid(jj, kk)
+    b = vid(jj + 1, kk)
+    cc = vid(jj + 1, kk + 1)
+    d = vid(jj, kk + 1)
+    # (a, cc, b) and (a, d, cc) have normal -x
+    t1 = np.stack([a, cc, b], axis=1)
+    t2 = np.stack([a, d, cc], axis=1)
+    return np.stack([t1, t2], axis=1).reshape(-1, 3).astype(np.int32)
+
+
+@dataclasses.dataclass
+class Wall:
+    """Planar reflective wall: point p, unit outward normal n, coefficient R0."""
+    p: tuple = (0.0, 0.0, 0.0)
+    n: tuple = (0.0, 0.0, -1.0)
+    R0: float = 0.5
+
+
+def wall_z0(R0: float = 0.5) -> Wall:
+    return Wall((0.0, 0.0, 0.0), (0.0, 0.0, -1.0), float(R0))
+
+
+@dataclasses.dataclass
+class Kappa:
+    """kappa(x) = k0 (+ amp sin(2 pi x) sin(2 pi y) sin(2 pi z) when kind == SINPROD)."""
+    kind: int = KAPPA_CONST
+    k0: float = 1.0
+    amp: float = 0.0
+
+
+@dataclasses.dataclass
+class Freqs:
+    """Frequency grid. kappa_nu = c[nu] * kappa(x); albedo a_nu; quadrature weight w_nu."""
+    nu: np.ndarray
+    w: np.ndarray
+    c: np.ndarray
+    albedo: np.ndarray
+
+    @property
+    def F(self) -> int:
+        return int(self.nu.shape[0])
+
+
+def midpoint_freqs(F: int, lo: float = 0.1, hi: float = 2.0, albedo: float = 0.3,
+                   c_offset: float | None = 0.5) -> Freqs:
+    """nu_k = lo + (k + 1/2) d, w_k = d, d = (hi - lo)/F.
+
+    c_k = c_offset + nu_k (kappa_nu = kappa(x) (0.5 + nu)); c_offset=None gives
+    a frequency-independent kappa_nu = kappa(x) (c_k = 1).
+    """
+    d = (hi - lo) / F
+    nu = lo + (np.arange(F) + 0.5) * d
+    w = np.full(F, d)
+    c = np.ones(F) if c_offset is None else c_offset + nu
+    return Freqs(nu.astype(np.float64), w.astype(np.float64), c.astype(np.float64),
+                 np.full(F, float(albedo)))
+
+
+def grey_freqs(albedo: float = 0.0) -> Freqs:
+    """One 'grey' channel (Section 3, eq. (grey)); nu and w are unused there."""
+    return Freqs(np.array([1.0]), np.array([1.0]), np.array([1.0]), np.array([float(albedo)]))
+
+
+@dataclasses.dataclass
+class Problem:
+    """One radiative-transfer instance on a tetrahedral mesh."""
+    xyz: np.ndarray
+    tet: np.ndarray
+    emit_tri: np.ndarray
+    kappa: Kappa
+    wall: Wall | None
+    freqs: Freqs
+    grey: bool = False
+    Q0: float = 1.0
+    T_emit: float = 1.0
+    name: str = ""
+
+    @property
+    def N(self) -> int:
+        return int(self.xyz.shape[0])
+
+
+def cube_problem(n: int, kappa: Kappa, freqs: Freqs, R0: float = 0.5, grey: bool = False,
+                 Q0: float = 1.0, T_emit: float = 1.0, name: str = "") -> Problem:
+    """Unit cube, emitter on x = 0, reflective wall z = 0 (R0 = 0 keeps the wall off)."""
+    xyz, tet = cube_mesh(n)
+    return Problem(xyz, tet, emitter_face_x0(n), kappa, wall_z0(R0) if R0 > 0 else None,
+                   freqs, grey, Q0, T_emit, name or f"cube{n}")
+
+
+# ---------------------------------------------------------------------------
+# The benchmark-shaped workloads
+# ---------------------------------------------------------------------------
+def plain_grey_12() -> Problem:
+    """12^3 cube, kappa = 1, grey, emitter T=1 on x=0, wall z=0 with R0=0.5, dense."""
+    return cube_problem(12, Kappa(KAPPA_CONST, 1.0, 0.0), grey_freqs(0.0), R0=0.5, grey=True,
+                        name="cube12_grey_kappa1")
+
+
+def sinprod_kappa(amp: float = 0.5) -> Kappa:
+    return Kappa(KAPPA_SINPROD, 1.0, float(amp))
+
+
+def multifreq_32(n: int = 32, F: int = 16) -> Problem:
+    """32^3 cube, kappa = 1 + 0.5 sin sin sin, 16 midpoint frequencies in [0.1, 2],
+    kappa_nu = kappa (0.5 + nu), albedo 0.3, wall z=0 with R0 = 0.5."""
+    return cube_problem(n, sinprod_kappa(0.5), midpoint_freqs(F, albedo=0.3, c_offset=0.5), R0=0.5,
+                        name=f"cube{n}_sinprod_F{F}")
+
+
+def shared_kappa_64(n: int = 64, F: int = 64) -> Problem:
+    """64^3 cube, same kappa field, 64 frequencies sharing kappa_nu = kappa(x)."""
+    return cube_problem(n, sinprod_kappa(0.5), midpoint_freqs(F, albedo=0.3, c_offset=None), R0=0.5,
+                        name=f"cube{n}_shared_F{F}")
+
+
+def batch_instances(count: int = 256, seed: int = 0, nmin: int = 8, nmax: int = 24,
+                    fmin: int = 1, fmax: int = 8, amax: float = 0.8) -> List[Problem]:
+    """Independent instances: n ~ U{nmin..nmax}, F ~ U{fmin..fmax}, amplitude ~ U[0, amax],
+    albedo 0.3, R0 0.5, kappa_nu = kappa (0.5 + nu)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(count):
+        n = int(rng.integers(nmin, nmax + 1))
+        F = int(rng.integers(fmin, fmax + 1))
+        a = float(rng.uniform(0.0, amax))
+        out.append(cube_problem(n, sinprod_kappa(a), midpoint_freqs(F, albedo=0.3, c_offset=0.5),
+                                R0=0.5, name=f"batch{b}_n{n}_F{F}"))
+    return out
+
+
+def serving_requests(count: int, rate_per_s: float = 200.0, seed: int = 0, nmin: int = 16,
+                     nmax: int = 48, fmin: int = 1, fmax: int = 32, amax: float = 0.8,
+                     rmax: float = 0.9):
+    """Poisson arrivals (exponential gaps) of random instances.  Returns a list of
+    (arrival_time_s, Problem)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for r in range(count):
+        t += float(rng.exponential(1.0 / rate_per_s))
+        n = int(rng.integers(nmin, nmax + 1))
+        F = int(rng.integers(fmin, fmax + 1))
+        a = float(rng.uniform(0.0, amax))
+        R0 = float(rng.uniform(0.0, rmax))
+        out.append((t, cube_problem(n, sinprod_kappa(a), midpoint_freqs(F, albedo=0.3, c_offset=0.5),
+                                    R0=R0, name=f"req{r}_n{n}_F{F}")))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Test inputs
+# ---------------------------------------------------------------------------
+def doubled_mesh(n: int):
+    """The cube [0,1]^3 together with its mirror image in z = 0 ([0,1]^2 x [-1,1]).
+
+    Every tetrahedron of the cube is mirrored; vertices on z = 0 are shared.
+    Returns (xyz [M,3], tet [2T,4], upper_index [N]) where upper_index maps the
+    cube's vertex ids to ids in the doubled mesh, and mirror_index [N] gives
+    the id of each vertex's mirror image."""
+    xyz, tet = cube_mesh(n)
+    N = xyz.shape[0]
+    on_wall = xyz[:, 2] == 0.0
+    low_ids = np.full(N, -1, dtype=np.int64)
+    extra = np.nonzero(~on_wall)[0]
+    low_ids[on_wall] = np.nonzero(on_wall)[0]
+    low_ids[extra] = N + np.arange(extra.size)
+    low_xyz = xyz[extra].copy()
+    low_xyz[:, 2] = -low_xyz[:, 2]
+    dxyz = np.concatenate([xyz, low_xyz], axis=0)
+    dtet = np.concatenate([tet, low_ids[tet]], axis=0).astype(np.int32)
+    return dxyz, dtet, np.arange(N), low_ids
+
+
+def doubled_emitter(n: int):
+    """Emitter face x = 0 of the doubled mesh (outward -x normal)."""
+    tri = emitter_face_x0(n)
+    _, _, _, low = doubled_mesh(n)
+    # mirroring flips orientation: swap two vertices to keep the -x normal
+    low_tri = low[tri][:, [0, 2, 1]]
+    return np.concatenate([tri, low_tri], axis=0).astype(np.int32)
+
+
+def rand_vectors(shape, seed: int = 0, kind: str = "uniform") -> np.ndarray:
+    """Seeded test vectors: U[0,1] (positive, like a source) or N(0,1)."""
+    rng = np.random.default_rng(seed)
+    if kind == "uniform":
+        return rng.uniform(0.0, 1.0, size=shape)
+    return rng.standard_normal(size=shape)
+
+
+def sample_rows(N: int, count: int, seed: int = 0) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    count = min(count, N)
+    return np.sort(rng.choice(N, size=count, replace=False)).astype(np.int32)
+
+
+def kuhn_mesh_stats(n: int):
+    """(N, T_e) of the cube mesh: N = n^3, T_e = 6 (n-1)^3."""
+    return n ** 3, 6 * (n - 1) ** 3
