@@ -1,0 +1,348 @@
+"""Benchmark: full solves of the 32^3, 16-frequency workload on GB300.
+
+One step = one pass of the whole hot path over one synthetic instance:
+host cluster/block tree, GPU ACA assembly of the 16 frequency operators, the
+emitter source, and the fixed point (source update, H-matvec, J update, FP64
+Newton temperature, FP64 residual) to tol 1e-6, all through the C ABI.
+
+Printed (rank 0, one JSON line): solves/s, the H-matvec bandwidth against the
+measured HBM peak (roofline of the per-iteration kernel pair, timed with CUDA
+events on the launching stream), the step-dominant assembly kernel's ALU
+roofline, the end-to-end rate with host buffers, the oracle CPU baseline,
+clock samples and the kernel launch count.
+
+--impl reference runs the FP64 CPU oracle (the reference arm of this build)
+on a bounded sample of the same workload and prints the same line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "solves/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+def workload(name):
+    if name == "cube32_F16":
+        return W.multifreq_32()
+    if name == "cube12_grey":
+        return W.plain_grey_12()
+    if name.startswith("cube") and "_F" in name:
+        n, F = name[4:].split("_F")
+        return W.multifreq_32(n=int(n), F=int(F))
+    raise ValueError(name)
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region (SM clock, reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2306_05789_gb300 as rt
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    from paper_2306_05789_gb300 import build as _b
+    if rank == 0 or world == 1:
+        _b.build()
+    if world > 1:
+        dist.barrier()
+    rt.lib()
+    prob = workload(args.workload)
+    far = {"f32": rt.RT_PREC_F32, "bf16": rt.RT_PREC_BF16, "f16": rt.RT_PREC_F16}[args.far_prec]
+    hp = rt.hparams(far_prec=far)
+    stream = torch.cuda.current_stream(dev)
+    F, N = prob.freqs.F, prob.N
+    J = torch.zeros(F, N, dtype=torch.float32, device=dev)
+    T = torch.zeros(N, dtype=torch.float64, device=dev)
+    Jh = torch.zeros(F, N, dtype=torch.float32).pin_memory()
+    Th = torch.zeros(N, dtype=torch.float64).pin_memory()
+
+    def step(e2e=False):
+        op = rt.rt_build_operator(prob, hp, stream)
+        st = op.solve_fixed_point(J, T, tol=args.tol, max_iter=300, check_every=4, stream=stream)
+        if e2e:
+            Jh.copy_(J, non_blocking=True)
+            Th.copy_(T, non_blocking=True)
+        return op, st
+
+    # warm-up
+    info = None
+    for _ in range(args.warmup):
+        op, st = step()
+        info = op.info()
+        op.free()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    if rank == 0:
+        clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = []
+    last = None
+    for k in range(args.steps):
+        op, st = step()
+        stats.append(st)
+        if k == args.steps - 1:
+            last = op
+        else:
+            op.free()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop() if rank == 0 else None
+    info = last.info()
+    # H-matvec: timed live on the last operator (the per-iteration kernel pair)
+    X = torch.rand(F, N, dtype=torch.float32, device=dev, generator=torch.Generator(device=dev).manual_seed(0))
+    Y = torch.zeros_like(X)
+    for _ in range(3):
+        last.apply(X, Y, stream)
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    n_apply = 20
+    a0.record(stream)
+    for _ in range(n_apply):
+        last.apply(X, Y, stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    t_apply = a0.elapsed_time(a1) / n_apply / 1e3
+    last.free()
+    # end to end: host buffers for the results, copies inside the timed region
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        op, _ = step(e2e=True)
+        torch.cuda.synchronize()
+        op.free()
+    t_e2e = (time.perf_counter() - t0) / e2e_steps
+
+    t_tensor = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
+    ms_max = float(t_tensor.item())
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    hbm, _, peak_kind = peaks()
+    iters = [s["iters"] for s in stats]
+    apply_gbs = info["apply_bytes"] / t_apply / 1e9
+    solves_per_s = world * args.steps / (ms_max / 1e3)
+    # launches inside one step: assembly (2 per ACA sweep x 4 + 6 misc), per-iteration kernels
+    per_iter = 6 + 2
+    launches = args.steps * (info["aca_steps"] * 8 + 8 + int(statistics.mean(iters)) * per_iter + 6)
+    out = {
+        "metric": METRIC,
+        "value": solves_per_s,
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.far_prec == "f32" else f"f32+{args.far_prec}",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "F": F, "kappa": "1+0.5 sin sin sin", "gauss_pts": 16,
+                   "aca_eps": 1e-4, "leaf": 64, "eta": 2.0, "R0": 0.5, "albedo": 0.3, "tol": args.tol,
+                   "far_prec": args.far_prec, "parallelism": f"replicas{world}",
+                   "l2": "operator larger than L2 (no flush needed)"},
+        "roofline": {"bound": "hbm", "kernel": "hmatvec (phase1+phase2, rt_apply)",
+                     "achieved": apply_gbs, "peak": hbm, "unit": "GB/s", "frac": apply_gbs / hbm,
+                     "traffic": None, "peak_kind": peak_kind,
+                     "algorithmic_bytes": info["apply_bytes"], "ms": t_apply * 1e3},
+        "hmatvec": {"gbs": apply_gbs, "ms": t_apply * 1e3, "bytes": info["apply_bytes"],
+                    "frac_of_" + peak_kind: apply_gbs / hbm},
+        "assembly": {"ms_aca": info["ms_aca"], "ms_near": info["ms_near"], "ms_source": info["ms_source"],
+                     "ms_tree": info["ms_tree"], "ms_pack": info["ms_pack"], "aca_steps": info["aca_steps"],
+                     "entries_evaluated": info["entries_evaluated"], "compression": info["compression"],
+                     "rank_max": info["rank_max"], "n_far": info["n_far"],
+                     "n_dense_fallback": info["n_dense_fallback"]},
+        "solve": {"iters_mean": statistics.mean(iters), "ms_solve_mean": statistics.mean(s["ms_total"] for s in stats)},
+        "e2e": {"value": world / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": int(prob.xyz.nbytes + prob.tet.nbytes
+                                                                                      + prob.emit_tri.nbytes),
+                "d2h_bytes_per_step": int(Jh.numel() * 4 + Th.numel() * 8)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(prob, np.mean(iters), args.cpu_rows)
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(prob, iters, rows):
+    """The FP64 oracle on a bounded sample: `rows` dense rows of all 16 operators and
+    their source values, plus a dense FP64 matvec rate; extrapolated to one full
+    dense-oracle solve of the same workload (assembly of every row + iters dense applies)."""
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count()
+    sel = W.sample_rows(prob.N, rows, seed=0)
+    t0 = time.perf_counter()
+    R = O.G_rows(prob, sel)
+    O.source_geometric(prob, sel)
+    t_rows = (time.perf_counter() - t0) / len(sel)
+    del R
+    # dense FP64 matvec throughput on the host cores
+    M = np.random.default_rng(0).random((4096, 4096))
+    x = np.random.default_rng(1).random((4096, 8))
+    t0 = time.perf_counter()
+    for _ in range(3):
+        M @ x
+    t_mv = (time.perf_counter() - t0) / 3
+    flops_rate = 2 * 4096 * 4096 * 8 / t_mv
+    F, N = prob.freqs.F, prob.N
+    t_solve = N * t_rows + iters * 2.0 * F * N * N / flops_rate
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(sel)} dense FP64 rows x {O.groups_of(prob.freqs)[0].shape[0]} groups + source, "
+                      f"extrapolated to N={N} rows and {iters:.0f} dense applies (measured {t_rows:.3f} s/row)"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle, each step a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    prob = workload(args.workload)
+    rows_per_step = args.cpu_rows
+    for _ in range(args.warmup):
+        O.G_rows(prob, W.sample_rows(prob.N, 1, seed=99))
+    t_rows = []
+    for k in range(args.steps):
+        sel = W.sample_rows(prob.N, rows_per_step, seed=k)
+        t0 = time.perf_counter()
+        O.G_rows(prob, sel)
+        O.source_geometric(prob, sel)
+        t_rows.append((time.perf_counter() - t0) / len(sel))
+    t_row = statistics.mean(t_rows)
+    F, N = prob.freqs.F, prob.N
+    M = np.random.default_rng(0).random((4096, 4096))
+    x = np.random.default_rng(1).random((4096, 8))
+    t0 = time.perf_counter()
+    for _ in range(3):
+        M @ x
+    rate = 2 * 4096 * 4096 * 8 / ((time.perf_counter() - t0) / 3)
+    iters = 30.0
+    t_solve = N * t_row + iters * 2.0 * F * N * N / rate
+    v = 1.0 / t_solve
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "F": F},
+        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"{rows_per_step} dense rows per step, extrapolated to N rows + {iters:.0f} "
+                                   "dense FP64 applies"},
+        "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="cube32_F16")
+    ap.add_argument("--far-prec", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--cpu-rows", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * rt.h -- C ABI of the GB300 (sm_103a) integral-form radiative-transfer
+ * library: assembly of the compressed operator Gbar (dense near-field blocks
+ * plus rank-r U V^T far-field blocks from partially pivoted ACA), its
+ * application to the multi-frequency iterate, and the monotone fixed point.
+ *
+ * Method: Pironneau & Tournier, "Reflective Conditions for Radiative
+ * Transfer in Integral Form with H-Matrices" (arXiv 2306.05789).
+ *   - kernel and reflected-path terms: Corollary and Example of Section 1.2
+ *   - P1 FEM matrix G_kappa^{ij} and source Sbar^E_i: Section 2
+ *   - H-matrix compression, admissibility max(R1,R2) < eta |x1-x2|, ACA with a
+ *     relative Frobenius tolerance: Section 2.1
+ *   - fixed-point algorithm, eq. (algo): Section 1.3; grey variant eq. (grey): Section 3
+ *
+ * Conventions for every entry point
+ *   - Return value: RT_OK (0) or a negative RT_E* code.  Nothing throws or
+ *     aborts across the ABI; rt_last_error() returns a thread-local message
+ *     describing the last failure on the calling thread.
+ *   - Host inputs (meshes, coefficient arrays) are owned by the caller and
+ *     copied during the call; they may be freed on return.
+ *   - Device pointers (X, Y, J, T, out) are owned by the caller, must hold the
+ *     stated number of elements, and are used in stream order on `stream`
+ *     (a cudaStream_t passed as void*, NULL = legacy default stream).
+ *   - Vectors over vertices and frequencies are laid out [F][N] (frequency
+ *     major, vertex index contiguous) in the caller's vertex order.
+ *   - The operator is owned by the library, resident on the device that was
+ *     current at build time, and released by rt_free().
+ *   - Results are deterministic for a given operator (no floating-point
+ *     atomics in the apply or solve paths).
+ */
+#ifndef RT_H
+#define RT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define RT_OK 0
+#define RT_EINVAL (-1)   /* invalid argument or malformed input */
+#define RT_ENOMEM (-2)   /* device or host allocation failed */
+#define RT_ECUDA (-3)    /* a CUDA call failed */
+#define RT_ENOCONV (-4)  /* fixed point did not reach tol within max_iter */
+#define RT_ETIMEOUT (-5) /* a bounded device-side wait gave up */
+
+/* kappa(x) descriptors (kappa_nu = c_nu * kappa(x)) */
+#define RT_KAPPA_CONST 0   /* kappa = k0 */
+#define RT_KAPPA_SINPROD 1 /* kappa = k0 + amp sin(2 pi x) sin(2 pi y) sin(2 pi z) */
+
+/* operator storage modes and precisions */
+#define RT_MODE_DENSE 0   /* every entry of G stored (FP64 or FP32) */
+#define RT_MODE_HMATRIX 1 /* H-matrix: dense leaves + ACA far blocks */
+#define RT_PREC_F64 0
+#define RT_PREC_F32 1
+#define RT_PREC_BF16 2
+#define RT_PREC_F16 3
+
+/* Tetrahedral P1 mesh of the domain (Section 2).  xyz: [n_vert][3] doubles;
+ * tet: [n_tet][4] vertex ids (0-based). */
+typedef struct {
+    int64_t n_vert;
+    const double* xyz;
+    int64_t n_tet;
+    const int32_t* tet;
+} rt_mesh;
+
+typedef struct {
+    int kind;  /* RT_KAPPA_* */
+    double k0; /* constant part */
+    double amp;
+} rt_kappa;
+
+/* Planar reflective wall (Section 2, planar reflective boundaries): a point
+ * p of the plane, the unit OUTWARD normal n, reflection coefficient R0.  The
+ * plane's intersection with the (convex) domain is taken as the reflecting
+ * face; at most one reflection per ray (Hypothesis 1, M = 1). */
+typedef struct {
+    double p[3];
+    double n[3];
+    double R0;
+} rt_wall;
+
+/* Frequency grid: F channels with quadrature weight w, absorption scale c
+ * (kappa_nu = c * kappa(x)) and albedo a.  Channels with equal c share one
+ * operator group (Remark of Section 2.1: one matrix per distinct kappa_nu). */
+typedef struct {
+    int F;
+    const double* nu;
+    const double* w;
+    const double* c;
+    const double* albedo;
+} rt_freqs;
+
+/* One problem instance.  Emitting boundary: n_emit triangles (vertex ids of
+ * the mesh, right-hand normal = outward normal) radiating
+ * Q_nu = Q0 [omega.n]_- B_nu(T_emit) (Example of Section 1), grey:
+ * Q0 sigma T_emit^4.  grey != 0 selects the grey formulation (eq. (grey),
+ * Section 3; F must be 1). */
+typedef struct {
+    rt_mesh mesh;
+    rt_kappa kappa;
+    int n_walls; /* 0 or 1 */
+    const rt_wall* walls;
+    int64_t n_emit;
+    const int32_t* emit_tri;
+    double Q0;
+    double T_emit;
+    int grey;
+    rt_freqs freqs;
+} rt_problem;
+
+/* Assembly parameters (Section 2 and 2.1). */
+typedef struct {
+    int mode;        /* RT_MODE_DENSE or RT_MODE_HMATRIX */
+    int prec;        /* dense: RT_PREC_F64 or RT_PREC_F32; H-matrix: RT_PREC_F32 (near field, vectors) */
+    int far_prec;    /* H-matrix far-field U/V storage: RT_PREC_F32, RT_PREC_BF16 or RT_PREC_F16 */
+    double aca_eps;  /* ACA relative Frobenius tolerance (e.g. 1e-4) */
+    int leaf;        /* cluster-tree leaf size (e.g. 64) */
+    double eta;      /* admissibility max(R1,R2) < eta |c1 - c2| (e.g. 2) */
+    int gauss_pts;   /* Gauss-Legendre points per line integral (1..32, e.g. 16) */
+    int rank_max;    /* ACA rank limit before a block is stored dense (0 = 512) */
+} rt_hparams;
+
+typedef struct rt_operator rt_operator;
+
+/* Operator statistics (filled by rt_operator_info). */
+typedef struct {
+    int64_t N, F, G;             /* vertices, frequencies, operator groups */
+    int mode, prec, far_prec;
+    int64_t n_leaves, n_near, n_far, n_dense_fallback;
+    int64_t stored_entries;      /* per group: sum m*n (dense) + sum r*(m+n) (far) */
+    double compression;          /* 1 - stored_entries / N^2 (per group) */
+    int64_t rank_min, rank_max, rank_sum;
+    int64_t aca_steps;           /* ACA sweeps until every block finished */
+    int64_t entries_evaluated;   /* kernel entries evaluated during assembly (all groups count once) */
+    int64_t apply_bytes;         /* algorithmic bytes moved by one rt_apply (all groups, see DESIGN) */
+    int64_t apply_flops;
+    int64_t device_bytes;        /* device memory held by the operator */
+    double ms_tree, ms_near, ms_aca, ms_pack, ms_source; /* assembly phase times */
+} rt_info;
+
+/* Fixed-point options (Section 1.3).  The iteration starts from T = T0 at
+ * every vertex and J = 0 (or J = J_dev on entry if use_J0 != 0). */
+typedef struct {
+    double tol;      /* stop when ||J^{k+1}-J^k||_2 / ||J^{k+1}||_2 <= tol */
+    int max_iter;
+    int check_every; /* iterations between host convergence checks (>= 1) */
+    double T0;
+    int use_J0;
+    int use_graph;   /* capture check_every iterations in a CUDA graph */
+} rt_solve_opts;
+
+typedef struct {
+    int iters;
+    int converged;
+    double residual;
+    double ms_total;
+} rt_solve_stats;
+
+/* Build the operator for one problem (Section 2, 2.1).  Host inputs are
+ * copied; assembly runs on `stream`; returns when the operator is complete.
+ * Errors: RT_EINVAL for malformed meshes/parameters, RT_ENOMEM, RT_ECUDA. */
+int rt_build_operator(const rt_problem* prob, const rt_hparams* hp, void* stream, rt_operator** out);
+
+/* Statistics of a built operator. */
+int rt_operator_info(const rt_operator* op, rt_info* info);
+
+/* Y = Gbar X per frequency (Y_nu = G_{g(nu)} X_nu), X and Y device arrays
+ * [F][N] in the caller's vertex order; element type double for a dense FP64
+ * operator, float otherwise.  X and Y must not overlap. */
+int rt_apply(rt_operator* op, const void* X, void* Y, void* stream);
+
+/* Sbar^E_nu (Proposition 2 / Example of Section 1.2, discretised as in
+ * Section 2) into out [F][N] (vector element type as in rt_apply). */
+int rt_source(rt_operator* op, void* out, void* stream);
+
+/* Evaluate `count` individual entries G_g^{ij} with the library's entry
+ * evaluator (same arithmetic as assembly): rows/cols are device int32 arrays
+ * of vertex ids (caller order), out is a device double array [count]. */
+int rt_eval_entries(rt_operator* op, int group, int64_t count, const int32_t* rows, const int32_t* cols,
+                    double* out, void* stream);
+
+/* Fixed point of Section 1.3 (eq. (algo)) on the device: S = a J + (1-a)
+ * B_nu(T), J <- Sbar^E + Gbar S, T <- Planck balance per vertex (FP64
+ * Newton, or (J/sigma)^(1/4) for grey).  J_dev [F][N] (vector element type),
+ * T_dev [N] doubles; both receive the final iterate.  Returns RT_ENOCONV
+ * (with J, T and stats filled) if tol is not reached within max_iter. */
+int rt_solve_fixed_point(rt_operator* op, const rt_solve_opts* opts, void* J_dev, double* T_dev,
+                         rt_solve_stats* stats, void* stream);
+
+/* Release the operator and its device memory. */
+void rt_free(rt_operator* op);
+
+/* Thread-local text of the last error on the calling thread ("" if none). */
+const char* rt_last_error(void);
+
+/* ---- host-only planning (no GPU needed) --------------------------------
+ * Cluster tree by recursive bisection at the median along the longest box
+ * axis down to `leaf` points, and the block tree with the admissibility rule
+ * max(R_t, R_s) < eta |c_t - c_s| of Section 2.1 (R = max distance from the
+ * centroid).  perm (may be NULL): [n] tree order -> vertex id.  blocks (may
+ * be NULL): [cap][5] rows (row0, m, col0, n, kind: 0 dense leaf, 1
+ * admissible) in tree order.  counts: [0] = leaves, [1] = dense blocks,
+ * [2] = admissible blocks. */
+int rt_plan(const double* xyz, int64_t n, int leaf, double eta, int32_t* perm, int32_t* blocks, int64_t cap,
+            int64_t* counts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_H */

@@ -1,0 +1,255 @@
+"""Python binding of the GB300 radiative-transfer library (C ABI in include/rt.h).
+
+Argument marshalling only: every step of assembly, apply and solve runs in the
+CUDA library ``librt.so``.  Device arrays are passed as torch tensors (their
+data pointers) together with the CUDA stream to run on.  Every call goes
+through :func:`lib`, which raises ImportError when the library has not been
+built -- there is no CPU fallback.
+
+Names follow the C ABI: :func:`rt_build_operator`, :meth:`Operator.apply`
+(``rt_apply``), :meth:`Operator.source` (``rt_source``),
+:meth:`Operator.eval_entries` (``rt_eval_entries``),
+:meth:`Operator.solve_fixed_point` (``rt_solve_fixed_point``),
+:meth:`Operator.info` (``rt_operator_info``), :func:`rt_plan`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librt.so")
+
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOCONV, RT_ETIMEOUT = 0, -1, -2, -3, -4, -5
+RT_KAPPA_CONST, RT_KAPPA_SINPROD = 0, 1
+RT_MODE_DENSE, RT_MODE_HMATRIX = 0, 1
+RT_PREC_F64, RT_PREC_F32, RT_PREC_BF16, RT_PREC_F16 = 0, 1, 2, 3
+
+_c_i64 = ctypes.c_int64
+_c_int = ctypes.c_int
+_c_dbl = ctypes.c_double
+_P = ctypes.c_void_p
+
+
+class RtMesh(ctypes.Structure):
+    _fields_ = [("n_vert", _c_i64), ("xyz", _P), ("n_tet", _c_i64), ("tet", _P)]
+
+
+class RtKappa(ctypes.Structure):
+    _fields_ = [("kind", _c_int), ("k0", _c_dbl), ("amp", _c_dbl)]
+
+
+class RtWall(ctypes.Structure):
+    _fields_ = [("p", _c_dbl * 3), ("n", _c_dbl * 3), ("R0", _c_dbl)]
+
+
+class RtFreqs(ctypes.Structure):
+    _fields_ = [("F", _c_int), ("nu", _P), ("w", _P), ("c", _P), ("albedo", _P)]
+
+
+class RtProblem(ctypes.Structure):
+    _fields_ = [("mesh", RtMesh), ("kappa", RtKappa), ("n_walls", _c_int), ("walls", _P), ("n_emit", _c_i64),
+                ("emit_tri", _P), ("Q0", _c_dbl), ("T_emit", _c_dbl), ("grey", _c_int), ("freqs", RtFreqs)]
+
+
+class RtHparams(ctypes.Structure):
+    _fields_ = [("mode", _c_int), ("prec", _c_int), ("far_prec", _c_int), ("aca_eps", _c_dbl), ("leaf", _c_int),
+                ("eta", _c_dbl), ("gauss_pts", _c_int), ("rank_max", _c_int)]
+
+
+class RtInfo(ctypes.Structure):
+    _fields_ = [("N", _c_i64), ("F", _c_i64), ("G", _c_i64), ("mode", _c_int), ("prec", _c_int), ("far_prec", _c_int),
+                ("n_leaves", _c_i64), ("n_near", _c_i64), ("n_far", _c_i64), ("n_dense_fallback", _c_i64),
+                ("stored_entries", _c_i64), ("compression", _c_dbl), ("rank_min", _c_i64), ("rank_max", _c_i64),
+                ("rank_sum", _c_i64), ("aca_steps", _c_i64), ("entries_evaluated", _c_i64),
+                ("apply_bytes", _c_i64), ("apply_flops", _c_i64), ("device_bytes", _c_i64),
+                ("ms_tree", _c_dbl), ("ms_near", _c_dbl), ("ms_aca", _c_dbl), ("ms_pack", _c_dbl),
+                ("ms_source", _c_dbl)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class RtSolveOpts(ctypes.Structure):
+    _fields_ = [("tol", _c_dbl), ("max_iter", _c_int), ("check_every", _c_int), ("T0", _c_dbl), ("use_J0", _c_int),
+                ("use_graph", _c_int)]
+
+
+class RtSolveStats(ctypes.Structure):
+    _fields_ = [("iters", _c_int), ("converged", _c_int), ("residual", _c_dbl), ("ms_total", _c_dbl)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# every symbol declared in include/rt.h
+EXPORTS = ("rt_build_operator", "rt_operator_info", "rt_apply", "rt_source", "rt_eval_entries",
+           "rt_solve_fixed_point", "rt_free", "rt_last_error", "rt_plan")
+
+_lib = None
+
+
+def lib():
+    """Load librt.so (built by ``paper_2306_05789_gb300.build``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run `python -m paper_2306_05789_gb300.build` "
+                          "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    L.rt_build_operator.argtypes = [ctypes.POINTER(RtProblem), ctypes.POINTER(RtHparams), _P, ctypes.POINTER(_P)]
+    L.rt_operator_info.argtypes = [_P, ctypes.POINTER(RtInfo)]
+    L.rt_apply.argtypes = [_P, _P, _P, _P]
+    L.rt_source.argtypes = [_P, _P, _P]
+    L.rt_eval_entries.argtypes = [_P, _c_int, _c_i64, _P, _P, _P, _P]
+    L.rt_solve_fixed_point.argtypes = [_P, ctypes.POINTER(RtSolveOpts), _P, _P, ctypes.POINTER(RtSolveStats), _P]
+    L.rt_free.argtypes = [_P]
+    L.rt_free.restype = None
+    L.rt_last_error.restype = ctypes.c_char_p
+    L.rt_plan.argtypes = [_P, _c_i64, _c_int, _c_dbl, _P, _P, _c_i64, _P]
+    _lib = L
+    return L
+
+
+class RtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"rt error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc):
+    if rc != RT_OK:
+        raise RtError(rc, lib().rt_last_error().decode(errors="replace"))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_P)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return _P(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return _P(stream)
+    return _P(stream.cuda_stream)
+
+
+def hparams(mode=RT_MODE_HMATRIX, prec=None, far_prec=RT_PREC_F32, aca_eps=1e-4, leaf=64, eta=2.0, gauss_pts=16,
+            rank_max=0) -> RtHparams:
+    if prec is None:
+        prec = RT_PREC_F32
+    return RtHparams(mode, prec, far_prec, aca_eps, leaf, eta, gauss_pts, rank_max)
+
+
+class _ProblemArgs:
+    """Holds the C structs and the numpy arrays they point into."""
+
+    def __init__(self, prob):
+        self.xyz = np.ascontiguousarray(prob.xyz, dtype=np.float64)
+        self.tet = np.ascontiguousarray(prob.tet, dtype=np.int32)
+        self.tri = np.ascontiguousarray(prob.emit_tri, dtype=np.int32).reshape(-1, 3)
+        fr = prob.freqs
+        self.nu = np.ascontiguousarray(fr.nu, dtype=np.float64)
+        self.w = np.ascontiguousarray(fr.w, dtype=np.float64)
+        self.c = np.ascontiguousarray(fr.c, dtype=np.float64)
+        self.a = np.ascontiguousarray(fr.albedo, dtype=np.float64)
+        self.walls = None
+        n_walls = 0
+        if prob.wall is not None:
+            self.walls = (RtWall * 1)()
+            for d in range(3):
+                self.walls[0].p[d] = float(prob.wall.p[d])
+                self.walls[0].n[d] = float(prob.wall.n[d])
+            self.walls[0].R0 = float(prob.wall.R0)
+            n_walls = 1
+        self.s = RtProblem()
+        self.s.mesh = RtMesh(self.xyz.shape[0], _ptr(self.xyz), self.tet.shape[0], _ptr(self.tet))
+        self.s.kappa = RtKappa(int(prob.kappa.kind), float(prob.kappa.k0), float(prob.kappa.amp))
+        self.s.n_walls = n_walls
+        self.s.walls = ctypes.cast(self.walls, _P) if self.walls is not None else None
+        self.s.n_emit = self.tri.shape[0]
+        self.s.emit_tri = _ptr(self.tri)
+        self.s.Q0 = float(prob.Q0)
+        self.s.T_emit = float(prob.T_emit)
+        self.s.grey = 1 if prob.grey else 0
+        self.s.freqs = RtFreqs(self.nu.shape[0], _ptr(self.nu), _ptr(self.w), _ptr(self.c), _ptr(self.a))
+
+
+class Operator:
+    """A built operator (owned by the library; released by :meth:`free`)."""
+
+    def __init__(self, handle, N, F, vec64):
+        self.h = handle
+        self.N = N
+        self.F = F
+        self.vec64 = vec64
+
+    def info(self) -> dict:
+        i = RtInfo()
+        _check(lib().rt_operator_info(self.h, ctypes.byref(i)))
+        return i.as_dict()
+
+    def apply(self, X, Y, stream=None):
+        """rt_apply: Y = Gbar X, torch tensors [F, N] on the device."""
+        _check(lib().rt_apply(self.h, _P(X.data_ptr()), _P(Y.data_ptr()), _stream_ptr(stream)))
+
+    def source(self, out, stream=None):
+        """rt_source: Sbar^E into out [F, N]."""
+        _check(lib().rt_source(self.h, _P(out.data_ptr()), _stream_ptr(stream)))
+
+    def eval_entries(self, group, rows, cols, out, stream=None):
+        """rt_eval_entries: out[k] = G_group[rows[k], cols[k]] (device int32 rows/cols, float64 out)."""
+        _check(lib().rt_eval_entries(self.h, int(group), int(rows.numel()), _P(rows.data_ptr()),
+                                     _P(cols.data_ptr()), _P(out.data_ptr()), _stream_ptr(stream)))
+
+    def solve_fixed_point(self, J, T, tol=1e-10, max_iter=500, check_every=1, T0=0.0, use_J0=False,
+                          use_graph=True, stream=None, raise_on_noconv=True) -> dict:
+        """rt_solve_fixed_point: J [F, N] and T [N] (float64) receive the final iterate."""
+        o = RtSolveOpts(float(tol), int(max_iter), int(check_every), float(T0), 1 if use_J0 else 0,
+                        1 if use_graph else 0)
+        st = RtSolveStats()
+        rc = lib().rt_solve_fixed_point(self.h, ctypes.byref(o), _P(J.data_ptr()), _P(T.data_ptr()),
+                                        ctypes.byref(st), _stream_ptr(stream))
+        d = st.as_dict()
+        d["rc"] = rc
+        if rc != RT_OK and (raise_on_noconv or rc != RT_ENOCONV):
+            _check(rc)
+        return d
+
+    def free(self):
+        if self.h:
+            lib().rt_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def rt_build_operator(prob, hp: RtHparams, stream=None) -> Operator:
+    """Build the operator of one problem (any object with the attributes of
+    ``workloads.Problem``: xyz, tet, emit_tri, kappa, wall, freqs, grey, Q0, T_emit)."""
+    args = _ProblemArgs(prob)
+    out = _P()
+    _check(lib().rt_build_operator(ctypes.byref(args.s), ctypes.byref(hp), _stream_ptr(stream), ctypes.byref(out)))
+    vec64 = hp.mode == RT_MODE_DENSE and hp.prec == RT_PREC_F64
+    return Operator(out, args.xyz.shape[0], args.nu.shape[0], vec64)
+
+
+def rt_plan(xyz, leaf=64, eta=2.0):
+    """Host-only cluster/block tree: (perm [N], blocks [nb,5], counts (leaves, dense, admissible))."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    n = xyz.shape[0]
+    counts = np.zeros(3, dtype=np.int64)
+    _check(lib().rt_plan(_ptr(xyz), n, int(leaf), float(eta), None, None, 0, _ptr(counts)))
+    perm = np.zeros(n, dtype=np.int32)
+    nb = int(counts[1] + counts[2])
+    blocks = np.zeros((max(nb, 1), 5), dtype=np.int32)
+    _check(lib().rt_plan(_ptr(xyz), n, int(leaf), float(eta), _ptr(perm), _ptr(blocks), nb, _ptr(counts)))
+    return perm, blocks[:nb], tuple(int(c) for c in counts)

@@ -1,0 +1,1133 @@
+// rt_assemble.cu -- assembly of the operator on the GPU (Section 2, 2.1):
+//   * constants: Gauss-Legendre nodes, tetrahedron and triangle rules
+//   * entry kernels (warp per entry) for dense blocks, ACA rows/columns and
+//     arbitrary entry lists
+//   * the emitter source Sbar^E
+//   * batched partially pivoted ACA with pivots shared by all kappa groups
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "rt_entry.cuh"
+#include "rt_internal.h"
+
+namespace rt {
+
+
+// ---------------------------------------------------------------------------
+// host: quadrature tables
+// ---------------------------------------------------------------------------
+// Gauss-Legendre nodes: Newton iteration on P_n from the asymptotic guess
+// cos(pi (4k + 3) / (4n + 2)); P_n and P_n' from the three-term recurrence.
+void gauss_legendre_nodes(int n, std::vector<double>& t, std::vector<double>& w)
+{
+    t.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int k = 0; k < n; ++k) {
+        double x = std::cos(kPi * (4.0 * k + 3.0) / (4.0 * n + 2.0));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double pm = 1.0, p = x;
+            for (int l = 1; l < n; ++l) {
+                double pn = ((2.0 * l + 1.0) * x * p - l * pm) / (l + 1.0);
+                pm = p;
+                p = pn;
+            }
+            dp = n * (pm - x * p) / (1.0 - x * x);
+            double step = p / dp;
+            x -= step;
+            if (std::fabs(step) <= 1e-16 * std::fabs(x) + 1e-300) break;
+        }
+        {
+            double pm = 1.0, p = x;
+            for (int l = 1; l < n; ++l) {
+                double pn = ((2.0 * l + 1.0) * x * p - l * pm) / (l + 1.0);
+                pm = p;
+                p = pn;
+            }
+            dp = n * (pm - x * p) / (1.0 - x * x);
+        }
+        t[k] = x;
+        w[k] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+}
+
+// Tetrahedron rules in barycentric coordinates: the symmetric 4-point rule of
+// degree 2 and the positive 14-point rule of degree 5 (two S31 orbits, one S22
+// orbit); triangle rules: 3-point degree 2 and Radon's 7-point degree 5.
+static void tet_rules(double* b, double* w)
+{
+    const double al = (5.0 + 3.0 * std::sqrt(5.0)) / 20.0, be = (5.0 - std::sqrt(5.0)) / 20.0;
+    int r = 0;
+    for (int k = 0; k < 4; ++k, ++r) {
+        for (int d = 0; d < 4; ++d) b[4 * r + d] = d == k ? al : be;
+        w[r] = 0.25;
+    }
+    const double s31[2][2] = {{0.0927352503108912, 0.07349304311636196}, {0.3108859192633006, 0.1126879257180159}};
+    for (int o = 0; o < 2; ++o)
+        for (int k = 0; k < 4; ++k, ++r) {
+            for (int d = 0; d < 4; ++d) b[4 * r + d] = d == k ? 1.0 - 3.0 * s31[o][0] : s31[o][0];
+            w[r] = s31[o][1];
+        }
+    const double s22 = 0.4544962958743504, ws22 = 0.04254602077708147;
+    for (int a = 0; a < 4; ++a)
+        for (int c = a + 1; c < 4; ++c, ++r) {
+            for (int d = 0; d < 4; ++d) b[4 * r + d] = (d == a || d == c) ? s22 : 0.5 - s22;
+            w[r] = ws22;
+        }
+}
+
+static void tri_rules(double* b, double* w)
+{
+    int r = 0;
+    for (int k = 0; k < 3; ++k, ++r) {
+        for (int d = 0; d < 3; ++d) b[3 * r + d] = d == k ? 2.0 / 3.0 : 1.0 / 6.0;
+        w[r] = 1.0 / 3.0;
+    }
+    b[3 * r] = b[3 * r + 1] = b[3 * r + 2] = 1.0 / 3.0;
+    w[r++] = 0.225;
+    const double q = std::sqrt(15.0);
+    const double orb[2][2] = {{(6.0 - q) / 21.0, (155.0 - q) / 1200.0}, {(6.0 + q) / 21.0, (155.0 + q) / 1200.0}};
+    for (int o = 0; o < 2; ++o)
+        for (int k = 0; k < 3; ++k, ++r) {
+            for (int d = 0; d < 3; ++d) b[3 * r + d] = d == k ? 1.0 - 2.0 * orb[o][0] : orb[o][0];
+            w[r] = orb[o][1];
+        }
+}
+
+int assemble_setup_constants(Operator& op, std::string& err)
+{
+    std::vector<double> t, w;
+    gauss_legendre_nodes(op.ngauss, t, w);
+    for (int g = 0; g < kMaxGauss; ++g) {
+        const double u = g < op.ngauss ? 0.5 * (1.0 + t[g]) : 0.0, hw = g < op.ngauss ? 0.5 * w[g] : 0.0;
+        op.kp.gu64[g] = u;
+        op.kp.gw64[g] = hw;
+        op.kp.gu32[g] = (float)u;
+        op.kp.gw32[g] = (float)hw;
+    }
+    // fixed rule tables: uploaded once per device
+    static bool done[64] = {false};
+    int dev = 0;
+    RT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 64 && done[dev]) return RT_OK;
+    double tb[18 * 4], tw[18];
+    float tbf[18 * 4], twf[18];
+    tet_rules(tb, tw);
+    for (int k = 0; k < 72; ++k) tbf[k] = (float)tb[k];
+    for (int k = 0; k < 18; ++k) twf[k] = (float)tw[k];
+    double rb[30], rw[10];
+    tri_rules(rb, rw);
+    RT_CUDA_TRY(cudaMemcpyToSymbol(c_tet_b, tb, sizeof(tb)));
+    RT_CUDA_TRY(cudaMemcpyToSymbol(c_tet_w, tw, sizeof(tw)));
+    RT_CUDA_TRY(cudaMemcpyToSymbol(c_tet_bf, tbf, sizeof(tbf)));
+    RT_CUDA_TRY(cudaMemcpyToSymbol(c_tet_wf, twf, sizeof(twf)));
+    RT_CUDA_TRY(cudaMemcpyToSymbol(c_tri_b, rb, sizeof(rb)));
+    RT_CUDA_TRY(cudaMemcpyToSymbol(c_tri_w, rw, sizeof(rw)));
+    RT_CUDA_TRY(cudaDeviceSynchronize());
+    if (dev < 64) done[dev] = true;
+    return RT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// entry kernels
+// ---------------------------------------------------------------------------
+constexpr int kWarpsPerCta = 8;
+
+__device__ __forceinline__ int find_span(const EntrySpan* sp, int ns, int64_t e)
+{
+    int lo = 0, hi = ns - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (sp[mid].first <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <class R, class OUT, int MG>
+__global__ void __launch_bounds__(32 * kWarpsPerCta) entries_span_kernel(KernelParams P, const EntrySpan* spans,
+                                                                         int nspans, int64_t total, OUT* out)
+{
+    __shared__ int s_tet[kWarpsPerCta][32], s_cnt[kWarpsPerCta][32], s_pre[kWarpsPerCta][33];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * kWarpsPerCta;
+    for (int64_t e = (int64_t)blockIdx.x * kWarpsPerCta + wib; e < total; e += nw) {
+        const int si = find_span(spans, nspans, e);
+        const EntrySpan sp = spans[si];
+        const int64_t loc = e - sp.first;
+        const int ii = (int)(loc / sp.nj), jj = (int)(loc % sp.nj);
+        R acc[MG];
+        entry_warp<R, MG>(P, sp.i0 + ii, sp.j0 + jj, acc, s_tet[wib], s_cnt[wib], s_pre[wib]);
+#pragma unroll
+        for (int g = 0; g < MG; ++g)
+            if (g < P.G && lane == (g & 31)) out[sp.base + g * sp.gs + ii * sp.is + jj * sp.js] = (OUT)acc[g];
+    }
+}
+
+// ACA rows (mode 0) / columns (mode 1) of the active far blocks.
+struct AcaActive {
+    int b;          // far block id
+    int row0, m, col0, n;
+    int64_t rbuf;   // offset of this block's [G][n] row buffer
+    int64_t cbuf;   // offset of this block's [G][m] column buffer
+    int64_t first_row, first_col;   // prefix of n (rows) and m (cols) over the active list
+    int64_t uoff, voff;             // pool offsets of this step's u [G][m] and v [G][n]
+    int skip;       // set by the pivot kernel: zero row, no rank this step
+};
+
+__device__ __forceinline__ int find_active(const AcaActive* a, int na, int64_t e, int mode)
+{
+    int lo = 0, hi = na - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        int64_t f = mode == 0 ? a[mid].first_row : a[mid].first_col;
+        if (f <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int MG>
+__global__ void __launch_bounds__(32 * kWarpsPerCta) aca_entries_kernel(KernelParams P, const AcaActive* act,
+                                                                        int na, int64_t total, int mode,
+                                                                        const int* istar, const int* jstar,
+                                                                        float* buf)
+{
+    __shared__ int s_tet[kWarpsPerCta][32], s_cnt[kWarpsPerCta][32], s_pre[kWarpsPerCta][33];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * kWarpsPerCta;
+    for (int64_t e = (int64_t)blockIdx.x * kWarpsPerCta + wib; e < total; e += nw) {
+        const int ai = find_active(act, na, e, mode);
+        const AcaActive a = act[ai];
+        if (mode == 1 && a.skip) continue;
+        int i, j, len;
+        int64_t pos;
+        if (mode == 0) {
+            pos = e - a.first_row;
+            i = a.row0 + istar[a.b];
+            j = a.col0 + (int)pos;
+            len = a.n;
+        } else {
+            pos = e - a.first_col;
+            i = a.row0 + (int)pos;
+            j = a.col0 + jstar[a.b];
+            len = a.m;
+        }
+        float acc[MG];
+        entry_warp<float, MG>(P, i, j, acc, s_tet[wib], s_cnt[wib], s_pre[wib]);
+#pragma unroll
+        for (int g = 0; g < MG; ++g)
+            if (g < P.G && lane == (g & 31)) buf[(mode == 0 ? a.rbuf : a.cbuf) + (int64_t)g * len + pos] = acc[g];
+    }
+}
+
+// Arbitrary (row, col) pairs, internal vertex ids.
+template <class R, int MG>
+__global__ void __launch_bounds__(32 * kWarpsPerCta) entries_pairs_kernel(KernelParams P, int group, int64_t count,
+                                                                          const int32_t* rows, const int32_t* cols,
+                                                                          const int* iperm, double* out)
+{
+    __shared__ int s_tet[kWarpsPerCta][32], s_cnt[kWarpsPerCta][32], s_pre[kWarpsPerCta][33];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * kWarpsPerCta;
+    for (int64_t e = (int64_t)blockIdx.x * kWarpsPerCta + wib; e < count; e += nw) {
+        int i = rows[e], j = cols[e];
+        if (iperm) {
+            i = iperm[i];
+            j = iperm[j];
+        }
+        R acc[MG];
+        entry_warp<R, MG>(P, i, j, acc, s_tet[wib], s_cnt[wib], s_pre[wib]);
+        R v = R(0);
+#pragma unroll
+        for (int g = 0; g < MG; ++g)
+            if (g == group) v = acc[g];
+        if (lane == 0) out[e] = (double)v;
+    }
+}
+
+static int grid_for(int64_t warps)
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t ctas = (warps + kWarpsPerCta - 1) / kWarpsPerCta;
+    int64_t cap = (int64_t)sms * 16;
+    return (int)std::max<int64_t>(1, std::min(ctas, cap));
+}
+
+// Dispatch on the group count: the accumulator array is sized at compile time.
+#define RT_DISPATCH_MG(G, MACRO) \
+    do {                         \
+        if ((G) <= 1) {          \
+            MACRO(1);            \
+        } else if ((G) <= 4) {   \
+            MACRO(4);            \
+        } else if ((G) <= 8) {   \
+            MACRO(8);            \
+        } else if ((G) <= 16) {  \
+            MACRO(16);           \
+        } else if ((G) <= 32) {  \
+            MACRO(32);           \
+        } else {                 \
+            MACRO(64);           \
+        }                        \
+    } while (0)
+
+template <class R, class OUT>
+static int launch_spans(Operator& op, const std::vector<EntrySpan>& spans_in, OUT* out, cudaStream_t s,
+                        std::string& err)
+{
+    if (spans_in.empty()) return RT_OK;
+    std::vector<EntrySpan> spans = spans_in;
+    int64_t total = 0;
+    for (auto& sp : spans) {
+        sp.first = total;
+        total += (int64_t)sp.ni * sp.nj;
+    }
+    EntrySpan* d_sp = nullptr;
+    RT_CUDA_TRY(cudaMallocAsync((void**)&d_sp, spans.size() * sizeof(EntrySpan), s));
+    RT_CUDA_TRY(cudaMemcpyAsync(d_sp, spans.data(), spans.size() * sizeof(EntrySpan), cudaMemcpyHostToDevice, s));
+    int grid = grid_for(total);
+    const int ns = (int)spans.size();
+#define RT_LAUNCH_SPANS(MG) \
+    entries_span_kernel<R, OUT, MG><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, d_sp, ns, total, out)
+    RT_DISPATCH_MG(op.G, RT_LAUNCH_SPANS);
+#undef RT_LAUNCH_SPANS
+    RT_CUDA_TRY(cudaGetLastError());
+    RT_CUDA_TRY(cudaFreeAsync(d_sp, s));
+    op.info.entries_evaluated += total;
+    return RT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// dense mode: the whole matrix [G][N][N] row-major
+// ---------------------------------------------------------------------------
+int assemble_dense(Operator& op, cudaStream_t s, std::string& err)
+{
+    const int64_t N = op.N;
+    const size_t esz = op.prec == RT_PREC_F64 ? 8 : 4;
+    int rc;
+    if (op.prec == RT_PREC_F64) {
+        double* d = nullptr;
+        if ((rc = dev_alloc(op, &d, (size_t)op.G * N * N, err))) return rc;
+        op.d_dense = d;
+    } else {
+        float* d = nullptr;
+        if ((rc = dev_alloc(op, &d, (size_t)op.G * N * N, err))) return rc;
+        op.d_dense = d;
+    }
+    // one span per row band keeps every span's entry count below 2^31
+    std::vector<EntrySpan> spans;
+    const int band = (int)std::max<int64_t>(1, std::min<int64_t>(N, (1 << 26) / std::max<int64_t>(N, 1)));
+    for (int64_t r0 = 0; r0 < N; r0 += band) {
+        EntrySpan sp{};
+        sp.i0 = (int)r0;
+        sp.ni = (int)std::min<int64_t>(band, N - r0);
+        sp.j0 = 0;
+        sp.nj = (int)N;
+        sp.base = r0 * N;
+        sp.gs = N * N;
+        sp.is = N;
+        sp.js = 1;
+        spans.push_back(sp);
+    }
+    if (op.prec == RT_PREC_F64) rc = launch_spans<double, double>(op, spans, (double*)op.d_dense, s, err);
+    else rc = launch_spans<float, float>(op, spans, (float*)op.d_dense, s, err);
+    if (rc) return rc;
+    op.info.stored_entries = N * N;
+    op.info.apply_bytes = (int64_t)op.F * N * N * (int64_t)esz + 2 * (int64_t)op.F * N * (int64_t)esz;
+    op.info.apply_flops = 2 * (int64_t)op.F * N * N;
+    return RT_OK;
+}
+
+int eval_entries(Operator& op, int group, int64_t count, const int32_t* rows, const int32_t* cols, double* out,
+                 cudaStream_t s, std::string& err)
+{
+    if (count <= 0) return RT_OK;
+    int grid = grid_for(count);
+    const int* ip = op.d_iperm;
+    if (op.prec == RT_PREC_F64) {
+#define RT_LAUNCH_PAIRS(MG) \
+    entries_pairs_kernel<double, MG><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, group, count, rows, cols, ip, out)
+        RT_DISPATCH_MG(op.G, RT_LAUNCH_PAIRS);
+#undef RT_LAUNCH_PAIRS
+    } else {
+#define RT_LAUNCH_PAIRS(MG) \
+    entries_pairs_kernel<float, MG><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, group, count, rows, cols, ip, out)
+        RT_DISPATCH_MG(op.G, RT_LAUNCH_PAIRS);
+#undef RT_LAUNCH_PAIRS
+    }
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// emitter source Sbar^E (Example of Section 1.2, Section 2)
+// ---------------------------------------------------------------------------
+// Shat_g(x_i) = (1/4pi) int_{Gamma_Q} ([(x-y).n]_-)^2 e^{-c_g tau(x,y)}/|x-y|^4
+//             + R0 ([(xbar-y).n]_-)^2 e^{-c_g(tau(x,x')+tau(x',y))}/|xbar-y|^4 dGamma(y),
+// 7-point rule within two diameters of the triangle centroid, 3-point rule
+// otherwise; a source point that is a vertex of the triangle contributes the
+// limit (angle at the vertex)/(8 pi) (times R0 for the image term).
+// One warp per vertex; lanes over triangles.  out[f][i] = Q_f Shat_{g(f)}(x_i).
+template <class R, int MG>
+__global__ void __launch_bounds__(256) source_kernel(KernelParams P, int n_emit, const int4* emit, const int* fgroup,
+                                                     const double* Q, int F, R* out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const R inv4pi = R(1.0 / (4.0 * kPi));
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < P.N; i += nw) {
+        const Vec3<R> xi = load_xyz<R>(P, (int)i);
+        Vec3<R> xb = xi;
+        bool on_wall = false;
+        if (P.has_wall) {
+            xb = mirror_point<R>(P, xi);
+            on_wall = dist2<R>(xi, xb) <= R(1e-20);
+        }
+        R acc[MG];
+#pragma unroll
+        for (int g = 0; g < MG; ++g) acc[g] = R(0);
+        for (int e = lane; e < n_emit; e += 32) {
+            const int4 tv = emit[e];
+            const Vec3<R> V0 = load_xyz<R>(P, tv.x), V1 = load_xyz<R>(P, tv.y), V2 = load_xyz<R>(P, tv.z);
+            const Vec3<R> e1 = {V1.x - V0.x, V1.y - V0.y, V1.z - V0.z};
+            const Vec3<R> e2 = {V2.x - V0.x, V2.y - V0.y, V2.z - V0.z};
+            Vec3<R> nn = {e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x};
+            const R a2 = sqrt_r(nn.x * nn.x + nn.y * nn.y + nn.z * nn.z);
+            nn.x /= a2;
+            nn.y /= a2;
+            nn.z /= a2;
+            const R area = R(0.5) * a2;
+            const Vec3<R> cen = {(V0.x + V1.x + V2.x) / R(3), (V0.y + V1.y + V2.y) / R(3), (V0.z + V1.z + V2.z) / R(3)};
+            R diam2 = dist2<R>(V0, V1);
+            diam2 = fmax(diam2, dist2<R>(V0, V2));
+            diam2 = fmax(diam2, dist2<R>(V1, V2));
+            int vloc = tv.x == (int)i ? 0 : (tv.y == (int)i ? 1 : (tv.z == (int)i ? 2 : -1));
+            for (int term = 0; term < 2; ++term) {
+                if (term == 1 && !P.has_wall) break;
+                const Vec3<R> src = term == 0 ? xi : xb;
+                const R scale = term == 0 ? R(1) : R(P.R0);
+                if (vloc >= 0 && (term == 0 || on_wall)) {
+                    // limit at a vertex of the emitter: angle / (8 pi)
+                    const Vec3<R> A = vloc == 0 ? V0 : (vloc == 1 ? V1 : V2);
+                    const Vec3<R> B = vloc == 0 ? V1 : (vloc == 1 ? V2 : V0);
+                    const Vec3<R> C = vloc == 0 ? V2 : (vloc == 1 ? V0 : V1);
+                    const Vec3<R> u = {B.x - A.x, B.y - A.y, B.z - A.z}, v = {C.x - A.x, C.y - A.y, C.z - A.z};
+                    R cs = (u.x * v.x + u.y * v.y + u.z * v.z) / sqrt_r((u.x * u.x + u.y * u.y + u.z * u.z) *
+                                                                         (v.x * v.x + v.y * v.y + v.z * v.z));
+                    cs = fmin(R(1), fmax(R(-1), cs));
+                    const R lim = scale * acos(cs) * R(1.0 / (8.0 * kPi));
+#pragma unroll
+                    for (int g = 0; g < MG; ++g)
+                        if (g < P.G) acc[g] += lim;
+                    continue;
+                }
+                const R sd = (src.x - V0.x) * nn.x + (src.y - V0.y) * nn.y + (src.z - V0.z) * nn.z;
+                if (!(sd < R(0))) continue;
+                const R cm = -sd;
+                const bool nearp = dist2<R>(src, cen) < R(4) * diam2;
+                const int q0 = nearp ? 3 : 0, nq = nearp ? 7 : 3;
+                for (int q = 0; q < nq; ++q) {
+                    const R b0 = R(c_tri_b[3 * (q0 + q)]), b1 = R(c_tri_b[3 * (q0 + q) + 1]),
+                            b2 = R(c_tri_b[3 * (q0 + q) + 2]);
+                    const Vec3<R> y = {b0 * V0.x + b1 * V1.x + b2 * V2.x, b0 * V0.y + b1 * V1.y + b2 * V2.y,
+                                       b0 * V0.z + b1 * V1.z + b2 * V2.z};
+                    const R r2 = dist2<R>(src, y);
+                    R tau;
+                    if (term == 0) {
+                        tau = optical_depth<R>(P, xi, y);
+                    } else {
+                        Vec3<R> xp = wall_point<R>(P, xb, y);
+                        tau = optical_depth<R>(P, xi, xp) + optical_depth<R>(P, xp, y);
+                    }
+                    const R geo = scale * area * R(c_tri_w[q0 + q]) * cm * cm / (r2 * r2) * inv4pi;
+#pragma unroll
+                    for (int g = 0; g < MG; ++g)
+                        if (g < P.G) acc[g] += geo * exp_r(-kp_c<R>(P, g) * tau);
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < MG; ++g) {
+            R v = acc[g];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            acc[g] = v;
+        }
+        if (lane == 0) {
+            for (int f = 0; f < F; ++f) {
+                R v = R(0);
+#pragma unroll
+                for (int g = 0; g < MG; ++g)
+                    if (g == fgroup[f]) v = acc[g];
+                out[(int64_t)f * P.N + i] = R(Q[f]) * v;
+            }
+        }
+    }
+}
+
+int assemble_source(Operator& op, cudaStream_t s, std::string& err)
+{
+    int rc;
+    int* d_fg = nullptr;
+    double* d_Q = nullptr;
+    RT_CUDA_TRY(cudaMallocAsync((void**)&d_fg, sizeof(int) * op.F, s));
+    RT_CUDA_TRY(cudaMallocAsync((void**)&d_Q, sizeof(double) * op.F, s));
+    RT_CUDA_TRY(cudaMemcpyAsync(d_fg, op.fgroup.data(), sizeof(int) * op.F, cudaMemcpyHostToDevice, s));
+    RT_CUDA_TRY(cudaMemcpyAsync(d_Q, op.Q.data(), sizeof(double) * op.F, cudaMemcpyHostToDevice, s));
+    const int grid = grid_for(op.N);
+    if (op.vec64) {
+        double* d = nullptr;
+        if ((rc = dev_alloc(op, &d, (size_t)op.F * op.N, err))) return rc;
+        op.d_SE = d;
+#define RT_LAUNCH_SRC(MG) \
+    source_kernel<double, MG><<<grid, 256, 0, s>>>(op.kp, op.n_emit, op.d_emit, d_fg, d_Q, op.F, d)
+        RT_DISPATCH_MG(op.G, RT_LAUNCH_SRC);
+#undef RT_LAUNCH_SRC
+    } else {
+        float* d = nullptr;
+        if ((rc = dev_alloc(op, &d, (size_t)op.F * op.N, err))) return rc;
+        op.d_SE = d;
+#define RT_LAUNCH_SRC(MG) \
+    source_kernel<float, MG><<<grid, 256, 0, s>>>(op.kp, op.n_emit, op.d_emit, d_fg, d_Q, op.F, d)
+        RT_DISPATCH_MG(op.G, RT_LAUNCH_SRC);
+#undef RT_LAUNCH_SRC
+    }
+    RT_CUDA_TRY(cudaGetLastError());
+    RT_CUDA_TRY(cudaFreeAsync(d_fg, s));
+    RT_CUDA_TRY(cudaFreeAsync(d_Q, s));
+    return RT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched partially pivoted ACA (Section 2.1), pivots shared by all groups.
+//
+// Every admissible block b (m x n) is approximated for all groups g at once:
+//   step k: residual row  R_g = G_g[i*, :] - sum_{l<k} u_{g,l}[i*] v_{g,l}
+//           pivot column  j*  = argmax_j sum_g |R_g[j]| / w_g   (first index on ties)
+//           v_g = R_g / R_g[j*]           (skipped for a group whose pivot is 0)
+//           u_g = G_g[:, j*] - sum_{l<k} u_{g,l} v_{g,l}[j*]
+//           ||S_g||_F^2 += 2 sum_{l<k} (u_l.u)(v_l.v) + |u|^2 |v|^2      (FP64)
+//           group g done when |u_g| |v_g| <= eps ||S_g||_F
+//           next row i* = argmax over unused rows of sum_g |u_g[i]| / w_g
+// w_g = ||S_g||_F (1 before the first term) puts the groups on one scale.
+// A block stops when every group is done; when another term would make
+// r (m + n) >= m n, or the rank limit is reached, it is stored dense.
+// The first pivot row is the block's first row.
+// ---------------------------------------------------------------------------
+namespace {
+
+enum { ACA_ACTIVE = 0, ACA_DONE = 1, ACA_DENSE = 2 };
+
+__device__ __forceinline__ unsigned long long score_key(float s, int idx)
+{
+    if (!(s >= 0.0f) || isinf(s)) s = 0.0f;
+    return ((unsigned long long)__float_as_uint(s) << 32) | (unsigned long long)(0xffffffffu - (unsigned)idx);
+}
+
+struct AcaDev {
+    int G;
+    int rmax;
+    double eps;
+    const FarBlock* blk;
+    int* istar;
+    int* jstar;
+    int* rank;
+    int* status;
+    double* norm2;      // [nfar][G]
+    float* wscale;      // [nfar][G]   score weights 1/w_g
+    float* inv;         // [nfar][G]
+    int64_t* uoff;      // [nfar][rmax]
+    int64_t* voff;      // [nfar][rmax]
+    unsigned char* used;   // [sum m]
+    int64_t* used_off;  // [nfar]
+    unsigned long long* key;   // [nfar]  row pivot key, then next-row key
+    unsigned* rowmax;   // [nfar][G]  max |R_g| of the current row (float bits)
+    double* dots;       // [nfar][rmax+1][G][2]  (u_l.u, v_l.v), l = rank -> (|u|^2, |v|^2)
+    float* pool;
+};
+
+// residual row: R_g[jj] -= sum_l u_{g,l}[i*] v_{g,l}[jj]; row key = argmax score.
+__global__ void aca_row_residual(AcaDev D, const AcaActive* act, int na, int64_t total, float* buf)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int ai = find_active(act, na, e, 0);
+        const AcaActive a = act[ai];
+        const int jj = (int)(e - a.first_row);
+        const int b = a.b, r = D.rank[b], is = D.istar[b];
+        float score = 0.0f;
+        for (int g = 0; g < D.G; ++g) {
+            float v = buf[a.rbuf + (int64_t)g * a.n + jj];
+            for (int l = 0; l < r; ++l) {
+                const float* U = D.pool + D.uoff[(int64_t)b * D.rmax + l] + (int64_t)g * a.m;
+                const float* V = D.pool + D.voff[(int64_t)b * D.rmax + l] + (int64_t)g * a.n;
+                v -= U[is] * V[jj];
+            }
+            buf[a.rbuf + (int64_t)g * a.n + jj] = v;
+            score += fabsf(v) * D.wscale[(int64_t)b * D.G + g];
+            if (isfinite(v)) atomicMax(&D.rowmax[(int64_t)b * D.G + g], __float_as_uint(fabsf(v)));
+        }
+        atomicMax(&D.key[b], score_key(score, jj));
+    }
+}
+
+// pivot column j*, 1/delta per group; a zero row is skipped.
+__global__ void aca_row_pivot(AcaDev D, AcaActive* act, int na, const float* buf)
+{
+    for (int ai = blockIdx.x * blockDim.x + threadIdx.x; ai < na; ai += gridDim.x * blockDim.x) {
+        AcaActive& a = act[ai];
+        const int b = a.b;
+        const unsigned long long k = D.key[b];
+        const float best = __uint_as_float((unsigned)(k >> 32));
+        const int j = (int)(0xffffffffu - (unsigned)(k & 0xffffffffu));
+        D.key[b] = 0ull;
+        if (!(best > 0.0f)) {
+            // exact zero row: mark it used and move to the next unused row
+            a.skip = 1;
+            D.used[D.used_off[b] + D.istar[b]] = 1;
+            int nxt = -1;
+            for (int i = 0; i < a.m; ++i)
+                if (!D.used[D.used_off[b] + i]) {
+                    nxt = i;
+                    break;
+                }
+            if (nxt < 0) D.status[b] = ACA_DONE;
+            else D.istar[b] = nxt;
+            continue;
+        }
+        a.skip = 0;
+        D.jstar[b] = j;
+        for (int g = 0; g < D.G; ++g) {
+            const float d = buf[a.rbuf + (int64_t)g * a.n + j];
+            const float rmx = __uint_as_float(D.rowmax[(int64_t)b * D.G + g]);
+            D.rowmax[(int64_t)b * D.G + g] = 0u;
+            // a group whose value at the shared pivot is negligible skips this term
+            D.inv[(int64_t)b * D.G + g] = (fabsf(d) > 1e-4f * rmx && fabsf(d) > 1e-37f) ? 1.0f / d : 0.0f;
+        }
+    }
+}
+
+// v_g = R_g * inv_g into the pool
+__global__ void aca_store_v(AcaDev D, const AcaActive* act, int na, int64_t total, const float* buf)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int ai = find_active(act, na, e, 0);
+        const AcaActive a = act[ai];
+        if (a.skip) continue;
+        const int jj = (int)(e - a.first_row);
+        for (int g = 0; g < D.G; ++g)
+            D.pool[a.voff + (int64_t)g * a.n + jj] =
+                buf[a.rbuf + (int64_t)g * a.n + jj] * D.inv[(int64_t)a.b * D.G + g];
+    }
+}
+
+// u_g = C_g - sum_l u_{g,l} v_{g,l}[j*]; next-row key over unused rows.
+__global__ void aca_col_residual(AcaDev D, const AcaActive* act, int na, int64_t total, const float* buf)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int ai = find_active(act, na, e, 1);
+        const AcaActive a = act[ai];
+        if (a.skip) continue;
+        const int ii = (int)(e - a.first_col);
+        const int b = a.b, r = D.rank[b], js = D.jstar[b];
+        float score = 0.0f;
+        for (int g = 0; g < D.G; ++g) {
+            float v = buf[a.cbuf + (int64_t)g * a.m + ii];
+            for (int l = 0; l < r; ++l) {
+                const float* U = D.pool + D.uoff[(int64_t)b * D.rmax + l] + (int64_t)g * a.m;
+                const float* V = D.pool + D.voff[(int64_t)b * D.rmax + l] + (int64_t)g * a.n;
+                v -= U[ii] * V[js];
+            }
+            if (D.inv[(int64_t)b * D.G + g] == 0.0f) v = 0.0f;
+            D.pool[a.uoff + (int64_t)g * a.m + ii] = v;
+            score += fabsf(v) * D.wscale[(int64_t)b * D.G + g];
+        }
+        if (ii != D.istar[b] && !D.used[D.used_off[b] + ii]) atomicMax(&D.key[b], score_key(score, ii));
+    }
+}
+
+// dots (u_l.u, v_l.v) for l = 0..rank (l = rank: the new term itself); one CTA per (block, l).
+struct DotItem {
+    int ai;
+    int l;
+};
+
+__global__ void __launch_bounds__(256) aca_dots(AcaDev D, const AcaActive* act, const DotItem* items, int nitems)
+{
+    __shared__ double red[2][8];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const DotItem di = items[it];
+        const AcaActive a = act[di.ai];
+        if (a.skip) continue;
+        const int b = a.b;
+        const int64_t ul = di.l == D.rank[b] ? a.uoff : D.uoff[(int64_t)b * D.rmax + di.l];
+        const int64_t vl = di.l == D.rank[b] ? a.voff : D.voff[(int64_t)b * D.rmax + di.l];
+        for (int g = 0; g < D.G; ++g) {
+            double su = 0.0, sv = 0.0;
+            const float* U0 = D.pool + ul + (int64_t)g * a.m;
+            const float* U1 = D.pool + a.uoff + (int64_t)g * a.m;
+            const float* V0 = D.pool + vl + (int64_t)g * a.n;
+            const float* V1 = D.pool + a.voff + (int64_t)g * a.n;
+            for (int i = threadIdx.x; i < a.m; i += blockDim.x) su += (double)U0[i] * (double)U1[i];
+            for (int j = threadIdx.x; j < a.n; j += blockDim.x) sv += (double)V0[j] * (double)V1[j];
+            for (int o = 16; o > 0; o >>= 1) {
+                su += __shfl_xor_sync(0xffffffffu, su, o);
+                sv += __shfl_xor_sync(0xffffffffu, sv, o);
+            }
+            if ((threadIdx.x & 31) == 0) {
+                red[0][threadIdx.x >> 5] = su;
+                red[1][threadIdx.x >> 5] = sv;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tu = 0.0, tv = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                    tu += red[0][w];
+                    tv += red[1][w];
+                }
+                double* dst = D.dots + (((int64_t)b * (D.rmax + 1) + di.l) * D.G + g) * 2;
+                dst[0] = tu;
+                dst[1] = tv;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void aca_finish(AcaDev D, const AcaActive* act, int na)
+{
+    for (int ai = blockIdx.x * blockDim.x + threadIdx.x; ai < na; ai += gridDim.x * blockDim.x) {
+        const AcaActive a = act[ai];
+        if (a.skip) continue;
+        const int b = a.b, r = D.rank[b];
+        bool all_done = true;
+        for (int g = 0; g < D.G; ++g) {
+            const double* dk = D.dots + (((int64_t)b * (D.rmax + 1) + r) * D.G + g) * 2;
+            const double uu = dk[0], vv = dk[1];
+            double s = D.norm2[(int64_t)b * D.G + g];
+            double cross = 0.0;
+            for (int l = 0; l < r; ++l) {
+                const double* dl = D.dots + (((int64_t)b * (D.rmax + 1) + l) * D.G + g) * 2;
+                cross += dl[0] * dl[1];
+            }
+            s += 2.0 * cross + uu * vv;
+            if (s < 0.0) s = 0.0;
+            D.norm2[(int64_t)b * D.G + g] = s;
+            const bool done = sqrt(uu * vv) <= D.eps * sqrt(s);
+            all_done = all_done && done;
+            D.wscale[(int64_t)b * D.G + g] = s > 0.0 ? (float)(1.0 / sqrt(s)) : 1.0f;
+        }
+        D.uoff[(int64_t)b * D.rmax + r] = a.uoff;
+        D.voff[(int64_t)b * D.rmax + r] = a.voff;
+        D.used[D.used_off[b] + D.istar[b]] = 1;
+        const int nr = r + 1;
+        D.rank[b] = nr;
+        const unsigned long long k = D.key[b];
+        D.key[b] = 0ull;
+        const float best = __uint_as_float((unsigned)(k >> 32));
+        if (all_done) {
+            D.status[b] = ACA_DONE;
+        } else if ((int64_t)(nr + 1) * (a.m + a.n) >= (int64_t)a.m * a.n || nr >= D.rmax) {
+            D.status[b] = ACA_DENSE;
+        } else if (k == 0ull || !(best > 0.0f)) {
+            // no unused row with a nonzero residual: the approximation is exact on all rows seen
+            D.status[b] = ACA_DONE;
+        } else {
+            D.istar[b] = (int)(0xffffffffu - (unsigned)(k & 0xffffffffu));
+        }
+    }
+}
+
+// repack converged blocks into V^T [G][r][n] and U^T [G][r][m] in the final storage type
+template <class T>
+__device__ __forceinline__ T to_store(float x);
+template <>
+__device__ __forceinline__ float to_store<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <>
+__device__ __forceinline__ __half to_store<__half>(float x) { return __float2half_rn(x); }
+
+struct PackItem {
+    int b;          // far block id
+    int l;          // term
+    int r, m, n;
+    int64_t voff_dst, uoff_dst;   // element offsets of the block's V^T and U^T in the final storage
+};
+
+template <class T>
+__global__ void aca_pack(AcaDev D, const PackItem* items, int nitems, T* dst)
+{
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const PackItem p = items[it];
+        const int64_t us = D.uoff[(int64_t)p.b * D.rmax + p.l], vs = D.voff[(int64_t)p.b * D.rmax + p.l];
+        for (int g = 0; g < D.G; ++g) {
+            for (int j = threadIdx.x; j < p.n; j += blockDim.x)
+                dst[p.voff_dst + ((int64_t)g * p.r + p.l) * p.n + j] = to_store<T>(D.pool[vs + (int64_t)g * p.n + j]);
+            for (int i = threadIdx.x; i < p.m; i += blockDim.x)
+                dst[p.uoff_dst + ((int64_t)g * p.r + p.l) * p.m + i] = to_store<T>(D.pool[us + (int64_t)g * p.m + i]);
+        }
+    }
+}
+
+}  // namespace
+
+int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
+{
+    int rc;
+    const int G = op.G;
+    const std::vector<FarBlock>& farb = op.plan.far_blocks;
+    const int nfar = (int)farb.size();
+    const int rmax = op.rank_max;
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, s);
+
+    std::vector<int> final_status(nfar, ACA_DENSE), final_rank(nfar, 0);
+    int64_t aca_steps = 0;
+    AcaDev D{};
+    std::vector<void*> tmp;   // freed at the end
+    auto talloc = [&](void** p, size_t bytes) -> int {
+        cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
+        if (e != cudaSuccess) {
+            err = std::string("cudaMalloc (ACA scratch): ") + cudaGetErrorString(e);
+            return RT_ENOMEM;
+        }
+        tmp.push_back(*p);
+        return RT_OK;
+    };
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(s);
+        for (void* p : tmp) cudaFree(p);
+        tmp.clear();
+    };
+    float* pool = nullptr;
+    int64_t pool_cap = 0, pool_used = 0;
+
+    if (nfar > 0) {
+        D.G = G;
+        D.rmax = rmax;
+        D.eps = op.aca_eps;
+        int64_t sum_m = 0;
+        std::vector<int64_t> used_off(nfar);
+        for (int b = 0; b < nfar; ++b) {
+            used_off[b] = sum_m;
+            sum_m += farb[b].m;
+        }
+#define TA(ptr, bytes)                                       \
+    do {                                                     \
+        if ((rc = talloc((void**)&(ptr), (bytes)))) {        \
+            cleanup();                                       \
+            return rc;                                       \
+        }                                                    \
+    } while (0)
+        FarBlock* d_blk;
+        TA(d_blk, sizeof(FarBlock) * nfar);
+        TA(D.istar, sizeof(int) * nfar);
+        TA(D.jstar, sizeof(int) * nfar);
+        TA(D.rank, sizeof(int) * nfar);
+        TA(D.status, sizeof(int) * nfar);
+        TA(D.norm2, sizeof(double) * nfar * G);
+        TA(D.wscale, sizeof(float) * nfar * G);
+        TA(D.inv, sizeof(float) * nfar * G);
+        TA(D.uoff, sizeof(int64_t) * nfar * rmax);
+        TA(D.voff, sizeof(int64_t) * nfar * rmax);
+        TA(D.used, sum_m);
+        TA(D.used_off, sizeof(int64_t) * nfar);
+        TA(D.key, sizeof(unsigned long long) * nfar);
+        TA(D.rowmax, sizeof(unsigned) * nfar * G);
+        TA(D.dots, sizeof(double) * 2 * (size_t)nfar * (rmax + 1) * G);
+        D.blk = d_blk;
+        RT_CUDA_TRY(cudaMemcpyAsync(d_blk, farb.data(), sizeof(FarBlock) * nfar, cudaMemcpyHostToDevice, s));
+        RT_CUDA_TRY(cudaMemsetAsync(D.istar, 0, sizeof(int) * nfar, s));
+        RT_CUDA_TRY(cudaMemsetAsync(D.rank, 0, sizeof(int) * nfar, s));
+        RT_CUDA_TRY(cudaMemsetAsync(D.status, 0, sizeof(int) * nfar, s));
+        RT_CUDA_TRY(cudaMemsetAsync(D.norm2, 0, sizeof(double) * nfar * G, s));
+        {
+            std::vector<float> ones((size_t)nfar * G, 1.0f);
+            RT_CUDA_TRY(cudaMemcpyAsync(D.wscale, ones.data(), sizeof(float) * ones.size(), cudaMemcpyHostToDevice, s));
+            RT_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        RT_CUDA_TRY(cudaMemsetAsync(D.used, 0, sum_m, s));
+        RT_CUDA_TRY(cudaMemcpyAsync(D.used_off, used_off.data(), sizeof(int64_t) * nfar, cudaMemcpyHostToDevice, s));
+        RT_CUDA_TRY(cudaMemsetAsync(D.key, 0, sizeof(unsigned long long) * nfar, s));
+        RT_CUDA_TRY(cudaMemsetAsync(D.rowmax, 0, sizeof(unsigned) * nfar * G, s));
+
+        // row/col buffers sized for all blocks at once
+        int64_t sum_n = 0;
+        for (auto& fb : farb) sum_n += fb.n;
+        float *rowbuf, *colbuf;
+        TA(rowbuf, sizeof(float) * (size_t)G * sum_n);
+        TA(colbuf, sizeof(float) * (size_t)G * sum_m);
+        AcaActive* d_act;
+        TA(d_act, sizeof(AcaActive) * nfar);
+        DotItem* d_dot;
+        int64_t dot_cap = 0;
+        d_dot = nullptr;
+        int* h_status = nullptr;
+        RT_CUDA_TRY(cudaMallocHost((void**)&h_status, sizeof(int) * nfar * 2));
+        std::vector<int> h_rank(nfar, 0);
+
+        // initial pool: the first 8 steps of every block
+        pool_cap = 0;
+        for (auto& fb : farb) pool_cap += (int64_t)G * (fb.m + fb.n) * 8;
+        {
+            cudaError_t e = cudaMalloc((void**)&pool, sizeof(float) * pool_cap);
+            if (e != cudaSuccess) {
+                cudaFreeHost(h_status);
+                cleanup();
+                err = "cudaMalloc (ACA pool) failed";
+                return RT_ENOMEM;
+            }
+        }
+        D.pool = pool;
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+
+        std::vector<int> status(nfar, ACA_ACTIVE);
+        std::vector<AcaActive> act;
+        std::vector<DotItem> dots;
+        for (int step = 0; step < rmax + 64; ++step) {
+            act.clear();
+            int64_t fr = 0, fc = 0, bufr = 0, bufc = 0;
+            int64_t need = 0;
+            for (int b = 0; b < nfar; ++b)
+                if (status[b] == ACA_ACTIVE) need += (int64_t)G * (farb[b].m + farb[b].n);
+            if (need == 0) break;
+            if (pool_used + need > pool_cap) {
+                int64_t ncap = std::max<int64_t>(pool_cap * 2, pool_used + need * 8);
+                float* np = nullptr;
+                cudaError_t e = cudaMalloc((void**)&np, sizeof(float) * ncap);
+                if (e != cudaSuccess) {
+                    cudaFreeHost(h_status);
+                    cudaFree(pool);
+                    cleanup();
+                    err = "cudaMalloc (ACA pool growth) failed";
+                    return RT_ENOMEM;
+                }
+                RT_CUDA_TRY(cudaMemcpyAsync(np, pool, sizeof(float) * pool_used, cudaMemcpyDeviceToDevice, s));
+                RT_CUDA_TRY(cudaStreamSynchronize(s));
+                cudaFree(pool);
+                pool = np;
+                pool_cap = ncap;
+                D.pool = pool;
+            }
+            for (int b = 0; b < nfar; ++b) {
+                if (status[b] != ACA_ACTIVE) continue;
+                AcaActive a{};
+                a.b = b;
+                a.row0 = farb[b].row0;
+                a.m = farb[b].m;
+                a.col0 = farb[b].col0;
+                a.n = farb[b].n;
+                a.first_row = fr;
+                a.first_col = fc;
+                a.rbuf = bufr;
+                a.cbuf = bufc;
+                a.uoff = pool_used;
+                pool_used += (int64_t)G * a.m;
+                a.voff = pool_used;
+                pool_used += (int64_t)G * a.n;
+                fr += a.n;
+                fc += a.m;
+                bufr += (int64_t)G * a.n;
+                bufc += (int64_t)G * a.m;
+                act.push_back(a);
+            }
+            const int na = (int)act.size();
+            RT_CUDA_TRY(cudaMemcpyAsync(d_act, act.data(), sizeof(AcaActive) * na, cudaMemcpyHostToDevice, s));
+            // 1. pivot rows
+            {
+                int grid = grid_for(fr);
+#define RT_LAUNCH_ACA(MG) \
+    aca_entries_kernel<MG><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, d_act, na, fr, 0, D.istar, D.jstar, rowbuf)
+                RT_DISPATCH_MG(G, RT_LAUNCH_ACA);
+#undef RT_LAUNCH_ACA
+                RT_CUDA_TRY(cudaGetLastError());
+            }
+            const int eg_r = (int)std::min<int64_t>((fr + 255) / 256, (int64_t)sms * 32);
+            aca_row_residual<<<std::max(1, eg_r), 256, 0, s>>>(D, d_act, na, fr, rowbuf);
+            aca_row_pivot<<<(na + 127) / 128, 128, 0, s>>>(D, d_act, na, rowbuf);
+            aca_store_v<<<std::max(1, eg_r), 256, 0, s>>>(D, d_act, na, fr, rowbuf);
+            // 2. pivot columns
+            {
+                int grid = grid_for(fc);
+#define RT_LAUNCH_ACAC(MG) \
+    aca_entries_kernel<MG><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, d_act, na, fc, 1, D.istar, D.jstar, colbuf)
+                RT_DISPATCH_MG(G, RT_LAUNCH_ACAC);
+#undef RT_LAUNCH_ACAC
+                RT_CUDA_TRY(cudaGetLastError());
+            }
+            const int eg_c = (int)std::min<int64_t>((fc + 255) / 256, (int64_t)sms * 32);
+            aca_col_residual<<<std::max(1, eg_c), 256, 0, s>>>(D, d_act, na, fc, colbuf);
+            // 3. dots with all previous terms and the new one
+            dots.clear();
+            for (int ai = 0; ai < na; ++ai)
+                for (int l = 0; l <= h_rank[act[ai].b]; ++l) dots.push_back({ai, l});
+            if ((int64_t)dots.size() > dot_cap) {
+                if (d_dot) cudaFree(d_dot);
+                dot_cap = (int64_t)dots.size() * 2;
+                RT_CUDA_TRY(cudaMalloc((void**)&d_dot, sizeof(DotItem) * dot_cap));
+            }
+            RT_CUDA_TRY(cudaMemcpyAsync(d_dot, dots.data(), sizeof(DotItem) * dots.size(), cudaMemcpyHostToDevice, s));
+            aca_dots<<<(int)std::min<int64_t>((int64_t)dots.size(), (int64_t)sms * 16), 256, 0, s>>>(
+                D, d_act, d_dot, (int)dots.size());
+            aca_finish<<<(na + 127) / 128, 128, 0, s>>>(D, d_act, na);
+            RT_CUDA_TRY(cudaGetLastError());
+            RT_CUDA_TRY(cudaMemcpyAsync(h_status, D.status, sizeof(int) * nfar, cudaMemcpyDeviceToHost, s));
+            RT_CUDA_TRY(cudaMemcpyAsync(h_status + nfar, D.rank, sizeof(int) * nfar, cudaMemcpyDeviceToHost, s));
+            RT_CUDA_TRY(cudaStreamSynchronize(s));
+            for (int b = 0; b < nfar; ++b) {
+                status[b] = h_status[b];
+                h_rank[b] = h_status[nfar + b];
+            }
+            ++aca_steps;
+        }
+        for (int b = 0; b < nfar; ++b) {
+            final_status[b] = status[b] == ACA_ACTIVE ? ACA_DENSE : status[b];
+            final_rank[b] = h_rank[b];
+        }
+        if (d_dot) cudaFree(d_dot);
+        cudaFreeHost(h_status);
+#undef TA
+    }
+    cudaEventRecord(ev1, s);
+    cudaEventSynchronize(ev1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    op.info.ms_aca = ms;
+    op.info.aca_steps = aca_steps;
+
+    // ---- final split: ACA blocks and dense blocks --------------------------
+    op.far_blocks.clear();
+    op.dense_blocks = op.plan.near_blocks;
+    op.rank.clear();
+    std::vector<int> far_src;
+    for (int b = 0; b < nfar; ++b) {
+        if (final_status[b] == ACA_DONE && final_rank[b] > 0) {
+            op.far_blocks.push_back(farb[b]);
+            op.rank.push_back(final_rank[b]);
+            far_src.push_back(b);
+        } else if (final_status[b] == ACA_DONE && final_rank[b] == 0) {
+            // an all-zero block: nothing to store
+        } else {
+            op.dense_blocks.push_back(farb[b]);
+            op.n_fallback++;
+        }
+    }
+    op.n_far = (int)op.far_blocks.size();
+    op.n_near = (int)op.dense_blocks.size();
+
+    // ---- far storage (pack) --------------------------------------------------
+    cudaEventRecord(ev0, s);
+    const int esz = op.far_prec == RT_PREC_F32 ? 4 : 2;
+    int64_t far_elems = 0;
+    op.far_v_off.assign(op.n_far, 0);
+    op.far_u_off.assign(op.n_far, 0);
+    for (int k = 0; k < op.n_far; ++k) {
+        const FarBlock& fb = op.far_blocks[k];
+        const int r = op.rank[k];
+        op.far_v_off[k] = far_elems;
+        far_elems += (int64_t)G * r * fb.n;
+        far_elems = (far_elems + 7) & ~(int64_t)7;
+        op.far_u_off[k] = far_elems;
+        far_elems += (int64_t)G * r * fb.m;
+        far_elems = (far_elems + 7) & ~(int64_t)7;
+    }
+    if (op.n_far > 0) {
+        char* d = nullptr;
+        if ((rc = dev_alloc(op, &d, (size_t)far_elems * esz, err))) {
+            if (pool) cudaFree(pool);
+            cleanup();
+            return rc;
+        }
+        op.d_far = d;
+        std::vector<PackItem> items;
+        for (int k = 0; k < op.n_far; ++k)
+            for (int l = 0; l < op.rank[k]; ++l)
+                items.push_back({far_src[k], l, op.rank[k], op.far_blocks[k].m, op.far_blocks[k].n, op.far_v_off[k],
+                                 op.far_u_off[k]});
+        PackItem* d_items = nullptr;
+        RT_CUDA_TRY(cudaMalloc((void**)&d_items, sizeof(PackItem) * items.size()));
+        RT_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), sizeof(PackItem) * items.size(), cudaMemcpyHostToDevice, s));
+        const int grid = (int)std::min<size_t>(items.size(), 152 * 64);
+        if (op.far_prec == RT_PREC_F32) aca_pack<float><<<grid, 256, 0, s>>>(D, d_items, (int)items.size(), (float*)d);
+        else if (op.far_prec == RT_PREC_BF16)
+            aca_pack<__nv_bfloat16><<<grid, 256, 0, s>>>(D, d_items, (int)items.size(), (__nv_bfloat16*)d);
+        else aca_pack<__half><<<grid, 256, 0, s>>>(D, d_items, (int)items.size(), (__half*)d);
+        RT_CUDA_TRY(cudaGetLastError());
+        RT_CUDA_TRY(cudaStreamSynchronize(s));
+        cudaFree(d_items);
+    }
+    if (pool) cudaFree(pool);
+    cleanup();
+    cudaEventRecord(ev1, s);
+    cudaEventSynchronize(ev1);
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    op.info.ms_pack = ms;
+
+    // ---- dense blocks (near leaves and fallbacks): A^T [G][n][m] ------------
+    cudaEventRecord(ev0, s);
+    int64_t near_elems = 0;
+    op.dense_off.assign(op.n_near, 0);
+    for (int k = 0; k < op.n_near; ++k) {
+        op.dense_off[k] = near_elems;
+        near_elems += (int64_t)G * op.dense_blocks[k].m * op.dense_blocks[k].n;
+        near_elems = (near_elems + 3) & ~(int64_t)3;
+    }
+    if (op.n_near > 0) {
+        if ((rc = dev_alloc(op, &op.d_near, (size_t)near_elems, err))) return rc;
+        std::vector<EntrySpan> spans;
+        for (int k = 0; k < op.n_near; ++k) {
+            const FarBlock& fb = op.dense_blocks[k];
+            EntrySpan sp{};
+            sp.i0 = fb.row0;
+            sp.ni = fb.m;
+            sp.j0 = fb.col0;
+            sp.nj = fb.n;
+            sp.base = op.dense_off[k];
+            sp.gs = (int64_t)fb.m * fb.n;
+            sp.is = 1;
+            sp.js = fb.m;
+            spans.push_back(sp);
+        }
+        if ((rc = launch_spans<float, float>(op, spans, op.d_near, s, err))) return rc;
+    }
+    RT_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaEventRecord(ev1, s);
+    cudaEventSynchronize(ev1);
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    op.info.ms_near = ms;
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+
+    // ---- statistics ------------------------------------------------------------
+    int64_t stored = 0, rsum = 0, rmin = INT64_MAX, rmx = 0;
+    for (int k = 0; k < op.n_near; ++k) stored += (int64_t)op.dense_blocks[k].m * op.dense_blocks[k].n;
+    for (int k = 0; k < op.n_far; ++k) {
+        stored += (int64_t)op.rank[k] * (op.far_blocks[k].m + op.far_blocks[k].n);
+        rsum += op.rank[k];
+        rmin = std::min<int64_t>(rmin, op.rank[k]);
+        rmx = std::max<int64_t>(rmx, op.rank[k]);
+    }
+    op.info.stored_entries = stored;
+    op.info.rank_sum = rsum;
+    op.info.rank_min = op.n_far ? rmin : 0;
+    op.info.rank_max = rmx;
+    for (int b = 0; b < nfar; ++b) op.info.entries_evaluated += (int64_t)final_rank[b] * (farb[b].m + farb[b].n);
+    return RT_OK;
+}
+
+}  // namespace rt

@@ -1,0 +1,468 @@
+// rt_capi.cu -- the C ABI (include/rt.h): validation, host geometry
+// preparation, operator lifetime and error reporting.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rt_internal.h"
+
+struct rt_operator {
+    rt::Operator op;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+void release(rt::Operator& op)
+{
+    for (void* p : op.allocations)
+        if (p) cudaFree(p);
+    op.allocations.clear();
+}
+
+double planck_host(double nu, double T)
+{
+    if (!(T > 0.0)) return 0.0;
+    return nu * nu * nu / std::expm1(nu / T);
+}
+
+int validate(const rt_problem* P, const rt_hparams* H)
+{
+    if (!P || !H) return fail(RT_EINVAL, "null problem or hparams");
+    const rt_mesh& M = P->mesh;
+    if (M.n_vert <= 3 || !M.xyz) return fail(RT_EINVAL, "mesh: need at least 4 vertices and xyz");
+    if (M.n_vert > (int64_t)1 << 28) return fail(RT_EINVAL, "mesh: too many vertices");
+    if (M.n_tet <= 0 || !M.tet) return fail(RT_EINVAL, "mesh: no tetrahedra");
+    if (M.n_tet > (int64_t)1 << 29) return fail(RT_EINVAL, "mesh: too many tetrahedra");
+    for (int64_t k = 0; k < 4 * M.n_tet; ++k)
+        if (M.tet[k] < 0 || M.tet[k] >= M.n_vert) return fail(RT_EINVAL, "mesh: tetrahedron vertex id out of range");
+    for (int64_t k = 0; k < 3 * M.n_vert; ++k)
+        if (!std::isfinite(M.xyz[k])) return fail(RT_EINVAL, "mesh: non-finite coordinate");
+    if (P->n_emit < 0 || (P->n_emit > 0 && !P->emit_tri)) return fail(RT_EINVAL, "emitter triangles missing");
+    for (int64_t k = 0; k < 3 * P->n_emit; ++k)
+        if (P->emit_tri[k] < 0 || P->emit_tri[k] >= M.n_vert) return fail(RT_EINVAL, "emitter vertex id out of range");
+    if (P->n_walls < 0 || P->n_walls > 1) return fail(RT_EINVAL, "n_walls must be 0 or 1 (one reflection per ray)");
+    if (P->n_walls == 1) {
+        if (!P->walls) return fail(RT_EINVAL, "walls pointer missing");
+        const double* n = P->walls[0].n;
+        const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(nn > 0.0) || !std::isfinite(nn)) return fail(RT_EINVAL, "wall normal must be nonzero");
+        if (!(P->walls[0].R0 >= 0.0 && P->walls[0].R0 <= 1.0)) return fail(RT_EINVAL, "R0 must lie in [0, 1]");
+    }
+    if (P->kappa.kind != RT_KAPPA_CONST && P->kappa.kind != RT_KAPPA_SINPROD) return fail(RT_EINVAL, "kappa kind");
+    if (!(P->kappa.k0 >= 0.0) || !std::isfinite(P->kappa.k0)) return fail(RT_EINVAL, "kappa: k0 must be >= 0");
+    if (P->kappa.kind == RT_KAPPA_SINPROD && !(std::fabs(P->kappa.amp) <= P->kappa.k0))
+        return fail(RT_EINVAL, "kappa must stay nonnegative (|amp| <= k0)");
+    const rt_freqs& Fq = P->freqs;
+    if (Fq.F < 1 || Fq.F > 4096) return fail(RT_EINVAL, "frequency count must be in [1, 4096]");
+    if (!Fq.nu || !Fq.w || !Fq.c || !Fq.albedo) return fail(RT_EINVAL, "frequency arrays missing");
+    for (int f = 0; f < Fq.F; ++f) {
+        if (!(Fq.c[f] > 0.0) || !std::isfinite(Fq.c[f])) return fail(RT_EINVAL, "c must be > 0");
+        if (!(Fq.albedo[f] >= 0.0 && Fq.albedo[f] <= 1.0)) return fail(RT_EINVAL, "albedo must lie in [0, 1]");
+        if (!P->grey && !(Fq.nu[f] > 0.0)) return fail(RT_EINVAL, "nu must be > 0");
+    }
+    if (P->grey && Fq.F != 1) return fail(RT_EINVAL, "grey formulation needs F == 1");
+    if (H->mode != RT_MODE_DENSE && H->mode != RT_MODE_HMATRIX) return fail(RT_EINVAL, "mode");
+    if (H->mode == RT_MODE_DENSE && H->prec != RT_PREC_F64 && H->prec != RT_PREC_F32)
+        return fail(RT_EINVAL, "dense mode needs prec F64 or F32");
+    if (H->mode == RT_MODE_HMATRIX) {
+        if (H->prec != RT_PREC_F32) return fail(RT_EINVAL, "H-matrix mode computes in F32 (prec = RT_PREC_F32)");
+        if (H->far_prec != RT_PREC_F32 && H->far_prec != RT_PREC_BF16 && H->far_prec != RT_PREC_F16)
+            return fail(RT_EINVAL, "far_prec must be F32, BF16 or F16");
+        if (!(H->aca_eps > 0.0 && H->aca_eps < 1.0)) return fail(RT_EINVAL, "aca_eps must lie in (0, 1)");
+        if (H->leaf < 1) return fail(RT_EINVAL, "leaf must be >= 1");
+        if (!(H->eta > 0.0)) return fail(RT_EINVAL, "eta must be > 0");
+        if (H->rank_max < 0 || H->rank_max > 8192) return fail(RT_EINVAL, "rank_max must be in [0, 8192]");
+    }
+    if (H->gauss_pts < 1 || H->gauss_pts > rt::kMaxGauss) return fail(RT_EINVAL, "gauss_pts must be in [1, 32]");
+    if (M.n_vert * (int64_t)M.n_vert * Fq.F > ((int64_t)1 << 40) && H->mode == RT_MODE_DENSE)
+        return fail(RT_EINVAL, "dense operator too large");
+    return RT_OK;
+}
+
+template <class T>
+int upload(rt::Operator& op, T** dst, const std::vector<T>& src, std::string& err)
+{
+    int rc = rt::dev_alloc(op, dst, src.size(), err);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        err = std::string("cudaMemcpy: ") + cudaGetErrorString(e);
+        return RT_ECUDA;
+    }
+    return RT_OK;
+}
+
+int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream_t s, std::string& err)
+{
+    using namespace rt;
+    int rc;
+    cudaEvent_t e0, e1;
+    RT_CUDA_TRY(cudaGetDevice(&op.device));
+    const int64_t N = P->mesh.n_vert, T = P->mesh.n_tet;
+    op.N = (int)N;
+    op.T = (int)T;
+    op.mode = H->mode;
+    op.prec = H->mode == RT_MODE_DENSE ? H->prec : RT_PREC_F32;
+    op.far_prec = H->mode == RT_MODE_DENSE ? op.prec : H->far_prec;
+    op.vec64 = op.mode == RT_MODE_DENSE && op.prec == RT_PREC_F64;
+    op.aca_eps = H->aca_eps;
+    op.leaf = H->leaf;
+    op.eta = H->eta;
+    op.ngauss = H->gauss_pts;
+    op.rank_max = H->rank_max > 0 ? H->rank_max : 512;
+    op.grey = P->grey ? 1 : 0;
+    const rt_freqs& Fq = P->freqs;
+    op.F = Fq.F;
+    op.nu.assign(Fq.nu, Fq.nu + Fq.F);
+    op.w.assign(Fq.w, Fq.w + Fq.F);
+    op.c.assign(Fq.c, Fq.c + Fq.F);
+    op.albedo.assign(Fq.albedo, Fq.albedo + Fq.F);
+    op.fgroup.assign(Fq.F, 0);
+    for (int f = 0; f < Fq.F; ++f) {
+        int g = -1;
+        for (int k = 0; k < (int)op.gc.size(); ++k)
+            if (op.gc[k] == Fq.c[f]) g = k;
+        if (g < 0) {
+            if ((int)op.gc.size() >= kMaxGroups) {
+                err = "more than 64 distinct kappa scales c";
+                return RT_EINVAL;
+            }
+            g = (int)op.gc.size();
+            op.gc.push_back(Fq.c[f]);
+        }
+        op.fgroup[f] = g;
+    }
+    op.G = (int)op.gc.size();
+    op.Q.assign(Fq.F, 0.0);
+    for (int f = 0; f < Fq.F; ++f)
+        op.Q[f] = P->grey ? P->Q0 * 6.493939402266829 * std::pow(P->T_emit, 4.0) : P->Q0 * planck_host(Fq.nu[f], P->T_emit);
+
+    // ---- vertex order: cluster tree (H-matrix) or caller order (dense) -------
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    if (op.mode == RT_MODE_HMATRIX) {
+        if ((rc = plan_build(P->mesh.xyz, N, op.leaf, op.eta, op.plan, err))) return rc;
+    } else {
+        op.plan = Plan();
+        op.plan.N = (int)N;
+        op.plan.perm.resize(N);
+        op.plan.iperm.resize(N);
+        for (int64_t k = 0; k < N; ++k) op.plan.perm[k] = op.plan.iperm[k] = (int)k;
+        op.plan.leaf_start.push_back(0);
+        op.plan.leaf_size.push_back((int)N);
+    }
+    const std::vector<int>& perm = op.plan.perm;
+    const std::vector<int>& iperm = op.plan.iperm;
+    std::vector<double> xyz64(3 * N);
+    std::vector<float4> xyz32(N);
+    for (int64_t t = 0; t < N; ++t) {
+        const double* p = P->mesh.xyz + 3 * (int64_t)perm[t];
+        for (int d = 0; d < 3; ++d) xyz64[3 * t + d] = p[d];
+        xyz32[t] = make_float4((float)p[0], (float)p[1], (float)p[2], 0.f);
+    }
+    std::vector<int4> tet(T);
+    std::vector<dbl4> tg64(T);
+    std::vector<float4> tg32(T);
+    std::vector<double> tv64(T);
+    std::vector<float> tv32(T);
+    std::vector<int> cnt(N + 1, 0);
+    for (int64_t k = 0; k < T; ++k) {
+        const int32_t* v = P->mesh.tet + 4 * k;
+        int a[4] = {iperm[v[0]], iperm[v[1]], iperm[v[2]], iperm[v[3]]};
+        tet[k] = make_int4(a[0], a[1], a[2], a[3]);
+        const double* X[4];
+        for (int d = 0; d < 4; ++d) X[d] = &xyz64[3 * (int64_t)a[d]];
+        double e[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int d = 0; d < 3; ++d) e[r][d] = X[r + 1][d] - X[0][d];
+        const double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                           e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                           e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+        const double vol = std::fabs(det) / 6.0;
+        if (!(vol > 0.0)) {
+            err = "mesh: degenerate tetrahedron " + std::to_string(k);
+            return RT_EINVAL;
+        }
+        double cen[3], dm = 0.0;
+        for (int d = 0; d < 3; ++d) cen[d] = 0.25 * (X[0][d] + X[1][d] + X[2][d] + X[3][d]);
+        for (int i = 0; i < 4; ++i)
+            for (int j = i + 1; j < 4; ++j) {
+                double s2 = 0.0;
+                for (int d = 0; d < 3; ++d) s2 += (X[i][d] - X[j][d]) * (X[i][d] - X[j][d]);
+                dm = std::max(dm, std::sqrt(s2));
+            }
+        tg64[k] = make_dbl4(cen[0], cen[1], cen[2], dm);
+        tg32[k] = make_float4((float)cen[0], (float)cen[1], (float)cen[2], (float)dm);
+        tv64[k] = vol;
+        tv32[k] = (float)vol;
+        for (int d = 0; d < 4; ++d) cnt[a[d] + 1]++;
+    }
+    for (int64_t v = 0; v < N; ++v) cnt[v + 1] += cnt[v];
+    std::vector<int> vt_idx(cnt[N]);
+    {
+        std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+        for (int64_t k = 0; k < T; ++k) {
+            const int a[4] = {tet[k].x, tet[k].y, tet[k].z, tet[k].w};
+            for (int d = 0; d < 4; ++d) vt_idx[fill[a[d]]++] = (int)(k << 2) | d;
+        }
+    }
+    for (int64_t v = 0; v < N; ++v)
+        if (cnt[v + 1] == cnt[v]) {
+            err = "mesh: vertex " + std::to_string(perm[v]) + " belongs to no tetrahedron";
+            return RT_EINVAL;
+        }
+    std::vector<int4> emit(std::max<int64_t>(P->n_emit, 1));
+    for (int64_t k = 0; k < P->n_emit; ++k)
+        emit[k] = make_int4(iperm[P->emit_tri[3 * k]], iperm[P->emit_tri[3 * k + 1]], iperm[P->emit_tri[3 * k + 2]], 0);
+    op.n_emit = (int)P->n_emit;
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    op.info.ms_tree = ms;
+
+    if ((rc = upload(op, &op.d_xyz64, xyz64, err))) return rc;
+    if ((rc = upload(op, &op.d_xyz32, xyz32, err))) return rc;
+    if ((rc = upload(op, &op.d_tet, tet, err))) return rc;
+    if ((rc = upload(op, &op.d_tgeo64, tg64, err))) return rc;
+    if ((rc = upload(op, &op.d_tgeo32, tg32, err))) return rc;
+    if ((rc = upload(op, &op.d_tvol64, tv64, err))) return rc;
+    if ((rc = upload(op, &op.d_tvol32, tv32, err))) return rc;
+    if ((rc = upload(op, &op.d_vt_ptr, cnt, err))) return rc;
+    if ((rc = upload(op, &op.d_vt_idx, vt_idx, err))) return rc;
+    if ((rc = upload(op, &op.d_perm, perm, err))) return rc;
+    if ((rc = upload(op, &op.d_iperm, iperm, err))) return rc;
+    if ((rc = upload(op, &op.d_emit, emit, err))) return rc;
+
+    KernelParams& kp = op.kp;
+    kp.N = (int)N;
+    kp.T = (int)T;
+    kp.kappa_kind = P->kappa.kind;
+    kp.k0 = P->kappa.k0;
+    kp.amp = P->kappa.kind == RT_KAPPA_SINPROD ? P->kappa.amp : 0.0;
+    kp.k0f = (float)kp.k0;
+    kp.ampf = (float)kp.amp;
+    kp.has_wall = (P->n_walls == 1 && P->walls[0].R0 > 0.0) ? 1 : 0;
+    if (P->n_walls == 1) {
+        const double* n = P->walls[0].n;
+        const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        for (int d = 0; d < 3; ++d) {
+            kp.wp[d] = P->walls[0].p[d];
+            kp.wn[d] = n[d] / nn;
+        }
+        kp.R0 = P->walls[0].R0;
+    }
+    kp.G = op.G;
+    for (int g = 0; g < op.G; ++g) {
+        kp.c[g] = op.gc[g];
+        kp.cf[g] = (float)op.gc[g];
+    }
+    kp.ngauss = op.ngauss;
+    kp.xyz32 = op.d_xyz32;
+    kp.xyz64 = op.d_xyz64;
+    kp.tet = op.d_tet;
+    kp.tgeo32 = op.d_tgeo32;
+    kp.tgeo64 = op.d_tgeo64;
+    kp.tvol32 = op.d_tvol32;
+    kp.tvol64 = op.d_tvol64;
+    kp.vt_ptr = op.d_vt_ptr;
+    kp.vt_idx = op.d_vt_idx;
+    if ((rc = assemble_setup_constants(op, err))) return rc;
+
+    cudaEventRecord(e0, s);
+    if ((rc = assemble_source(op, s, err))) return rc;
+    cudaEventRecord(e1, s);
+    RT_CUDA_TRY(cudaEventSynchronize(e1));
+    cudaEventElapsedTime(&ms, e0, e1);
+    op.info.ms_source = ms;
+    if (op.mode == RT_MODE_DENSE) {
+        cudaEventRecord(e0, s);
+        if ((rc = assemble_dense(op, s, err))) return rc;
+        cudaEventRecord(e1, s);
+        RT_CUDA_TRY(cudaEventSynchronize(e1));
+        cudaEventElapsedTime(&ms, e0, e1);
+        op.info.ms_near = ms;
+        op.n_near = 1;
+    } else {
+        if ((rc = assemble_hmatrix(op, s, err))) return rc;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if ((rc = hmatvec_prepare(op, err))) return rc;
+    const size_t esz = op.vec64 ? 8 : 4;
+    {
+        char *a = nullptr, *b = nullptr;
+        if ((rc = dev_alloc(op, &a, (size_t)op.F * N * esz, err))) return rc;
+        if ((rc = dev_alloc(op, &b, (size_t)op.F * N * esz, err))) return rc;
+        op.d_xt = (float*)a;
+        op.d_yt = (float*)b;
+    }
+    RT_CUDA_TRY(cudaStreamSynchronize(s));
+    RT_CUDA_TRY(cudaGetLastError());
+    // statistics
+    rt_info& I = op.info;
+    I.N = N;
+    I.F = op.F;
+    I.G = op.G;
+    I.mode = op.mode;
+    I.prec = op.prec;
+    I.far_prec = op.far_prec;
+    I.n_leaves = (int64_t)op.plan.leaf_start.size();
+    I.n_near = op.mode == RT_MODE_DENSE ? 1 : (int64_t)op.plan.near_blocks.size();
+    I.n_far = op.n_far;
+    I.n_dense_fallback = op.n_fallback;
+    I.compression = 1.0 - (double)I.stored_entries / ((double)N * (double)N);
+    return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rt_build_operator(const rt_problem* prob, const rt_hparams* hp, void* stream, rt_operator** out)
+{
+    if (!out) return fail(RT_EINVAL, "out is null");
+    *out = nullptr;
+    int rc = validate(prob, hp);
+    if (rc) return rc;
+    rt_operator* h = new (std::nothrow) rt_operator();
+    if (!h) return fail(RT_ENOMEM, "host allocation failed");
+    std::string err;
+    try {
+        rc = build(h->op, prob, hp, (cudaStream_t)stream, err);
+    } catch (const std::bad_alloc&) {
+        rc = RT_ENOMEM;
+        err = "host allocation failed";
+    } catch (...) {
+        rc = RT_EINVAL;
+        err = "unexpected exception during build";
+    }
+    if (rc) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        release(h->op);
+        delete h;
+        return fail(rc, err);
+    }
+    *out = h;
+    g_err.clear();
+    return RT_OK;
+}
+
+int rt_operator_info(const rt_operator* op, rt_info* info)
+{
+    if (!op || !info) return fail(RT_EINVAL, "null argument");
+    *info = op->op.info;
+    return RT_OK;
+}
+
+int rt_apply(rt_operator* h, const void* X, void* Y, void* stream)
+{
+    if (!h || !X || !Y) return fail(RT_EINVAL, "null argument");
+    rt::Operator& op = h->op;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::string err;
+    int rc;
+    if (op.mode == RT_MODE_DENSE) {
+        rc = rt::apply_tree(op, X, Y, s, err);
+    } else {
+        rc = rt::permute_vectors(op, X, op.d_xt, 1, op.vec64, op.F, s);
+        if (!rc) rc = rt::apply_tree(op, op.d_xt, op.d_yt, s, err);
+        if (!rc) rc = rt::permute_vectors(op, op.d_yt, Y, 0, op.vec64, op.F, s);
+        if (rc && err.empty()) err = "kernel launch failed";
+    }
+    if (rc) return fail(rc, err);
+    return RT_OK;
+}
+
+int rt_source(rt_operator* h, void* out, void* stream)
+{
+    if (!h || !out) return fail(RT_EINVAL, "null argument");
+    rt::Operator& op = h->op;
+    int rc = rt::permute_vectors(op, op.d_SE, out, 0, op.vec64, op.F, (cudaStream_t)stream);
+    if (rc) return fail(rc, "permute failed");
+    return RT_OK;
+}
+
+int rt_eval_entries(rt_operator* h, int group, int64_t count, const int32_t* rows, const int32_t* cols, double* out,
+                    void* stream)
+{
+    if (!h || (count > 0 && (!rows || !cols || !out))) return fail(RT_EINVAL, "null argument");
+    if (group < 0 || group >= h->op.G) return fail(RT_EINVAL, "group out of range");
+    std::string err;
+    int rc = rt::eval_entries(h->op, group, count, rows, cols, out, (cudaStream_t)stream, err);
+    if (rc) return fail(rc, err);
+    return RT_OK;
+}
+
+int rt_solve_fixed_point(rt_operator* h, const rt_solve_opts* opts, void* J_dev, double* T_dev, rt_solve_stats* stats,
+                         void* stream)
+{
+    if (!h || !opts || !J_dev || !T_dev) return fail(RT_EINVAL, "null argument");
+    if (opts->max_iter < 1 || opts->check_every < 1 || !(opts->tol >= 0.0) || !(opts->T0 >= 0.0))
+        return fail(RT_EINVAL, "invalid solve options");
+    rt_solve_stats st{};
+    std::string err;
+    int rc = rt::solve_fixed_point(h->op, *opts, J_dev, T_dev, st, (cudaStream_t)stream, err);
+    if (stats) *stats = st;
+    if (rc) return fail(rc, err);
+    return RT_OK;
+}
+
+void rt_free(rt_operator* h)
+{
+    if (!h) return;
+    cudaDeviceSynchronize();
+    release(h->op);
+    delete h;
+}
+
+const char* rt_last_error(void) { return g_err.c_str(); }
+
+int rt_plan(const double* xyz, int64_t n, int leaf, double eta, int32_t* perm, int32_t* blocks, int64_t cap,
+            int64_t* counts)
+{
+    if (!xyz || !counts) return fail(RT_EINVAL, "null argument");
+    rt::Plan P;
+    std::string err;
+    int rc;
+    try {
+        rc = rt::plan_build(xyz, n, leaf, eta, P, err);
+    } catch (...) {
+        rc = RT_ENOMEM;
+        err = "host allocation failed";
+    }
+    if (rc) return fail(rc, err);
+    counts[0] = (int64_t)P.leaf_start.size();
+    counts[1] = (int64_t)P.near_blocks.size();
+    counts[2] = (int64_t)P.far_blocks.size();
+    if (perm)
+        for (int64_t k = 0; k < n; ++k) perm[k] = P.perm[k];
+    if (blocks) {
+        int64_t k = 0;
+        for (const auto& b : P.near_blocks) {
+            if (k >= cap) break;
+            int32_t* o = blocks + 5 * k++;
+            o[0] = b.row0; o[1] = b.m; o[2] = b.col0; o[3] = b.n; o[4] = 0;
+        }
+        for (const auto& b : P.far_blocks) {
+            if (k >= cap) break;
+            int32_t* o = blocks + 5 * k++;
+            o[0] = b.row0; o[1] = b.m; o[2] = b.col0; o[3] = b.n; o[4] = 1;
+        }
+    }
+    return RT_OK;
+}
+
+}  // extern "C"

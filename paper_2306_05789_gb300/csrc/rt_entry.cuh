@@ -1,0 +1,270 @@
+// rt_entry.cuh -- device evaluation of one matrix entry G_g^{ij} (Section 2).
+//
+//   G_g^{ij} = sum_{T containing x_j} sum_q |T| w_q lambda_j(y_q) K_g(x_i, y_q)
+//   K_g(x, y) = c_g kappa(y) / (4 pi) [ e^{-c_g tau(x,y)} / |x-y|^2
+//                                      + R0 e^{-c_g (tau(x,x') + tau(x',y))} / |xbar-y|^2 ]
+// (Corollary and Example of Section 1.2 with kappa folded in as in the FEM
+// matrix of Section 2; xbar = mirror image of x in the wall, x' = [xbar,y]
+// cut with the wall plane; tau = line integral of kappa by n-point Gauss.)
+// Quadrature per term: 14-point degree-5 rule when the term's source point
+// (x_i for the direct term, xbar_i for the reflected one) lies within two
+// diameters of the tetrahedron's centroid, 4-point degree-2 rule otherwise.
+//
+// One warp evaluates one entry: the (tetrahedron, quadrature point, term)
+// items of the entry are distributed over the lanes through a warp prefix sum,
+// each lane accumulates all groups, and a butterfly reduction leaves the sums
+// in every lane.  tau is computed once per item and shared by all groups
+// (kappa_nu = c_g kappa(x) => tau_g = c_g tau).
+#pragma once
+
+#include "rt_internal.h"
+
+namespace rt {
+
+// Tetrahedron and triangle rules as barycentric coordinates, set from the
+// host once per device.  (The Gauss nodes live in KernelParams.)  This header
+// is included by one translation unit only.
+__constant__ double c_tet_b[18 * 4];  // rows 0..3: 4-point rule, rows 4..17: 14-point rule
+__constant__ double c_tet_w[18];
+__constant__ float c_tet_bf[18 * 4];
+__constant__ float c_tet_wf[18];
+__constant__ double c_tri_b[10 * 3];  // rows 0..2: 3-point rule, rows 3..9: 7-point rule
+__constant__ double c_tri_w[10];
+
+template <class R>
+struct Vec3 {
+    R x, y, z;
+};
+
+template <class R>
+__device__ __forceinline__ R gauss_u(const KernelParams& P, int g);
+template <>
+__device__ __forceinline__ float gauss_u<float>(const KernelParams& P, int g) { return P.gu32[g]; }
+template <>
+__device__ __forceinline__ double gauss_u<double>(const KernelParams& P, int g) { return P.gu64[g]; }
+template <class R>
+__device__ __forceinline__ R gauss_w(const KernelParams& P, int g);
+template <>
+__device__ __forceinline__ float gauss_w<float>(const KernelParams& P, int g) { return P.gw32[g]; }
+template <>
+__device__ __forceinline__ double gauss_w<double>(const KernelParams& P, int g) { return P.gw64[g]; }
+
+template <class R>
+__device__ __forceinline__ R tet_b(int q, int k);
+template <>
+__device__ __forceinline__ float tet_b<float>(int q, int k) { return c_tet_bf[4 * q + k]; }
+template <>
+__device__ __forceinline__ double tet_b<double>(int q, int k) { return c_tet_b[4 * q + k]; }
+template <class R>
+__device__ __forceinline__ R tet_w(int q);
+template <>
+__device__ __forceinline__ float tet_w<float>(int q) { return c_tet_wf[q]; }
+template <>
+__device__ __forceinline__ double tet_w<double>(int q) { return c_tet_w[q]; }
+
+__device__ __forceinline__ float sinpi_r(float x) { return sinpif(x); }
+__device__ __forceinline__ double sinpi_r(double x) { return sinpi(x); }
+__device__ __forceinline__ float exp_r(float x) { return expf(x); }
+__device__ __forceinline__ double exp_r(double x) { return exp(x); }
+__device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
+
+template <class R>
+__device__ __forceinline__ R kp_k0(const KernelParams& P);
+template <>
+__device__ __forceinline__ float kp_k0<float>(const KernelParams& P) { return P.k0f; }
+template <>
+__device__ __forceinline__ double kp_k0<double>(const KernelParams& P) { return P.k0; }
+template <class R>
+__device__ __forceinline__ R kp_amp(const KernelParams& P);
+template <>
+__device__ __forceinline__ float kp_amp<float>(const KernelParams& P) { return P.ampf; }
+template <>
+__device__ __forceinline__ double kp_amp<double>(const KernelParams& P) { return P.amp; }
+template <class R>
+__device__ __forceinline__ R kp_c(const KernelParams& P, int g);
+template <>
+__device__ __forceinline__ float kp_c<float>(const KernelParams& P, int g) { return P.cf[g]; }
+template <>
+__device__ __forceinline__ double kp_c<double>(const KernelParams& P, int g) { return P.c[g]; }
+
+template <class R>
+__device__ __forceinline__ Vec3<R> load_xyz(const KernelParams& P, int v);
+template <>
+__device__ __forceinline__ Vec3<float> load_xyz<float>(const KernelParams& P, int v)
+{
+    float4 a = P.xyz32[v];
+    return {a.x, a.y, a.z};
+}
+template <>
+__device__ __forceinline__ Vec3<double> load_xyz<double>(const KernelParams& P, int v)
+{
+    return {P.xyz64[3 * (int64_t)v], P.xyz64[3 * (int64_t)v + 1], P.xyz64[3 * (int64_t)v + 2]};
+}
+
+template <class R>
+__device__ __forceinline__ void load_tgeo(const KernelParams& P, int t, Vec3<R>& c, R& diam, R& vol);
+template <>
+__device__ __forceinline__ void load_tgeo<float>(const KernelParams& P, int t, Vec3<float>& c, float& diam,
+                                                 float& vol)
+{
+    float4 g = P.tgeo32[t];
+    c = {g.x, g.y, g.z};
+    diam = g.w;
+    vol = P.tvol32[t];
+}
+template <>
+__device__ __forceinline__ void load_tgeo<double>(const KernelParams& P, int t, Vec3<double>& c, double& diam,
+                                                  double& vol)
+{
+    dbl4 g = P.tgeo64[t];
+    c = {g.x, g.y, g.z};
+    diam = g.w;
+    vol = P.tvol64[t];
+}
+
+template <class R>
+__device__ __forceinline__ R dist2(const Vec3<R>& a, const Vec3<R>& b)
+{
+    R dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    return dx * dx + dy * dy + dz * dz;
+}
+
+template <class R>
+__device__ __forceinline__ R kappa_at(const KernelParams& P, R x, R y, R z)
+{
+    R k = kp_k0<R>(P);
+    if (P.kappa_kind == RT_KAPPA_SINPROD)
+        k += kp_amp<R>(P) * sinpi_r(R(2) * x) * sinpi_r(R(2) * y) * sinpi_r(R(2) * z);
+    return k;
+}
+
+// int_[a,b] kappa = |b-a| sum_g (w_g/2) kappa(a + u_g (b-a)).  For constant
+// kappa the Gauss sum equals kappa |b-a| exactly (weights sum to 1).
+template <class R>
+__device__ __forceinline__ R optical_depth(const KernelParams& P, const Vec3<R>& a, const Vec3<R>& b)
+{
+    R dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+    R L = sqrt_r(dx * dx + dy * dy + dz * dz);
+    if (P.kappa_kind != RT_KAPPA_SINPROD) return kp_k0<R>(P) * L;
+    R s = R(0);
+    for (int g = 0; g < P.ngauss; ++g) {
+        R u = gauss_u<R>(P, g);
+        s += gauss_w<R>(P, g) * kappa_at<R>(P, a.x + u * dx, a.y + u * dy, a.z + u * dz);
+    }
+    return L * s;
+}
+
+template <class R>
+__device__ __forceinline__ Vec3<R> mirror_point(const KernelParams& P, const Vec3<R>& x)
+{
+    R s = (x.x - R(P.wp[0])) * R(P.wn[0]) + (x.y - R(P.wp[1])) * R(P.wn[1]) + (x.z - R(P.wp[2])) * R(P.wn[2]);
+    return {x.x - R(2) * s * R(P.wn[0]), x.y - R(2) * s * R(P.wn[1]), x.z - R(2) * s * R(P.wn[2])};
+}
+
+// x' on the wall plane along [xbar, y]
+template <class R>
+__device__ __forceinline__ Vec3<R> wall_point(const KernelParams& P, const Vec3<R>& xb, const Vec3<R>& y)
+{
+    R sb = (xb.x - R(P.wp[0])) * R(P.wn[0]) + (xb.y - R(P.wp[1])) * R(P.wn[1]) + (xb.z - R(P.wp[2])) * R(P.wn[2]);
+    R sy = (y.x - R(P.wp[0])) * R(P.wn[0]) + (y.y - R(P.wp[1])) * R(P.wn[1]) + (y.z - R(P.wp[2])) * R(P.wn[2]);
+    R den = sb - sy;
+    R t = den > R(0) ? sb / den : R(0);
+    return {xb.x + t * (y.x - xb.x), xb.y + t * (y.y - xb.y), xb.z + t * (y.z - xb.z)};
+}
+
+// Evaluates G_g^{ij} for all groups g < P.G with the whole warp; every lane
+// returns the sums in acc.  s_tet / s_cnt / s_pre: per-warp shared scratch of
+// 32, 32 and 33 ints.
+template <class R, int MG>
+__device__ void entry_warp(const KernelParams& P, int i, int j, R (&acc)[MG], int* s_tet, int* s_cnt, int* s_pre)
+{
+    const int lane = threadIdx.x & 31;
+    const Vec3<R> xi = load_xyz<R>(P, i);
+    Vec3<R> xb = xi;
+    if (P.has_wall) xb = mirror_point<R>(P, xi);
+#pragma unroll
+    for (int g = 0; g < MG; ++g) acc[g] = R(0);
+    const int t0 = P.vt_ptr[j], t1 = P.vt_ptr[j + 1];
+    const R inv4pi = R(1.0 / (4.0 * kPi));
+    for (int base = t0; base < t1; base += 32) {
+        const int nt = min(32, t1 - base);
+        int cnt = 0;
+        if (lane < nt) {
+            int packed = P.vt_idx[base + lane];
+            Vec3<R> cen;
+            R diam, vol;
+            load_tgeo<R>(P, packed >> 2, cen, diam, vol);
+            R lim = R(4) * diam * diam;
+            int nd = dist2<R>(xi, cen) < lim ? 14 : 4;
+            int nr = P.has_wall ? (dist2<R>(xb, cen) < lim ? 14 : 4) : 0;
+            cnt = nd + nr;
+            s_tet[lane] = packed;
+            s_cnt[lane] = nd | (nr << 8);
+        }
+        int pre = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int v = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, pre, 31);
+        s_pre[lane] = pre - cnt;
+        __syncwarp();
+        for (int k = lane; k < total; k += 32) {
+            // locate the tetrahedron: last t with s_pre[t] <= k
+            int lo = 0, hi = nt - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (s_pre[mid] <= k) lo = mid; else hi = mid - 1;
+            }
+            const int t = lo;
+            const int q = k - s_pre[t];
+            const int packed = s_tet[t];
+            const int nd = s_cnt[t] & 0xff, nr = s_cnt[t] >> 8;
+            const int tet = packed >> 2, loc = packed & 3;
+            const bool refl = q >= nd;
+            const int qq = refl ? q - nd : q;
+            const int nq = refl ? nr : nd;
+            const int row = (nq == 14 ? 4 : 0) + qq;
+            const int4 tv = P.tet[tet];
+            const Vec3<R> v0 = load_xyz<R>(P, tv.x), v1 = load_xyz<R>(P, tv.y), v2 = load_xyz<R>(P, tv.z),
+                          v3 = load_xyz<R>(P, tv.w);
+            const R b0 = tet_b<R>(row, 0), b1 = tet_b<R>(row, 1), b2 = tet_b<R>(row, 2), b3 = tet_b<R>(row, 3);
+            Vec3<R> y;
+            y.x = b0 * v0.x + b1 * v1.x + b2 * v2.x + b3 * v3.x;
+            y.y = b0 * v0.y + b1 * v1.y + b2 * v2.y + b3 * v3.y;
+            y.z = b0 * v0.z + b1 * v1.z + b2 * v2.z + b3 * v3.z;
+            const R lam = loc == 0 ? b0 : (loc == 1 ? b1 : (loc == 2 ? b2 : b3));
+            R vol;
+            if constexpr (sizeof(R) == 4) vol = P.tvol32[tet]; else vol = P.tvol64[tet];
+            R r2, tau;
+            if (!refl) {
+                r2 = dist2<R>(xi, y);
+                tau = optical_depth<R>(P, xi, y);
+            } else {
+                Vec3<R> xp = wall_point<R>(P, xb, y);
+                r2 = dist2<R>(xb, y);
+                tau = optical_depth<R>(P, xi, xp) + optical_depth<R>(P, xp, y);
+            }
+            R w = vol * tet_w<R>(row) * lam * kappa_at<R>(P, y.x, y.y, y.z) * inv4pi / r2;
+            if (refl) w *= R(P.R0);
+#pragma unroll
+            for (int g = 0; g < MG; ++g)
+                if (g < P.G) {
+                    R cg = kp_c<R>(P, g);
+                    acc[g] += w * cg * exp_r(-cg * tau);
+                }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int g = 0; g < MG; ++g) {
+        R v = acc[g];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        acc[g] = v;
+    }
+}
+
+}  // namespace rt

@@ -1,0 +1,192 @@
+// rt_internal.h -- internal structures of the radiative-transfer library.
+//
+// Layout conventions (all device arrays, tree order of vertices):
+//   xyz      : float4 [N] (x, y, z, 0) and double [N][3]
+//   tet      : int4 [T] vertex ids in tree order
+//   tgeo     : float4/dbl4 [T] (centroid x, y, z, diameter); tvol [T]
+//   vt_ptr   : int [N+1], vt_idx: int [nnz] packed (tet << 2) | local vertex slot
+//   vectors  : [F][N] frequency-major
+//   far block b, group g : V^T [r][n] at far_v[b] + g*r*n, U^T [r][m] at far_u[b] + g*r*m
+//   dense block b, group g: A^T [n][m] (column-major) at dense_off[b] + g*m*n
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rt.h"
+
+namespace rt {
+
+constexpr int kMaxGroups = 64;
+constexpr int kMaxGauss = 32;
+constexpr double kPi = 3.14159265358979323846;
+
+struct alignas(16) dbl4 {
+    double x, y, z, w;
+};
+inline dbl4 make_dbl4(double x, double y, double z, double w) { return dbl4{x, y, z, w}; }
+
+// Kernel parameters of one instance (passed by value to kernels).
+struct KernelParams {
+    int N;              // vertices
+    int T;              // tetrahedra
+    int kappa_kind;
+    float k0f, ampf;
+    double k0, amp;
+    int has_wall;       // R0 != 0 and a wall is present
+    double wp[3], wn[3];
+    double R0;
+    int G;              // groups
+    double c[kMaxGroups];
+    float cf[kMaxGroups];
+    int ngauss;
+    // Gauss-Legendre nodes mapped to [0,1] (u = (1+t)/2) and half weights
+    float gu32[kMaxGauss], gw32[kMaxGauss];
+    double gu64[kMaxGauss], gw64[kMaxGauss];
+    // device geometry (tree order)
+    const float4* xyz32;
+    const double* xyz64;
+    const int4* tet;
+    const float4* tgeo32;
+    const dbl4* tgeo64;
+    const float* tvol32;
+    const double* tvol64;
+    const int* vt_ptr;
+    const int* vt_idx;
+};
+
+// A rectangular set of entries G_g[i0 + ii][j0 + jj], ii < ni, jj < nj, written
+// to out[base + g*gs + ii*is + jj*js] (float or double, per launch).
+struct EntrySpan {
+    int i0, ni, j0, nj;
+    int64_t base, gs, is, js;
+    int64_t first;   // prefix: index of this span's first entry in the launch
+};
+
+// One far (admissible) block in tree order.
+struct FarBlock {
+    int row0, m, col0, n;
+};
+
+// Host-side plan of one instance.
+struct Plan {
+    int N = 0;
+    int leaf = 64;
+    std::vector<int> perm;      // tree position -> original vertex id
+    std::vector<int> iperm;     // original vertex id -> tree position
+    std::vector<int> leaf_start, leaf_size;   // leaves in tree order
+    std::vector<FarBlock> near_blocks;        // dense leaf blocks
+    std::vector<FarBlock> far_blocks;         // admissible blocks
+};
+
+int plan_build(const double* xyz, int64_t n, int leaf, double eta, Plan& out, std::string& err);
+
+// Operator (one instance).
+struct Operator {
+    int device = 0;
+    int mode = RT_MODE_HMATRIX, prec = RT_PREC_F32, far_prec = RT_PREC_F32;
+    int N = 0, F = 0, G = 0, T = 0;
+    int grey = 0;
+    double aca_eps = 1e-4, eta = 2.0;
+    int leaf = 64, ngauss = 16, rank_max = 512;
+    KernelParams kp{};
+    // frequencies (host copies) and the group of each frequency
+    std::vector<double> nu, w, c, albedo, Q;
+    std::vector<int> fgroup;
+    std::vector<double> gc;     // group scales
+    Plan plan;
+    // device geometry
+    float4* d_xyz32 = nullptr;
+    double* d_xyz64 = nullptr;
+    int4* d_tet = nullptr;
+    float4* d_tgeo32 = nullptr;
+    dbl4* d_tgeo64 = nullptr;
+    float* d_tvol32 = nullptr;
+    double* d_tvol64 = nullptr;
+    int* d_vt_ptr = nullptr;
+    int* d_vt_idx = nullptr;
+    int* d_perm = nullptr;      // tree -> original
+    int* d_iperm = nullptr;     // original -> tree
+    // emitter
+    int n_emit = 0;
+    int4* d_emit = nullptr;     // tree-order vertex ids of each triangle (w unused)
+    double* d_emit_lim = nullptr; // per vertex: sum of (angle / 8 pi) over emitter triangles at the vertex
+    // source (tree order), vector element type = vec64 ? double : float
+    int vec64 = 0;
+    void* d_SE = nullptr;       // [F][N]
+    // dense mode
+    void* d_dense = nullptr;    // [G][N][N] row-major (double or float)
+    // H-matrix mode
+    int n_near = 0, n_far = 0, n_fallback = 0;
+    std::vector<int> rank;      // per far block (final; -1 = stored dense)
+    std::vector<FarBlock> far_blocks, dense_blocks;   // final split
+    float* d_near = nullptr;    // dense blocks' A^T
+    std::vector<int64_t> dense_off;
+    void* d_far = nullptr;      // far U/V (float, bf16 or f16)
+    std::vector<int64_t> far_v_off, far_u_off;
+    // matvec work lists (device)
+    void* d_p1_items = nullptr; int n_p1 = 0;
+    void* d_p2_leaf = nullptr;  int n_p2 = 0;
+    void* d_p2_segs = nullptr;  int n_p2_segs = 0;
+    float* d_w = nullptr;       int64_t w_len = 0;   // phase-1 scratch [sum r][F]
+    float* d_xt = nullptr;      // permuted input scratch [F][N]
+    float* d_yt = nullptr;      // permuted output scratch [F][N]
+    // solver scratch
+    void* d_J = nullptr; void* d_S = nullptr; void* d_Y = nullptr;
+    double* d_T = nullptr;
+    double* d_part = nullptr; int n_part = 0;
+    double* d_res = nullptr;
+    double* h_res = nullptr;    // pinned
+    // frequency tables on device
+    double* d_fq = nullptr;     // [F][4]: nu, w*c*(1-a), a, group
+    int* d_fq_group = nullptr;  // [F] group of each frequency
+    // stats
+    rt_info info{};
+    std::vector<void*> allocations;
+};
+
+// ---- kernels / drivers implemented in the .cu files -----------------------
+int assemble_setup_constants(Operator& op, std::string& err);
+void gauss_legendre_nodes(int n, std::vector<double>& t, std::vector<double>& w);
+int assemble_dense(Operator& op, cudaStream_t s, std::string& err);
+int assemble_source(Operator& op, cudaStream_t s, std::string& err);
+int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err);
+int eval_entries(Operator& op, int group, int64_t count, const int32_t* rows, const int32_t* cols, double* out,
+                 cudaStream_t s, std::string& err);
+int hmatvec_prepare(Operator& op, std::string& err);
+// X, Y in tree order, [F][N], element type float (H-matrix / dense F32) or double (dense F64)
+int apply_tree(Operator& op, const void* X, void* Y, cudaStream_t s, std::string& err);
+int permute_vectors(Operator& op, const void* in, void* out, int to_tree, int is64, int rows, cudaStream_t s);
+int solve_fixed_point(Operator& op, const rt_solve_opts& o, void* J, double* T, rt_solve_stats& st,
+                      cudaStream_t s, std::string& err);
+
+// error helpers
+#define RT_CUDA_TRY(expr)                                                            \
+    do {                                                                             \
+        cudaError_t e_ = (expr);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            err = std::string(#expr) + ": " + cudaGetErrorString(e_);               \
+            return RT_ECUDA;                                                         \
+        }                                                                            \
+    } while (0)
+
+template <class T>
+int dev_alloc(Operator& op, T** p, size_t count, std::string& err)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        err = std::string("cudaMalloc(") + std::to_string(count * sizeof(T)) + " bytes): " + cudaGetErrorString(e);
+        *p = nullptr;
+        return RT_ENOMEM;
+    }
+    op.allocations.push_back((void*)*p);
+    op.info.device_bytes += (int64_t)(count * sizeof(T));
+    return RT_OK;
+}
+
+}  // namespace rt

@@ -1,0 +1,271 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+Element-by-element on small meshes (several leaves, ragged leaf sizes), and on
+sampled rows at the 32^3 benchmark size.  Tolerances:
+  * FP64 dense path: 1e-11 relative (both sides FP64; only rounding order and
+    the sin(2 pi x) vs sinpi(2x) evaluation differ);
+  * FP32 entries: 2e-5 relative to the entry plus 1e-6 of the row's largest
+    entry (FP32 optical depth over 16 nodes, FP32 exp, ~200-term sums);
+  * H-matrix (ACA eps = 1e-4) apply and solve: relative L2 error 1e-4 class
+    (each test states its bound).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2306_05789_gb300 as rt
+import workloads as W
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2306_05789_gb300 import build
+    build.build()
+    O.build()
+
+
+def dense_hp(prec=rt.RT_PREC_F64):
+    return rt.hparams(mode=rt.RT_MODE_DENSE, prec=prec)
+
+
+def entries(op, group, rows, cols):
+    r = torch.tensor(np.asarray(rows, dtype=np.int32), device=DEV)
+    c = torch.tensor(np.asarray(cols, dtype=np.int32), device=DEV)
+    out = torch.zeros(r.numel(), dtype=torch.float64, device=DEV)
+    op.eval_entries(group, r, c, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+# ---------------------------------------------------------------------------
+# entries and source
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [rt.RT_PREC_F64, rt.RT_PREC_F32])
+def test_entries_match_oracle_rows(prec):
+    p = W.cube_problem(7, W.sinprod_kappa(0.5), W.midpoint_freqs(3, albedo=0.3), R0=0.5)
+    op = rt.rt_build_operator(p, dense_hp(prec))
+    rows = np.array([0, 3, 48, 171, 342], dtype=np.int32)
+    R = O.G_rows(p, rows)                      # [r, G, N]
+    c, _ = O.groups_of(p.freqs)
+    for g in range(len(c)):
+        ii = np.repeat(rows, p.N)
+        jj = np.tile(np.arange(p.N), len(rows))
+        got = entries(op, g, ii, jj).reshape(len(rows), p.N)
+        ref = R[:, g, :]
+        if prec == rt.RT_PREC_F64:
+            np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-16)
+        else:
+            tol = 2e-5 * np.abs(ref) + 1e-6 * np.abs(ref).max(axis=1, keepdims=True)
+            assert (np.abs(got - ref) <= tol).all(), np.abs(got - ref).max()
+    op.free()
+
+
+@pytest.mark.parametrize("prec", [rt.RT_PREC_F64, rt.RT_PREC_F32])
+def test_source_matches_oracle(prec):
+    p = W.cube_problem(7, W.sinprod_kappa(0.5), W.midpoint_freqs(3, albedo=0.3), R0=0.5)
+    op = rt.rt_build_operator(p, dense_hp(prec))
+    dt = torch.float64 if prec == rt.RT_PREC_F64 else torch.float32
+    SE = torch.zeros(p.freqs.F, p.N, dtype=dt, device=DEV)
+    op.source(SE)
+    torch.cuda.synchronize()
+    ref = O.DenseOperator(p).SE
+    got = SE.double().cpu().numpy()
+    if prec == rt.RT_PREC_F64:
+        np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-16)
+    else:
+        np.testing.assert_allclose(got, ref, rtol=2e-5, atol=1e-6 * np.abs(ref).max())
+    op.free()
+
+
+def test_source_grey_with_emitter_and_wall_vertices():
+    """Vertices on the emitter and on the wall line take the limit values."""
+    p = W.cube_problem(6, W.Kappa(W.KAPPA_CONST, 0.7, 0.0), W.grey_freqs(), R0=0.5, grey=True)
+    op = rt.rt_build_operator(p, dense_hp())
+    SE = torch.zeros(1, p.N, dtype=torch.float64, device=DEV)
+    op.source(SE)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(SE.cpu().numpy(), O.DenseOperator(p).SE, rtol=1e-11, atol=1e-16)
+    op.free()
+
+
+# ---------------------------------------------------------------------------
+# the plain method: dense FP64 operator, grey fixed point (12^3, kappa = 1)
+# ---------------------------------------------------------------------------
+def test_dense_fp64_apply_matches_oracle():
+    p = W.cube_problem(8, W.sinprod_kappa(0.5), W.midpoint_freqs(2, albedo=0.3), R0=0.5)
+    op = rt.rt_build_operator(p, dense_hp())
+    X = W.rand_vectors((2, p.N), seed=0)
+    Xd = torch.tensor(X, device=DEV)
+    Y = torch.zeros_like(Xd)
+    op.apply(Xd, Y)
+    torch.cuda.synchronize()
+    ref = O.DenseOperator(p).apply(X)
+    np.testing.assert_allclose(Y.cpu().numpy(), ref, rtol=1e-11)
+    op.free()
+
+
+def test_plain_grey_12_fixed_point_matches_oracle():
+    """12^3 cube, kappa = 1, grey, emitter T = 1 on x = 0, wall z = 0 with R0 = 0.5,
+    dense FP64, fixed point to a 1e-10 residual."""
+    p = W.plain_grey_12()
+    op = rt.rt_build_operator(p, dense_hp())
+    J = torch.zeros(1, p.N, dtype=torch.float64, device=DEV)
+    T = torch.zeros(p.N, dtype=torch.float64, device=DEV)
+    st = op.solve_fixed_point(J, T, tol=1e-10, max_iter=200, check_every=1)
+    ora = O.DenseOperator(p)
+    ref = O.fixed_point(p, ora, tol=1e-10)
+    assert st["converged"] == 1
+    assert st["iters"] == ref["iters"]
+    np.testing.assert_allclose(J.cpu().numpy(), ref["J"], rtol=1e-9)
+    np.testing.assert_allclose(T.cpu().numpy(), ref["T"], rtol=1e-9)
+    # and the limit is the direct linear solve (I - G) J = Sbar^E
+    Jd = np.linalg.solve(np.eye(p.N) - ora.G[0], ora.SE[0])
+    assert rel_l2(J.cpu().numpy()[0], Jd) < 1e-9
+    op.free()
+
+
+def test_multifrequency_dense_fixed_point_matches_oracle():
+    p = W.cube_problem(6, W.sinprod_kappa(0.5), W.midpoint_freqs(4, albedo=0.3), R0=0.5)
+    op = rt.rt_build_operator(p, dense_hp())
+    J = torch.zeros(4, p.N, dtype=torch.float64, device=DEV)
+    T = torch.zeros(p.N, dtype=torch.float64, device=DEV)
+    st = op.solve_fixed_point(J, T, tol=1e-12, max_iter=300, check_every=5)
+    ref = O.fixed_point(p, O.DenseOperator(p), tol=1e-12)
+    assert st["converged"] == 1
+    np.testing.assert_allclose(T.cpu().numpy(), ref["T"], rtol=1e-10)
+    np.testing.assert_allclose(J.cpu().numpy(), ref["J"], rtol=1e-9, atol=1e-14)
+    op.free()
+
+
+def test_monotone_iterates_on_gpu():
+    """T^k increasing from T^0 = 0 (Section 1.3): checked on the GPU iterates one step at a time."""
+    p = W.cube_problem(6, W.sinprod_kappa(0.5), W.midpoint_freqs(3, albedo=0.3), R0=0.5)
+    op = rt.rt_build_operator(p, dense_hp())
+    J = torch.zeros(3, p.N, dtype=torch.float64, device=DEV)
+    T = torch.zeros(p.N, dtype=torch.float64, device=DEV)
+    prev = np.zeros(p.N)
+    for k in range(1, 8):
+        st = op.solve_fixed_point(J, T, tol=0.0, max_iter=k, check_every=k, raise_on_noconv=False)
+        cur = T.cpu().numpy()
+        assert st["iters"] == k
+        assert (cur > prev).all()
+        prev = cur
+    op.free()
+
+
+# ---------------------------------------------------------------------------
+# H-matrix (FP32 near field, ACA far field)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,leaf,F", [(12, 64, 4), (10, 32, 2)])
+def test_hmatrix_apply_matches_dense_oracle(n, leaf, F):
+    p = W.cube_problem(n, W.sinprod_kappa(0.5), W.midpoint_freqs(F, albedo=0.3), R0=0.5)
+    op = rt.rt_build_operator(p, rt.hparams(leaf=leaf))
+    info = op.info()
+    assert info["n_far"] > 0
+    for kind in ("uniform", "normal"):
+        X = W.rand_vectors((F, p.N), seed=1, kind=kind)
+        Xd = torch.tensor(X, dtype=torch.float32, device=DEV)
+        Y = torch.zeros_like(Xd)
+        op.apply(Xd, Y)
+        torch.cuda.synchronize()
+        ref = O.DenseOperator(p).apply(X)
+        err = rel_l2(Y.cpu().numpy(), ref)
+        assert err < 3e-4, (kind, err, info)
+    op.free()
+
+
+def test_hmatrix_fixed_point_matches_dense_oracle():
+    p = W.cube_problem(12, W.sinprod_kappa(0.5), W.midpoint_freqs(4, albedo=0.3), R0=0.5)
+    op = rt.rt_build_operator(p, rt.hparams())
+    J = torch.zeros(4, p.N, dtype=torch.float32, device=DEV)
+    T = torch.zeros(p.N, dtype=torch.float64, device=DEV)
+    st = op.solve_fixed_point(J, T, tol=1e-6, max_iter=200, check_every=4)
+    ref = O.fixed_point(p, O.DenseOperator(p), tol=1e-10)
+    assert st["converged"] == 1
+    assert rel_l2(T.cpu().numpy(), ref["T"]) < 1e-4
+    assert rel_l2(J.cpu().numpy(), ref["J"]) < 3e-4
+    op.free()
+
+
+def test_hmatrix_handles_ragged_and_tiny_meshes():
+    for n, leaf in ((5, 8), (7, 16), (9, 50)):
+        p = W.cube_problem(n, W.sinprod_kappa(0.3), W.midpoint_freqs(1, albedo=0.0), R0=0.9)
+        op = rt.rt_build_operator(p, rt.hparams(leaf=leaf))
+        X = W.rand_vectors((1, p.N), seed=n)
+        Xd = torch.tensor(X, dtype=torch.float32, device=DEV)
+        Y = torch.zeros_like(Xd)
+        op.apply(Xd, Y)
+        torch.cuda.synchronize()
+        assert rel_l2(Y.cpu().numpy(), O.DenseOperator(p).apply(X)) < 3e-4
+        op.free()
+
+
+def test_invalid_inputs_are_rejected():
+    p = W.cube_problem(5, W.sinprod_kappa(0.5), W.midpoint_freqs(2), R0=0.5)
+    bad = W.Problem(p.xyz, p.tet.copy(), p.emit_tri, p.kappa, p.wall, p.freqs)
+    bad.tet[3, 1] = p.N + 5
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_build_operator(bad, rt.hparams())
+    assert e.value.code == rt.RT_EINVAL
+    with pytest.raises(rt.RtError):
+        rt.rt_build_operator(p, rt.hparams(aca_eps=0.0))
+    with pytest.raises(rt.RtError):
+        rt.rt_build_operator(p, rt.hparams(mode=rt.RT_MODE_DENSE, prec=rt.RT_PREC_BF16))
+
+
+# ---------------------------------------------------------------------------
+# benchmark size: 32^3, 16 frequencies (sampled rows)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def op32():
+    p = W.multifreq_32()
+    op = rt.rt_build_operator(p, rt.hparams())
+    yield p, op
+    op.free()
+
+
+def test_32cube_sampled_rows_of_the_apply(op32):
+    p, op = op32
+    rows = W.sample_rows(p.N, 12, seed=0)
+    X = W.rand_vectors((p.freqs.F, p.N), seed=0)
+    Xd = torch.tensor(X, dtype=torch.float32, device=DEV)
+    Y = torch.zeros_like(Xd)
+    op.apply(Xd, Y)
+    torch.cuda.synchronize()
+    R = O.G_rows(p, rows)          # [r, G, N]
+    _, gidx = O.groups_of(p.freqs)
+    ref = np.stack([R[:, gidx[f], :] @ X[f] for f in range(p.freqs.F)])   # [F, r]
+    got = Y.cpu().numpy()[:, rows]
+    assert rel_l2(got, ref) < 3e-4
+    info = op.info()
+    assert info["compression"] > 0.5
+
+
+def test_32cube_solve_one_step_residual(op32):
+    p, op = op32
+    J = torch.zeros(p.freqs.F, p.N, dtype=torch.float32, device=DEV)
+    T = torch.zeros(p.N, dtype=torch.float64, device=DEV)
+    st = op.solve_fixed_point(J, T, tol=1e-6, max_iter=200, check_every=4)
+    assert st["converged"] == 1
+    rows = W.sample_rows(p.N, 8, seed=1)
+    Jh = J.double().cpu().numpy()
+    Th = T.cpu().numpy()
+    res = O.one_step_residual(p, rows, Jh, Th)
+    assert np.linalg.norm(res) / np.linalg.norm(Jh[:, rows]) < 3e-4
+    # the temperature solves the Planck balance for the returned J
+    np.testing.assert_allclose(O.temperature_newton(Jh[:, rows], p.freqs), Th[rows], rtol=1e-5)
