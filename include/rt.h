@@ -58,6 +58,10 @@ extern "C" {
 #define RT_PREC_BF16 2
 #define RT_PREC_F16 3
 
+/* admissibility readings of max(R1,R2) < eta |x1 - x2| (Section 2.1) */
+#define RT_ADM_GAP 0    /* |x1 - x2| = distance between the clusters' bounding spheres (|c1-c2| - R1 - R2) */
+#define RT_ADM_CENTER 1 /* |x1 - x2| = distance between the cluster centroids (literal) */
+
 /* Tetrahedral P1 mesh of the domain (Section 2).  xyz: [n_vert][3] doubles;
  * tet: [n_tet][4] vertex ids (0-based). */
 typedef struct {
@@ -122,6 +126,7 @@ typedef struct {
     double eta;      /* admissibility max(R1,R2) < eta |c1 - c2| (e.g. 2) */
     int gauss_pts;   /* Gauss-Legendre points per line integral (1..32, e.g. 16) */
     int rank_max;    /* ACA rank limit before a block is stored dense (0 = 512) */
+    int adm;         /* RT_ADM_GAP (default) or RT_ADM_CENTER */
 } rt_hparams;
 
 typedef struct rt_operator rt_operator;
@@ -200,13 +205,14 @@ const char* rt_last_error(void);
 /* ---- host-only planning (no GPU needed) --------------------------------
  * Cluster tree by recursive bisection at the median along the longest box
  * axis down to `leaf` points, and the block tree with the admissibility rule
- * max(R_t, R_s) < eta |c_t - c_s| of Section 2.1 (R = max distance from the
- * centroid).  perm (may be NULL): [n] tree order -> vertex id.  blocks (may
+ * of Section 2.1, max(R_t, R_s) < eta d(t, s) with R = max distance from the
+ * centroid and d = |c_t - c_s| - R_t - R_s (adm = RT_ADM_GAP) or
+ * d = |c_t - c_s| (adm = RT_ADM_CENTER).  perm (may be NULL): [n] tree order -> vertex id.  blocks (may
  * be NULL): [cap][5] rows (row0, m, col0, n, kind: 0 dense leaf, 1
  * admissible) in tree order.  counts: [0] = leaves, [1] = dense blocks,
  * [2] = admissible blocks. */
-int rt_plan(const double* xyz, int64_t n, int leaf, double eta, int32_t* perm, int32_t* blocks, int64_t cap,
-            int64_t* counts);
+int rt_plan(const double* xyz, int64_t n, int leaf, double eta, int adm, int32_t* perm, int32_t* blocks,
+            int64_t cap, int64_t* counts);
 
 #ifdef __cplusplus
 }

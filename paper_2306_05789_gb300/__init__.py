@@ -26,6 +26,7 @@ RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOCONV, RT_ETIMEOUT = 0, -1, -2, -3, 
 RT_KAPPA_CONST, RT_KAPPA_SINPROD = 0, 1
 RT_MODE_DENSE, RT_MODE_HMATRIX = 0, 1
 RT_PREC_F64, RT_PREC_F32, RT_PREC_BF16, RT_PREC_F16 = 0, 1, 2, 3
+RT_ADM_GAP, RT_ADM_CENTER = 0, 1
 
 _c_i64 = ctypes.c_int64
 _c_int = ctypes.c_int
@@ -56,7 +57,7 @@ class RtProblem(ctypes.Structure):
 
 class RtHparams(ctypes.Structure):
     _fields_ = [("mode", _c_int), ("prec", _c_int), ("far_prec", _c_int), ("aca_eps", _c_dbl), ("leaf", _c_int),
-                ("eta", _c_dbl), ("gauss_pts", _c_int), ("rank_max", _c_int)]
+                ("eta", _c_dbl), ("gauss_pts", _c_int), ("rank_max", _c_int), ("adm", _c_int)]
 
 
 class RtInfo(ctypes.Structure):
@@ -109,7 +110,7 @@ def lib():
     L.rt_free.argtypes = [_P]
     L.rt_free.restype = None
     L.rt_last_error.restype = ctypes.c_char_p
-    L.rt_plan.argtypes = [_P, _c_i64, _c_int, _c_dbl, _P, _P, _c_i64, _P]
+    L.rt_plan.argtypes = [_P, _c_i64, _c_int, _c_dbl, _c_int, _P, _P, _c_i64, _P]
     _lib = L
     return L
 
@@ -139,10 +140,10 @@ def _stream_ptr(stream):
 
 
 def hparams(mode=RT_MODE_HMATRIX, prec=None, far_prec=RT_PREC_F32, aca_eps=1e-4, leaf=64, eta=2.0, gauss_pts=16,
-            rank_max=0) -> RtHparams:
+            rank_max=0, adm=RT_ADM_GAP) -> RtHparams:
     if prec is None:
         prec = RT_PREC_F32
-    return RtHparams(mode, prec, far_prec, aca_eps, leaf, eta, gauss_pts, rank_max)
+    return RtHparams(mode, prec, far_prec, aca_eps, leaf, eta, gauss_pts, rank_max, adm)
 
 
 class _ProblemArgs:
@@ -242,14 +243,15 @@ def rt_build_operator(prob, hp: RtHparams, stream=None) -> Operator:
     return Operator(out, args.xyz.shape[0], args.nu.shape[0], vec64)
 
 
-def rt_plan(xyz, leaf=64, eta=2.0):
+def rt_plan(xyz, leaf=64, eta=2.0, adm=RT_ADM_GAP):
     """Host-only cluster/block tree: (perm [N], blocks [nb,5], counts (leaves, dense, admissible))."""
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
     n = xyz.shape[0]
     counts = np.zeros(3, dtype=np.int64)
-    _check(lib().rt_plan(_ptr(xyz), n, int(leaf), float(eta), None, None, 0, _ptr(counts)))
+    _check(lib().rt_plan(_ptr(xyz), n, int(leaf), float(eta), int(adm), None, None, 0, _ptr(counts)))
     perm = np.zeros(n, dtype=np.int32)
     nb = int(counts[1] + counts[2])
     blocks = np.zeros((max(nb, 1), 5), dtype=np.int32)
-    _check(lib().rt_plan(_ptr(xyz), n, int(leaf), float(eta), _ptr(perm), _ptr(blocks), nb, _ptr(counts)))
+    _check(lib().rt_plan(_ptr(xyz), n, int(leaf), float(eta), int(adm), _ptr(perm), _ptr(blocks), nb,
+                         _ptr(counts)))
     return perm, blocks[:nb], tuple(int(c) for c in counts)

@@ -723,7 +723,10 @@ __global__ void aca_finish(AcaDev D, const AcaActive* act, int na)
             s += 2.0 * cross + uu * vv;
             if (s < 0.0) s = 0.0;
             D.norm2[(int64_t)b * D.G + g] = s;
-            const bool done = sqrt(uu * vv) <= D.eps * sqrt(s);
+            // a group that skipped this shared pivot (1/delta = 0) has learned nothing
+            // from the term and is not declared converged by it
+            const bool skipped = D.inv[(int64_t)b * D.G + g] == 0.0f;
+            const bool done = !skipped && sqrt(uu * vv) <= D.eps * sqrt(s);
             all_done = all_done && done;
             D.wscale[(int64_t)b * D.G + g] = s > 0.0 ? (float)(1.0 / sqrt(s)) : 1.0f;
         }

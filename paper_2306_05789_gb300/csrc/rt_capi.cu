@@ -28,6 +28,8 @@ void release(rt::Operator& op)
     for (void* p : op.allocations)
         if (p) cudaFree(p);
     op.allocations.clear();
+    if (op.cap_stream) cudaStreamDestroy(op.cap_stream);
+    op.cap_stream = nullptr;
 }
 
 double planck_host(double nu, double T)
@@ -83,6 +85,7 @@ int validate(const rt_problem* P, const rt_hparams* H)
         if (H->leaf < 1) return fail(RT_EINVAL, "leaf must be >= 1");
         if (!(H->eta > 0.0)) return fail(RT_EINVAL, "eta must be > 0");
         if (H->rank_max < 0 || H->rank_max > 8192) return fail(RT_EINVAL, "rank_max must be in [0, 8192]");
+        if (H->adm != RT_ADM_GAP && H->adm != RT_ADM_CENTER) return fail(RT_EINVAL, "adm must be RT_ADM_GAP or RT_ADM_CENTER");
     }
     if (H->gauss_pts < 1 || H->gauss_pts > rt::kMaxGauss) return fail(RT_EINVAL, "gauss_pts must be in [1, 32]");
     if (M.n_vert * (int64_t)M.n_vert * Fq.F > ((int64_t)1 << 40) && H->mode == RT_MODE_DENSE)
@@ -119,6 +122,7 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
     op.aca_eps = H->aca_eps;
     op.leaf = H->leaf;
     op.eta = H->eta;
+    op.adm = H->adm;
     op.ngauss = H->gauss_pts;
     op.rank_max = H->rank_max > 0 ? H->rank_max : 512;
     op.grey = P->grey ? 1 : 0;
@@ -153,7 +157,7 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
     if (op.mode == RT_MODE_HMATRIX) {
-        if ((rc = plan_build(P->mesh.xyz, N, op.leaf, op.eta, op.plan, err))) return rc;
+        if ((rc = plan_build(P->mesh.xyz, N, op.leaf, op.eta, op.adm, op.plan, err))) return rc;
     } else {
         op.plan = Plan();
         op.plan.N = (int)N;
@@ -430,15 +434,15 @@ void rt_free(rt_operator* h)
 
 const char* rt_last_error(void) { return g_err.c_str(); }
 
-int rt_plan(const double* xyz, int64_t n, int leaf, double eta, int32_t* perm, int32_t* blocks, int64_t cap,
-            int64_t* counts)
+int rt_plan(const double* xyz, int64_t n, int leaf, double eta, int adm, int32_t* perm, int32_t* blocks,
+            int64_t cap, int64_t* counts)
 {
     if (!xyz || !counts) return fail(RT_EINVAL, "null argument");
     rt::Plan P;
     std::string err;
     int rc;
     try {
-        rc = rt::plan_build(xyz, n, leaf, eta, P, err);
+        rc = rt::plan_build(xyz, n, leaf, eta, adm, P, err);
     } catch (...) {
         rc = RT_ENOMEM;
         err = "host allocation failed";

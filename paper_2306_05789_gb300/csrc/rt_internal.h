@@ -82,7 +82,7 @@ struct Plan {
     std::vector<FarBlock> far_blocks;         // admissible blocks
 };
 
-int plan_build(const double* xyz, int64_t n, int leaf, double eta, Plan& out, std::string& err);
+int plan_build(const double* xyz, int64_t n, int leaf, double eta, int adm, Plan& out, std::string& err);
 
 // Operator (one instance).
 struct Operator {
@@ -91,6 +91,7 @@ struct Operator {
     int N = 0, F = 0, G = 0, T = 0;
     int grey = 0;
     double aca_eps = 1e-4, eta = 2.0;
+    int adm = RT_ADM_GAP;
     int leaf = 64, ngauss = 16, rank_max = 512;
     KernelParams kp{};
     // frequencies (host copies) and the group of each frequency
@@ -140,6 +141,7 @@ struct Operator {
     double* d_part = nullptr; int n_part = 0;
     double* d_res = nullptr;
     double* h_res = nullptr;    // pinned
+    cudaStream_t cap_stream = nullptr;   // library-owned stream used for graph capture
     // frequency tables on device
     double* d_fq = nullptr;     // [F][4]: nu, w*c*(1-a), a, group
     int* d_fq_group = nullptr;  // [F] group of each frequency

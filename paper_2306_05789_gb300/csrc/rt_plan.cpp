@@ -6,9 +6,12 @@
 // and radius (largest distance from the centroid).
 //
 // Block tree: recursion from (root, root); a pair (t, s) is admissible when
-// max(R_t, R_s) < eta |c_t - c_s| (the paper's geometric criterion, taken
-// literally), and then becomes one far block compressed by ACA; otherwise the
-// non-leaf side(s) are split; two leaves give a dense block.
+// max(R_t, R_s) < eta d(t, s) (the paper's geometric criterion) and then
+// becomes one far block compressed by ACA; otherwise the non-leaf side(s) are
+// split; two leaves give a dense block.  d(t, s) is the distance between the
+// clusters' bounding spheres, |c_t - c_s| - R_t - R_s (RT_ADM_GAP), or the
+// distance between the centroids, |c_t - c_s| (RT_ADM_CENTER, the literal
+// reading, under which touching clusters are admissible).
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -80,15 +83,17 @@ struct Builder {
     }
 };
 
-void block_recursion(const std::vector<Cluster>& cl, double eta, int t, int s, std::vector<FarBlock>& nearb,
-                     std::vector<FarBlock>& farb)
+void block_recursion(const std::vector<Cluster>& cl, double eta, int adm, int t, int s,
+                     std::vector<FarBlock>& nearb, std::vector<FarBlock>& farb)
 {
     const Cluster& T = cl[t];
     const Cluster& S = cl[s];
     double d2 = 0.0;
     for (int k = 0; k < 3; ++k) d2 += (T.c[k] - S.c[k]) * (T.c[k] - S.c[k]);
-    bool adm = std::max(T.R, S.R) < eta * std::sqrt(d2);
-    if (adm) {
+    double d = std::sqrt(d2);
+    if (adm == RT_ADM_GAP) d -= T.R + S.R;
+    const bool admissible = d > 0.0 && std::max(T.R, S.R) < eta * d;
+    if (admissible) {
         farb.push_back({T.start, T.size, S.start, S.size});
         return;
     }
@@ -98,22 +103,22 @@ void block_recursion(const std::vector<Cluster>& cl, double eta, int t, int s, s
         return;
     }
     if (tl) {
-        block_recursion(cl, eta, t, S.left, nearb, farb);
-        block_recursion(cl, eta, t, S.right, nearb, farb);
+        block_recursion(cl, eta, adm, t, S.left, nearb, farb);
+        block_recursion(cl, eta, adm, t, S.right, nearb, farb);
     } else if (sl) {
-        block_recursion(cl, eta, T.left, s, nearb, farb);
-        block_recursion(cl, eta, T.right, s, nearb, farb);
+        block_recursion(cl, eta, adm, T.left, s, nearb, farb);
+        block_recursion(cl, eta, adm, T.right, s, nearb, farb);
     } else {
-        block_recursion(cl, eta, T.left, S.left, nearb, farb);
-        block_recursion(cl, eta, T.left, S.right, nearb, farb);
-        block_recursion(cl, eta, T.right, S.left, nearb, farb);
-        block_recursion(cl, eta, T.right, S.right, nearb, farb);
+        block_recursion(cl, eta, adm, T.left, S.left, nearb, farb);
+        block_recursion(cl, eta, adm, T.left, S.right, nearb, farb);
+        block_recursion(cl, eta, adm, T.right, S.left, nearb, farb);
+        block_recursion(cl, eta, adm, T.right, S.right, nearb, farb);
     }
 }
 
 }  // namespace
 
-int plan_build(const double* xyz, int64_t n, int leaf, double eta, Plan& out, std::string& err)
+int plan_build(const double* xyz, int64_t n, int leaf, double eta, int adm, Plan& out, std::string& err)
 {
     if (n <= 0 || n > (int64_t)1 << 30) {
         err = "plan: vertex count out of range";
@@ -121,6 +126,10 @@ int plan_build(const double* xyz, int64_t n, int leaf, double eta, Plan& out, st
     }
     if (leaf < 1) {
         err = "plan: leaf size must be >= 1";
+        return RT_EINVAL;
+    }
+    if (adm != RT_ADM_GAP && adm != RT_ADM_CENTER) {
+        err = "plan: unknown admissibility reading";
         return RT_EINVAL;
     }
     if (!(eta > 0.0)) {
@@ -146,7 +155,7 @@ int plan_build(const double* xyz, int64_t n, int leaf, double eta, Plan& out, st
             out.leaf_size.push_back(C.size);
         }
     // leaves are produced in tree order by the depth-first build
-    block_recursion(B.cl, eta, 0, 0, out.near_blocks, out.far_blocks);
+    block_recursion(B.cl, eta, adm, 0, 0, out.near_blocks, out.far_blocks);
     auto key = [](const FarBlock& a, const FarBlock& b) {
         if (a.row0 != b.row0) return a.row0 < b.row0;
         return a.col0 < b.col0;

@@ -258,11 +258,14 @@ static int solve_impl(Operator& op, const rt_solve_opts& o, void* J_out, double*
                 if (graph) cudaGraphDestroy(graph);
                 gexec = nullptr;
                 graph = nullptr;
-                RT_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                // capture on a library-owned stream (the caller's stream may be the
+                // legacy default stream, which cannot be captured); replay on `s`
+                if (!op.cap_stream) RT_CUDA_TRY(cudaStreamCreateWithFlags(&op.cap_stream, cudaStreamNonBlocking));
+                RT_CUDA_TRY(cudaStreamBeginCapture(op.cap_stream, cudaStreamCaptureModeThreadLocal));
                 int crc = RT_OK;
                 for (int k = 0; k < todo && crc == RT_OK; ++k)
-                    crc = one_iteration<V>(op, s, op.grey, d_ctr, d_ctr + 1, cap, err);
-                cudaError_t ce = cudaStreamEndCapture(s, &graph);
+                    crc = one_iteration<V>(op, op.cap_stream, op.grey, d_ctr, d_ctr + 1, cap, err);
+                cudaError_t ce = cudaStreamEndCapture(op.cap_stream, &graph);
                 if (crc) return crc;
                 if (ce != cudaSuccess) {
                     err = std::string("graph capture: ") + cudaGetErrorString(ce);

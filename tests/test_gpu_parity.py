@@ -185,7 +185,7 @@ def test_hmatrix_apply_matches_dense_oracle(n, leaf, F):
         torch.cuda.synchronize()
         ref = O.DenseOperator(p).apply(X)
         err = rel_l2(Y.cpu().numpy(), ref)
-        assert err < 3e-4, (kind, err, info)
+        assert err < 1e-4, (kind, err, info)
     op.free()
 
 
@@ -197,8 +197,8 @@ def test_hmatrix_fixed_point_matches_dense_oracle():
     st = op.solve_fixed_point(J, T, tol=1e-6, max_iter=200, check_every=4)
     ref = O.fixed_point(p, O.DenseOperator(p), tol=1e-10)
     assert st["converged"] == 1
-    assert rel_l2(T.cpu().numpy(), ref["T"]) < 1e-4
-    assert rel_l2(J.cpu().numpy(), ref["J"]) < 3e-4
+    assert rel_l2(T.cpu().numpy(), ref["T"]) < 1e-5
+    assert rel_l2(J.cpu().numpy(), ref["J"]) < 1e-4
     op.free()
 
 
@@ -211,8 +211,24 @@ def test_hmatrix_handles_ragged_and_tiny_meshes():
         Y = torch.zeros_like(Xd)
         op.apply(Xd, Y)
         torch.cuda.synchronize()
-        assert rel_l2(Y.cpu().numpy(), O.DenseOperator(p).apply(X)) < 3e-4
+        assert rel_l2(Y.cpu().numpy(), O.DenseOperator(p).apply(X)) < 1e-4
         op.free()
+
+
+def test_literal_center_admissibility_is_kept_as_an_option():
+    """The literal centre-distance reading admits touching clusters; it still builds and
+    applies (with a larger ACA error, reported in the design doc)."""
+    p = W.cube_problem(8, W.sinprod_kappa(0.5), W.midpoint_freqs(2, albedo=0.3), R0=0.5)
+    op = rt.rt_build_operator(p, rt.hparams(leaf=32, adm=rt.RT_ADM_CENTER))
+    info = op.info()
+    X = W.rand_vectors((2, p.N), seed=3)
+    Xd = torch.tensor(X, dtype=torch.float32, device=DEV)
+    Y = torch.zeros_like(Xd)
+    op.apply(Xd, Y)
+    torch.cuda.synchronize()
+    assert info["n_far"] + info["n_dense_fallback"] > 0
+    assert rel_l2(Y.cpu().numpy(), O.DenseOperator(p).apply(X)) < 3e-2
+    op.free()
 
 
 def test_invalid_inputs_are_rejected():
@@ -251,9 +267,9 @@ def test_32cube_sampled_rows_of_the_apply(op32):
     _, gidx = O.groups_of(p.freqs)
     ref = np.stack([R[:, gidx[f], :] @ X[f] for f in range(p.freqs.F)])   # [F, r]
     got = Y.cpu().numpy()[:, rows]
-    assert rel_l2(got, ref) < 3e-4
+    assert rel_l2(got, ref) < 1e-4
     info = op.info()
-    assert info["compression"] > 0.5
+    assert info["compression"] > 0.7
 
 
 def test_32cube_solve_one_step_residual(op32):
@@ -266,6 +282,6 @@ def test_32cube_solve_one_step_residual(op32):
     Jh = J.double().cpu().numpy()
     Th = T.cpu().numpy()
     res = O.one_step_residual(p, rows, Jh, Th)
-    assert np.linalg.norm(res) / np.linalg.norm(Jh[:, rows]) < 3e-4
+    assert np.linalg.norm(res) / np.linalg.norm(Jh[:, rows]) < 1e-4
     # the temperature solves the Planck balance for the returned J
-    np.testing.assert_allclose(O.temperature_newton(Jh[:, rows], p.freqs), Th[rows], rtol=1e-5)
+    np.testing.assert_allclose(O.temperature_newton(Jh[:, rows], p.freqs), Th[rows], rtol=1e-9)
