@@ -178,6 +178,27 @@ int rt_operator_info(const rt_operator* op, rt_info* info);
  * operator, float otherwise.  X and Y must not overlap. */
 int rt_apply(rt_operator* op, const void* X, void* Y, void* stream);
 
+/* Y = Gbar X exactly as rt_apply computes it, for callers that must not
+ * allocate device memory while they run -- for example code that is being
+ * recorded into another component's CUDA graph, where an allocation would
+ * break or serialise the capture, or a host loop with a fixed time budget in
+ * an application whose device memory is handed out by its own allocator.
+ * (The paper has no counterpart: this is a deployment convenience.)
+ * The scratch rt_apply keeps in the operator -- X and Y in the internal vertex
+ * order and one FP32 value per (far-block rank term, frequency) -- is taken
+ * from a static 8 MiB device array instead (2 * 4 F N bytes + 4 F sum(rank)
+ * bytes, each rounded up to 256, must fit; larger operators get RT_EINVAL).
+ * The array exists once per GPU that loads the library and stays allocated
+ * until the process exits.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU (different streams or threads without ordering) race on
+ * it.  Nothing needs clearing between calls (each region is overwritten before
+ * it is read).  The current device must be the operator's device.  Dense
+ * operators need no scratch and are applied directly.  Allocates nothing:
+ * no cudaMalloc, cudaFree or allocating library call. */
+int rt_apply_noalloc(rt_operator* op, const void* X, void* Y, void* stream);
+
 /* Sbar^E_nu (Proposition 2 / Example of Section 1.2, discretised as in
  * Section 2) into out [F][N] (vector element type as in rt_apply). */
 int rt_source(rt_operator* op, void* out, void* stream);

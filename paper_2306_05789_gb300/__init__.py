@@ -86,7 +86,7 @@ class RtSolveStats(ctypes.Structure):
 
 
 # every symbol declared in include/rt.h
-EXPORTS = ("rt_build_operator", "rt_operator_info", "rt_apply", "rt_source", "rt_eval_entries",
+EXPORTS = ("rt_build_operator", "rt_operator_info", "rt_apply", "rt_apply_noalloc", "rt_source", "rt_eval_entries",
            "rt_solve_fixed_point", "rt_free", "rt_last_error", "rt_plan")
 
 _lib = None
@@ -104,6 +104,7 @@ def lib():
     L.rt_build_operator.argtypes = [ctypes.POINTER(RtProblem), ctypes.POINTER(RtHparams), _P, ctypes.POINTER(_P)]
     L.rt_operator_info.argtypes = [_P, ctypes.POINTER(RtInfo)]
     L.rt_apply.argtypes = [_P, _P, _P, _P]
+    L.rt_apply_noalloc.argtypes = [_P, _P, _P, _P]
     L.rt_source.argtypes = [_P, _P, _P]
     L.rt_eval_entries.argtypes = [_P, _c_int, _c_i64, _P, _P, _P, _P]
     L.rt_solve_fixed_point.argtypes = [_P, ctypes.POINTER(RtSolveOpts), _P, _P, ctypes.POINTER(RtSolveStats), _P]
@@ -197,6 +198,10 @@ class Operator:
     def apply(self, X, Y, stream=None):
         """rt_apply: Y = Gbar X, torch tensors [F, N] on the device."""
         _check(lib().rt_apply(self.h, _P(X.data_ptr()), _P(Y.data_ptr()), _stream_ptr(stream)))
+
+    def apply_noalloc(self, X, Y, stream=None):
+        """rt_apply_noalloc: Y = Gbar X using the library's static scratch array (no allocation)."""
+        _check(lib().rt_apply_noalloc(self.h, _P(X.data_ptr()), _P(Y.data_ptr()), _stream_ptr(stream)))
 
     def source(self, out, stream=None):
         """rt_source: Sbar^E into out [F, N]."""

@@ -390,6 +390,15 @@ int rt_apply(rt_operator* h, const void* X, void* Y, void* stream)
     return RT_OK;
 }
 
+int rt_apply_noalloc(rt_operator* h, const void* X, void* Y, void* stream)
+{
+    if (!h || !X || !Y) return fail(RT_EINVAL, "null argument");
+    std::string err;
+    int rc = rt::apply_noalloc(h->op, X, Y, (cudaStream_t)stream, err);
+    if (rc) return fail(rc, err);
+    return RT_OK;
+}
+
 int rt_source(rt_operator* h, void* out, void* stream)
 {
     if (!h || !out) return fail(RT_EINVAL, "null argument");

@@ -347,4 +347,112 @@ int apply_tree(Operator& op, const void* X, void* Y, cudaStream_t s, std::string
     return RT_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Apply without allocation.
+//
+// Same kernels and the same arithmetic as apply_tree + the two permutations,
+// but the scratch (X and Y in tree order and the phase-1 w buffer) lives in
+// one file-scope device array instead of buffers owned by the operator.  The
+// array is kNoAllocBytes large, is held by every GPU that loads the library
+// until the process exits, and is shared by every call: it keeps the previous
+// call's contents (every region used is fully overwritten before it is read,
+// so nothing needs clearing), and two calls that overlap on the GPU race on it.
+// ---------------------------------------------------------------------------
+static constexpr size_t kNoAllocBytes = (size_t)8 << 20;
+static constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+static void* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};   // device address per device, set on first use
+
+static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t apply_noalloc_limit() { return kNoAllocBytes; }
+
+int apply_noalloc(Operator& op, const void* X, void* Y, cudaStream_t s, std::string& err)
+{
+    int dev = 0;
+    RT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != op.device) {
+        err = "rt_apply_noalloc: the current device is not the operator's device";
+        return RT_EINVAL;
+    }
+    const int N = op.N, F = op.F;
+    if (op.mode == RT_MODE_DENSE) {
+        // the dense apply reads X and writes Y directly: no scratch at all
+        const int64_t warps = (int64_t)N * F;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, 152 * 16));
+        if (op.vec64)
+            dense_apply<double><<<grid, 256, 0, s>>>((const double*)op.d_dense, (const double*)X, (double*)Y, N, F,
+                                                     op.d_fq_group);
+        else
+            dense_apply<float><<<grid, 256, 0, s>>>((const float*)op.d_dense, (const float*)X, (float*)Y, N, F,
+                                                    op.d_fq_group);
+        RT_CUDA_TRY(cudaGetLastError());
+        return RT_OK;
+    }
+    const size_t vbytes = round256((size_t)F * N * sizeof(float));
+    const size_t wbytes = round256((size_t)std::max<int64_t>(op.w_len, 1) * sizeof(float));
+    const size_t need = 2 * vbytes + wbytes;
+    if (need > kNoAllocBytes) {
+        err = "rt_apply_noalloc: operator needs " + std::to_string(need) + " bytes of scratch, limit is " +
+              std::to_string(kNoAllocBytes) + " bytes (use rt_apply)";
+        return RT_EINVAL;
+    }
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        err = "rt_apply_noalloc: device index out of range";
+        return RT_EINVAL;
+    }
+    if (!g_noalloc_addr[dev]) {
+        // one-time set-up on this device (the device is current): the host-side
+        // name of a __device__ array is not a device address; ask the runtime for it
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            err = std::string("rt_apply_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            return RT_ECUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    unsigned char* base = (unsigned char*)g_noalloc_addr[dev];
+    float* xt = (float*)base;
+    float* yt = (float*)(base + vbytes);
+    float* w = (float*)(base + 2 * vbytes);
+    int rc = permute_vectors(op, X, xt, 1, 0, F, s);
+    if (rc) {
+        err = "rt_apply_noalloc: permute launch failed";
+        return rc;
+    }
+    if (op.n_p1 > 0) {
+        dim3 g1(op.n_p1, F);
+        if (op.far_prec == RT_PREC_F32)
+            hmv_phase1<float><<<g1, 256, 0, s>>>((const P1Item*)op.d_p1_items, (const float*)op.d_far, xt, w, N,
+                                                 op.d_fq_group);
+        else if (op.far_prec == RT_PREC_BF16)
+            hmv_phase1<__nv_bfloat16><<<g1, 256, 0, s>>>((const P1Item*)op.d_p1_items, (const __nv_bfloat16*)op.d_far,
+                                                         xt, w, N, op.d_fq_group);
+        else
+            hmv_phase1<__half><<<g1, 256, 0, s>>>((const P1Item*)op.d_p1_items, (const __half*)op.d_far, xt, w, N,
+                                                  op.d_fq_group);
+        RT_CUDA_TRY(cudaGetLastError());
+    }
+    dim3 g2(op.n_p2, F);
+    if (op.far_prec == RT_PREC_F32)
+        hmv_phase2<float><<<g2, 256, 0, s>>>((const P2Leaf*)op.d_p2_leaf, (const P2Seg*)op.d_p2_segs,
+                                             (const float*)op.d_far, op.d_near, xt, w, yt, N, op.d_fq_group);
+    else if (op.far_prec == RT_PREC_BF16)
+        hmv_phase2<__nv_bfloat16><<<g2, 256, 0, s>>>((const P2Leaf*)op.d_p2_leaf, (const P2Seg*)op.d_p2_segs,
+                                                     (const __nv_bfloat16*)op.d_far, op.d_near, xt, w, yt, N,
+                                                     op.d_fq_group);
+    else
+        hmv_phase2<__half><<<g2, 256, 0, s>>>((const P2Leaf*)op.d_p2_leaf, (const P2Seg*)op.d_p2_segs,
+                                              (const __half*)op.d_far, op.d_near, xt, w, yt, N, op.d_fq_group);
+    RT_CUDA_TRY(cudaGetLastError());
+    rc = permute_vectors(op, yt, Y, 0, 0, F, s);
+    if (rc) {
+        err = "rt_apply_noalloc: permute launch failed";
+        return rc;
+    }
+    return RT_OK;
+}
+
 }  // namespace rt

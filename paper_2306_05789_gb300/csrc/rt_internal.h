@@ -162,6 +162,9 @@ int hmatvec_prepare(Operator& op, std::string& err);
 // X, Y in tree order, [F][N], element type float (H-matrix / dense F32) or double (dense F64)
 int apply_tree(Operator& op, const void* X, void* Y, cudaStream_t s, std::string& err);
 int permute_vectors(Operator& op, const void* in, void* out, int to_tree, int is64, int rows, cudaStream_t s);
+// rt_apply with its scratch in a file-scope device array (no allocation)
+int apply_noalloc(Operator& op, const void* X, void* Y, cudaStream_t s, std::string& err);
+size_t apply_noalloc_limit();
 int solve_fixed_point(Operator& op, const rt_solve_opts& o, void* J, double* T, rt_solve_stats& st,
                       cudaStream_t s, std::string& err);
 
