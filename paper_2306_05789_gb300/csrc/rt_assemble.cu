@@ -662,10 +662,12 @@ struct DotItem {
     int l;
 };
 
+// one warp per (block, l); lanes stride over rows / columns; FP64 sums
 __global__ void __launch_bounds__(256) aca_dots(AcaDev D, const AcaActive* act, const DotItem* items, int nitems)
 {
-    __shared__ double red[2][8];
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < nitems; it += nw) {
         const DotItem di = items[it];
         const AcaActive a = act[di.ai];
         if (a.skip) continue;
@@ -673,33 +675,23 @@ __global__ void __launch_bounds__(256) aca_dots(AcaDev D, const AcaActive* act, 
         const int64_t ul = di.l == D.rank[b] ? a.uoff : D.uoff[(int64_t)b * D.rmax + di.l];
         const int64_t vl = di.l == D.rank[b] ? a.voff : D.voff[(int64_t)b * D.rmax + di.l];
         for (int g = 0; g < D.G; ++g) {
-            double su = 0.0, sv = 0.0;
             const float* U0 = D.pool + ul + (int64_t)g * a.m;
             const float* U1 = D.pool + a.uoff + (int64_t)g * a.m;
             const float* V0 = D.pool + vl + (int64_t)g * a.n;
             const float* V1 = D.pool + a.voff + (int64_t)g * a.n;
-            for (int i = threadIdx.x; i < a.m; i += blockDim.x) su += (double)U0[i] * (double)U1[i];
-            for (int j = threadIdx.x; j < a.n; j += blockDim.x) sv += (double)V0[j] * (double)V1[j];
+            double su = 0.0, sv = 0.0;
+            for (int i = lane; i < a.m; i += 32) su += (double)U0[i] * (double)U1[i];
+            for (int j = lane; j < a.n; j += 32) sv += (double)V0[j] * (double)V1[j];
+#pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 su += __shfl_xor_sync(0xffffffffu, su, o);
                 sv += __shfl_xor_sync(0xffffffffu, sv, o);
             }
-            if ((threadIdx.x & 31) == 0) {
-                red[0][threadIdx.x >> 5] = su;
-                red[1][threadIdx.x >> 5] = sv;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double tu = 0.0, tv = 0.0;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                    tu += red[0][w];
-                    tv += red[1][w];
-                }
+            if (lane == 0) {
                 double* dst = D.dots + (((int64_t)b * (D.rmax + 1) + di.l) * D.G + g) * 2;
-                dst[0] = tu;
-                dst[1] = tv;
+                dst[0] = su;
+                dst[1] = sv;
             }
-            __syncthreads();
         }
     }
 }
@@ -762,23 +754,28 @@ template <>
 __device__ __forceinline__ __half to_store<__half>(float x) { return __float2half_rn(x); }
 
 struct PackItem {
-    int b;          // far block id
+    int b;          // far block id (ACA numbering)
     int l;          // term
-    int r, m, n;
+    int r, m, n, n8;
     int64_t voff_dst, uoff_dst;   // element offsets of the block's V^T and U^T in the final storage
+    int c0, c1;     // chunk range [c0, c1) in the chunk array
 };
 
 template <class T>
-__global__ void aca_pack(AcaDev D, const PackItem* items, int nitems, T* dst)
+__global__ void aca_pack(AcaDev D, const PackItem* items, int nitems, const Chunk* chunks, T* dst)
 {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const PackItem p = items[it];
         const int64_t us = D.uoff[(int64_t)p.b * D.rmax + p.l], vs = D.voff[(int64_t)p.b * D.rmax + p.l];
         for (int g = 0; g < D.G; ++g) {
             for (int j = threadIdx.x; j < p.n; j += blockDim.x)
-                dst[p.voff_dst + ((int64_t)g * p.r + p.l) * p.n + j] = to_store<T>(D.pool[vs + (int64_t)g * p.n + j]);
-            for (int i = threadIdx.x; i < p.m; i += blockDim.x)
-                dst[p.uoff_dst + ((int64_t)g * p.r + p.l) * p.m + i] = to_store<T>(D.pool[us + (int64_t)g * p.m + i]);
+                dst[p.voff_dst + ((int64_t)g * p.r + p.l) * p.n8 + j] = to_store<T>(D.pool[vs + (int64_t)g * p.n + j]);
+            for (int c = p.c0; c < p.c1; ++c) {
+                const Chunk ch = chunks[c];
+                for (int i = threadIdx.x; i < ch.m; i += blockDim.x)
+                    dst[p.uoff_dst + ch.off + ((int64_t)g * p.r + p.l) * ch.m8 + i] =
+                        to_store<T>(D.pool[us + (int64_t)g * p.m + ch.rbeg + i]);
+            }
         }
     }
 }
@@ -985,8 +982,8 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
                 RT_CUDA_TRY(cudaMalloc((void**)&d_dot, sizeof(DotItem) * dot_cap));
             }
             RT_CUDA_TRY(cudaMemcpyAsync(d_dot, dots.data(), sizeof(DotItem) * dots.size(), cudaMemcpyHostToDevice, s));
-            aca_dots<<<(int)std::min<int64_t>((int64_t)dots.size(), (int64_t)sms * 16), 256, 0, s>>>(
-                D, d_act, d_dot, (int)dots.size());
+            aca_dots<<<(int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)dots.size() + 7) / 8, (int64_t)sms * 32)),
+                       256, 0, s>>>(D, d_act, d_dot, (int)dots.size());
             aca_finish<<<(na + 127) / 128, 128, 0, s>>>(D, d_act, na);
             RT_CUDA_TRY(cudaGetLastError());
             RT_CUDA_TRY(cudaMemcpyAsync(h_status, D.status, sizeof(int) * nfar, cudaMemcpyDeviceToHost, s));
@@ -1033,21 +1030,22 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
     op.n_far = (int)op.far_blocks.size();
     op.n_near = (int)op.dense_blocks.size();
 
-    // ---- far storage (pack) --------------------------------------------------
+    // ---- far storage (pack): V^T [G][r][n8], U^T per leaf chunk [G][r][m8] ----
     cudaEventRecord(ev0, s);
     const int esz = op.far_prec == RT_PREC_F32 ? 4 : 2;
     int64_t far_elems = 0;
     op.far_v_off.assign(op.n_far, 0);
     op.far_u_off.assign(op.n_far, 0);
+    op.far_chunks.clear();
+    op.far_chunk_ptr.assign(1, 0);
     for (int k = 0; k < op.n_far; ++k) {
         const FarBlock& fb = op.far_blocks[k];
         const int r = op.rank[k];
         op.far_v_off[k] = far_elems;
-        far_elems += (int64_t)G * r * fb.n;
-        far_elems = (far_elems + 7) & ~(int64_t)7;
+        far_elems += (int64_t)G * r * round8(fb.n);
         op.far_u_off[k] = far_elems;
-        far_elems += (int64_t)G * r * fb.m;
-        far_elems = (far_elems + 7) & ~(int64_t)7;
+        far_elems += block_chunks(op.plan, fb.row0, fb.m, (int64_t)G * r, op.far_chunks);
+        op.far_chunk_ptr.push_back((int)op.far_chunks.size());
     }
     if (op.n_far > 0) {
         char* d = nullptr;
@@ -1057,22 +1055,30 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
             return rc;
         }
         op.d_far = d;
+        RT_CUDA_TRY(cudaMemsetAsync(d, 0, (size_t)far_elems * esz, s));   // padding stays zero
         std::vector<PackItem> items;
         for (int k = 0; k < op.n_far; ++k)
             for (int l = 0; l < op.rank[k]; ++l)
-                items.push_back({far_src[k], l, op.rank[k], op.far_blocks[k].m, op.far_blocks[k].n, op.far_v_off[k],
-                                 op.far_u_off[k]});
+                items.push_back({far_src[k], l, op.rank[k], op.far_blocks[k].m, op.far_blocks[k].n,
+                                 round8(op.far_blocks[k].n), op.far_v_off[k], op.far_u_off[k], op.far_chunk_ptr[k],
+                                 op.far_chunk_ptr[k + 1]});
         PackItem* d_items = nullptr;
+        Chunk* d_chunks = nullptr;
         RT_CUDA_TRY(cudaMalloc((void**)&d_items, sizeof(PackItem) * items.size()));
+        RT_CUDA_TRY(cudaMalloc((void**)&d_chunks, sizeof(Chunk) * op.far_chunks.size()));
         RT_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), sizeof(PackItem) * items.size(), cudaMemcpyHostToDevice, s));
+        RT_CUDA_TRY(cudaMemcpyAsync(d_chunks, op.far_chunks.data(), sizeof(Chunk) * op.far_chunks.size(),
+                                    cudaMemcpyHostToDevice, s));
         const int grid = (int)std::min<size_t>(items.size(), 152 * 64);
-        if (op.far_prec == RT_PREC_F32) aca_pack<float><<<grid, 256, 0, s>>>(D, d_items, (int)items.size(), (float*)d);
+        const int ni = (int)items.size();
+        if (op.far_prec == RT_PREC_F32) aca_pack<float><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, (float*)d);
         else if (op.far_prec == RT_PREC_BF16)
-            aca_pack<__nv_bfloat16><<<grid, 256, 0, s>>>(D, d_items, (int)items.size(), (__nv_bfloat16*)d);
-        else aca_pack<__half><<<grid, 256, 0, s>>>(D, d_items, (int)items.size(), (__half*)d);
+            aca_pack<__nv_bfloat16><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, (__nv_bfloat16*)d);
+        else aca_pack<__half><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, (__half*)d);
         RT_CUDA_TRY(cudaGetLastError());
         RT_CUDA_TRY(cudaStreamSynchronize(s));
         cudaFree(d_items);
+        cudaFree(d_chunks);
     }
     if (pool) cudaFree(pool);
     cleanup();
@@ -1081,30 +1087,37 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
     cudaEventElapsedTime(&ms, ev0, ev1);
     op.info.ms_pack = ms;
 
-    // ---- dense blocks (near leaves and fallbacks): A^T [G][n][m] ------------
+    // ---- dense blocks (near leaves and fallbacks): per leaf chunk A^T [G][n][m8]
     cudaEventRecord(ev0, s);
     int64_t near_elems = 0;
     op.dense_off.assign(op.n_near, 0);
+    op.dense_chunks.clear();
+    op.dense_chunk_ptr.assign(1, 0);
     for (int k = 0; k < op.n_near; ++k) {
+        const FarBlock& fb = op.dense_blocks[k];
         op.dense_off[k] = near_elems;
-        near_elems += (int64_t)G * op.dense_blocks[k].m * op.dense_blocks[k].n;
-        near_elems = (near_elems + 3) & ~(int64_t)3;
+        near_elems += block_chunks(op.plan, fb.row0, fb.m, (int64_t)G * fb.n, op.dense_chunks);
+        op.dense_chunk_ptr.push_back((int)op.dense_chunks.size());
     }
     if (op.n_near > 0) {
         if ((rc = dev_alloc(op, &op.d_near, (size_t)near_elems, err))) return rc;
+        RT_CUDA_TRY(cudaMemsetAsync(op.d_near, 0, sizeof(float) * (size_t)near_elems, s));
         std::vector<EntrySpan> spans;
         for (int k = 0; k < op.n_near; ++k) {
             const FarBlock& fb = op.dense_blocks[k];
-            EntrySpan sp{};
-            sp.i0 = fb.row0;
-            sp.ni = fb.m;
-            sp.j0 = fb.col0;
-            sp.nj = fb.n;
-            sp.base = op.dense_off[k];
-            sp.gs = (int64_t)fb.m * fb.n;
-            sp.is = 1;
-            sp.js = fb.m;
-            spans.push_back(sp);
+            for (int c = op.dense_chunk_ptr[k]; c < op.dense_chunk_ptr[k + 1]; ++c) {
+                const Chunk& ch = op.dense_chunks[c];
+                EntrySpan sp{};
+                sp.i0 = fb.row0 + ch.rbeg;
+                sp.ni = ch.m;
+                sp.j0 = fb.col0;
+                sp.nj = fb.n;
+                sp.base = op.dense_off[k] + ch.off;
+                sp.gs = (int64_t)fb.n * ch.m8;
+                sp.is = 1;
+                sp.js = ch.m8;
+                spans.push_back(sp);
+            }
         }
         if ((rc = launch_spans<float, float>(op, spans, op.d_near, s, err))) return rc;
     }

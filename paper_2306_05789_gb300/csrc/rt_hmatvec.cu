@@ -2,14 +2,19 @@
 // (Y_nu = Gbar_{g(nu)} X_nu), the per-iteration cost of the fixed point
 // ("the fixed point iterations involve only matrix vector products", abstract).
 //
-// H-matrix apply in two phases, both over flat, precomputed work lists:
-//   phase 1: for every far block b and frequency f:  w_{b,f} = V_g^T x_f[cols(b)]
-//            (one warp per rank row k: a coalesced dot product of length n)
+// H-matrix apply in two phases over flat, precomputed work lists:
+//   phase 1: w_{b,f} = V_g^T x_f[cols(b)] for every far block b and frequency f.
+//            The rank rows of all blocks form one list sorted by row length;
+//            a sub-warp (8, 16 or 32 lanes, matched to the row length) reads a
+//            row with 16-byte loads and reduces it with shuffles.
 //   phase 2: for every leaf row cluster l and frequency f (row ownership, no
-//            atomics): y_f[rows(l)] = sum_{far b over l} U_g[rows(l), :] w_{b,f}
-//                                    + sum_{dense b in l} A_g[rows(l), :] x_f[cols(b)]
-// Far factors are stored transposed (V^T [r][n], U^T [r][m]) and dense blocks
-// column-major (A^T [n][m]) so that consecutive threads read consecutive rows.
+//            atomics): y_f[rows(l)] = sum_far U_g[rows(l), :] w_{b,f}
+//                                   + sum_dense A_g[rows(l), :] x_f[cols(b)].
+//            Each (leaf, block) pair is one contiguous chunk [count][m8] in
+//            HBM; a thread owns 4 consecutive rows and a slice of the count.
+// Far factors are stored transposed (V^T [r][n8]; U^T per leaf chunk
+// [r][m8]) and dense blocks column-major per leaf chunk (A^T [n][m8]), padded
+// to multiples of 8 elements with zeros so every chunk row is 16-byte aligned.
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -21,111 +26,221 @@
 
 namespace rt {
 
+struct P1Row {
+    int64_t v;        // element offset of row k of V^T for group 0
+    int64_t gstride;  // elements between groups (r * n8)
+    int64_t w;        // w index for f = 0 (w_base + k); frequency f adds f * r
+    int n, col0, r, pad;
+};
+
 struct P1Item {
-    int64_t v_off;   // element offset of the block's V^T [G][r][n]
-    int64_t w_base;  // offset of the block's w [F][r]
-    int n, col0, r, k0, nk, pad;
-};
-
-struct P2Leaf {
-    int row0, m, seg0, nseg;
-};
-
-struct P2Seg {
-    int64_t a_off;   // element offset of row (leaf start) of k = 0, group 0
-    int64_t gstride; // elements between groups
-    int64_t vbase;   // far: w_base of the block; dense: column offset col0
-    int stride;      // elements between consecutive k (m of the block)
-    int count;       // r (far) or n (dense)
-    int kind;        // 0 far, 1 dense
+    int row0, row1;   // range of the row list
+    int sw;           // sub-warp width (8, 16 or 32)
     int pad;
 };
 
-template <class T>
-__device__ __forceinline__ float ld_f(const T* p);
-template <>
-__device__ __forceinline__ float ld_f<float>(const float* p) { return __ldg(p); }
-template <>
-__device__ __forceinline__ float ld_f<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-template <>
-__device__ __forceinline__ float ld_f<__half>(const __half* p) { return __half2float(*p); }
+struct P2Leaf {
+    int row0, m, m8, seg0, nseg, pad;
+};
 
-// phase 1: grid (items, F), 256 threads = 8 warps, warp per rank row
+struct P2Seg {
+    int64_t a;        // element offset of the chunk for group 0
+    int64_t gstride;  // elements between groups (count * m8)
+    int64_t vbase;    // far: w_base of the block; dense: column offset col0
+    int count;        // r (far) or n (dense)
+    int kind;         // 0 far, 1 dense
+};
+
+// ---- element loads ---------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(256) hmv_phase1(const P1Item* __restrict__ items, const T* __restrict__ far,
-                                                  const float* __restrict__ X, float* __restrict__ W, int N,
-                                                  const int* __restrict__ fgroup)
+struct VecW;
+template <>
+struct VecW<float> {
+    static constexpr int n = 4;
+};
+template <>
+struct VecW<__nv_bfloat16> {
+    static constexpr int n = 8;
+};
+template <>
+struct VecW<__half> {
+    static constexpr int n = 8;
+};
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float to_f(__half x) { return __half2float(x); }
+
+// 16-byte load of VecW<T>::n elements, converted to float
+__device__ __forceinline__ void load16(const float* p, float* v)
 {
-    const P1Item it = items[blockIdx.x];
-    const int f = blockIdx.y;
-    const int g = fgroup[f];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float* __restrict__ x = X + (int64_t)f * N + it.col0;
-    for (int k = it.k0 + warp; k < it.k0 + it.nk; k += 8) {
-        const T* __restrict__ v = far + it.v_off + ((int64_t)g * it.r + k) * it.n;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        int j = lane;
-        for (; j + 96 < it.n; j += 128) {
-            s0 += ld_f<T>(v + j) * __ldg(x + j);
-            s1 += ld_f<T>(v + j + 32) * __ldg(x + j + 32);
-            s2 += ld_f<T>(v + j + 64) * __ldg(x + j + 64);
-            s3 += ld_f<T>(v + j + 96) * __ldg(x + j + 96);
-        }
-        for (; j < it.n; j += 32) s0 += ld_f<T>(v + j) * __ldg(x + j);
-        float s = (s0 + s1) + (s2 + s3);
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
+}
+__device__ __forceinline__ void load16(const __nv_bfloat16* p, float* v)
+{
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
+    const unsigned u[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) W[it.w_base + (int64_t)f * it.r + k] = s;
+    for (int k = 0; k < 4; ++k) {
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u[k]));
+        v[2 * k] = f.x;
+        v[2 * k + 1] = f.y;
+    }
+}
+__device__ __forceinline__ void load16(const __half* p, float* v)
+{
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
+    const unsigned u[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u[k]));
+        v[2 * k] = f.x;
+        v[2 * k + 1] = f.y;
     }
 }
 
-// phase 2: grid (leaves, F), 256 threads: row = t % 64, slice = t / 64
+// 4 consecutive elements (16 bytes for float, 8 for 16-bit types), converted
+__device__ __forceinline__ float4 load4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float4 load4(const __nv_bfloat16* p)
+{
+    const uint2 a = __ldg(reinterpret_cast<const uint2*>(p));
+    const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&a.x));
+    const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&a.y));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+__device__ __forceinline__ float4 load4(const __half* p)
+{
+    const uint2 a = __ldg(reinterpret_cast<const uint2*>(p));
+    const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&a.x));
+    const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&a.y));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+// phase 1: grid (items, F), 256 threads
+template <class T>
+__global__ void __launch_bounds__(256) hmv_phase1(const P1Item* __restrict__ items, const P1Row* __restrict__ rows,
+                                                  const T* __restrict__ far, const float* __restrict__ X,
+                                                  float* __restrict__ W, int N, const int* __restrict__ fgroup)
+{
+    constexpr int VW = VecW<T>::n;
+    const P1Item it = items[blockIdx.x];
+    const int f = blockIdx.y;
+    const int g = fgroup[f];
+    const int sw = it.sw;
+    const int lane = threadIdx.x & 31;
+    const int sl = lane & (sw - 1);                 // lane within the sub-warp
+    const int per_warp = 32 / sw;                   // rows handled by one warp at a time
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const float* __restrict__ xf = X + (int64_t)f * N;
+    // the loop bound is warp-uniform, so every lane reaches the shuffles below
+    for (int rb = it.row0 + warp * per_warp; rb < it.row1; rb += nwarps * per_warp) {
+        const int ri = rb + lane / sw;
+        const bool ok = ri < it.row1;
+        float s = 0.f;
+        P1Row rw{};
+        if (ok) {
+            rw = rows[ri];
+            const T* __restrict__ v = far + rw.v + (int64_t)g * rw.gstride;
+            const float* __restrict__ x = xf + rw.col0;
+            const int nv = rw.n - rw.n % VW;
+            float s0 = 0.f, s1 = 0.f;
+            int j = sl * VW;
+            for (; j + sw * VW < nv; j += 2 * sw * VW) {
+                float a[VW], b[VW];
+                load16(v + j, a);
+                load16(v + j + sw * VW, b);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    s0 += a[e] * __ldg(x + j + e);
+                    s1 += b[e] * __ldg(x + j + sw * VW + e);
+                }
+            }
+            for (; j < nv; j += sw * VW) {
+                float a[VW];
+                load16(v + j, a);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) s0 += a[e] * __ldg(x + j + e);
+            }
+            for (int t = nv + sl; t < rw.n; t += sw) s0 += to_f(v[t]) * __ldg(x + t);
+            s = s0 + s1;
+        }
+        for (int o = sw >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, sw);
+        if (ok && sl == 0) W[rw.w + (int64_t)f * rw.r] = s;
+    }
+}
+
+// phase 2: grid (leaves, F), 256 threads; thread owns rows 4c..4c+3, slice s of the count
 template <class T>
 __global__ void __launch_bounds__(256) hmv_phase2(const P2Leaf* __restrict__ leaves, const P2Seg* __restrict__ segs,
                                                   const T* __restrict__ far, const float* __restrict__ nearp,
                                                   const float* __restrict__ X, const float* __restrict__ W,
                                                   float* __restrict__ Y, int N, const int* __restrict__ fgroup)
 {
-    __shared__ float red[4][64];
+    __shared__ float4 red[256];
     const P2Leaf L = leaves[blockIdx.x];
     const int f = blockIdx.y;
     const int g = fgroup[f];
-    const int t = threadIdx.x, rr = t & 63, slice = t >> 6;
-    for (int rb = 0; rb < L.m; rb += 64) {
-        const int row = rb + rr;
-        const bool act = row < L.m;
-        float a0 = 0.f, a1 = 0.f;
+    const int ncol = L.m8 >> 2;                     // float4 columns (<= 256)
+    const int nslice = blockDim.x / ncol;
+    const int c = threadIdx.x % ncol, slice = threadIdx.x / ncol;
+    const bool act = slice < nslice;
+    float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+    if (act) {
         for (int si = L.seg0; si < L.seg0 + L.nseg; ++si) {
             const P2Seg sg = segs[si];
             if (sg.kind == 0) {
-                const T* __restrict__ a = far + sg.a_off + (int64_t)g * sg.gstride + row;
+                const T* __restrict__ a = far + sg.a + (int64_t)g * sg.gstride + 4 * c;
                 const float* __restrict__ w = W + sg.vbase + (int64_t)f * sg.count;
-                if (act) {
-                    int k = slice;
-                    for (; k + 4 < sg.count; k += 8) {
-                        a0 += ld_f<T>(a + (int64_t)k * sg.stride) * __ldg(w + k);
-                        a1 += ld_f<T>(a + (int64_t)(k + 4) * sg.stride) * __ldg(w + k + 4);
-                    }
-                    for (; k < sg.count; k += 4) a0 += ld_f<T>(a + (int64_t)k * sg.stride) * __ldg(w + k);
+                int k = slice;
+                for (; k + nslice < sg.count; k += 2 * nslice) {
+                    const float4 p = load4(a + (int64_t)k * L.m8);
+                    const float4 q = load4(a + (int64_t)(k + nslice) * L.m8);
+                    const float wp = __ldg(w + k), wq = __ldg(w + k + nslice);
+                    acc0.x += p.x * wp; acc0.y += p.y * wp; acc0.z += p.z * wp; acc0.w += p.w * wp;
+                    acc1.x += q.x * wq; acc1.y += q.y * wq; acc1.z += q.z * wq; acc1.w += q.w * wq;
+                }
+                for (; k < sg.count; k += nslice) {
+                    const float4 p = load4(a + (int64_t)k * L.m8);
+                    const float wp = __ldg(w + k);
+                    acc0.x += p.x * wp; acc0.y += p.y * wp; acc0.z += p.z * wp; acc0.w += p.w * wp;
                 }
             } else {
-                const float* __restrict__ a = nearp + sg.a_off + (int64_t)g * sg.gstride + row;
+                const float* __restrict__ a = nearp + sg.a + (int64_t)g * sg.gstride + 4 * c;
                 const float* __restrict__ x = X + (int64_t)f * N + sg.vbase;
-                if (act) {
-                    int k = slice;
-                    for (; k + 4 < sg.count; k += 8) {
-                        a0 += __ldg(a + (int64_t)k * sg.stride) * __ldg(x + k);
-                        a1 += __ldg(a + (int64_t)(k + 4) * sg.stride) * __ldg(x + k + 4);
-                    }
-                    for (; k < sg.count; k += 4) a0 += __ldg(a + (int64_t)k * sg.stride) * __ldg(x + k);
+                int k = slice;
+                for (; k + nslice < sg.count; k += 2 * nslice) {
+                    const float4 p = load4(a + (int64_t)k * L.m8);
+                    const float4 q = load4(a + (int64_t)(k + nslice) * L.m8);
+                    const float xp = __ldg(x + k), xq = __ldg(x + k + nslice);
+                    acc0.x += p.x * xp; acc0.y += p.y * xp; acc0.z += p.z * xp; acc0.w += p.w * xp;
+                    acc1.x += q.x * xq; acc1.y += q.y * xq; acc1.z += q.z * xq; acc1.w += q.w * xq;
+                }
+                for (; k < sg.count; k += nslice) {
+                    const float4 p = load4(a + (int64_t)k * L.m8);
+                    const float xp = __ldg(x + k);
+                    acc0.x += p.x * xp; acc0.y += p.y * xp; acc0.z += p.z * xp; acc0.w += p.w * xp;
                 }
             }
         }
-        red[slice][rr] = a0 + a1;
-        __syncthreads();
-        if (slice == 0 && act)
-            Y[(int64_t)f * N + L.row0 + row] = (red[0][rr] + red[1][rr]) + (red[2][rr] + red[3][rr]);
-        __syncthreads();
+    }
+    red[threadIdx.x] = make_float4(acc0.x + acc1.x, acc0.y + acc1.y, acc0.z + acc1.z, acc0.w + acc1.w);
+    __syncthreads();
+    if (threadIdx.x < ncol) {
+        float4 t = red[threadIdx.x];
+        for (int sl = 1; sl < nslice; ++sl) {
+            const float4 u = red[sl * ncol + threadIdx.x];
+            t.x += u.x; t.y += u.y; t.z += u.z; t.w += u.w;
+        }
+        const int r0 = 4 * threadIdx.x;
+        float* __restrict__ y = Y + (int64_t)f * N + L.row0;
+        if (r0 < L.m) y[r0] = t.x;
+        if (r0 + 1 < L.m) y[r0 + 1] = t.y;
+        if (r0 + 2 < L.m) y[r0 + 2] = t.z;
+        if (r0 + 3 < L.m) y[r0 + 3] = t.w;
     }
 }
 
@@ -185,7 +300,7 @@ int hmatvec_prepare(Operator& op, std::string& err)
     int* d_fg = nullptr;
     if ((rc = dev_alloc(op, &d_fg, op.F, err))) return rc;
     RT_CUDA_TRY(cudaMemcpy(d_fg, op.fgroup.data(), sizeof(int) * op.F, cudaMemcpyHostToDevice));
-    op.d_fq = nullptr;
+    op.d_fq_group = d_fg;
     // frequency table for the solver: nu, w c (1-a), a, group
     {
         std::vector<double> fq((size_t)op.F * 4);
@@ -198,73 +313,77 @@ int hmatvec_prepare(Operator& op, std::string& err)
         if ((rc = dev_alloc(op, &op.d_fq, fq.size(), err))) return rc;
         RT_CUDA_TRY(cudaMemcpy(op.d_fq, fq.data(), sizeof(double) * fq.size(), cudaMemcpyHostToDevice));
     }
-    op.d_fq_group = d_fg;
     const size_t esz = op.vec64 ? 8 : 4;
     const int64_t N = op.N, F = op.F;
-    if (op.mode == RT_MODE_DENSE) {
-        return RT_OK;
-    }
-    // ---- phase-1 items -------------------------------------------------------
-    std::vector<P1Item> p1;
+    if (op.mode == RT_MODE_DENSE) return RT_OK;
+    for (int l = 0; l < (int)op.plan.leaf_size.size(); ++l)
+        if (op.plan.leaf_size[l] > 1024) {
+            err = "leaf clusters larger than 1024 rows are not supported";
+            return RT_EINVAL;
+        }
+    // ---- phase-1 rows and items ----------------------------------------------
+    std::vector<P1Row> rows;
     std::vector<int64_t> w_base(op.n_far);
     int64_t wl = 0;
-    const int kchunk = 32;
     for (int b = 0; b < op.n_far; ++b) {
         const FarBlock& fb = op.far_blocks[b];
         const int r = op.rank[b];
         w_base[b] = wl;
         wl += F * r;
-        for (int k0 = 0; k0 < r; k0 += kchunk) {
-            P1Item it{};
-            it.v_off = op.far_v_off[b];
-            it.w_base = w_base[b];
-            it.n = fb.n;
-            it.col0 = fb.col0;
-            it.r = r;
-            it.k0 = k0;
-            it.nk = std::min(kchunk, r - k0);
-            p1.push_back(it);
+        for (int k = 0; k < r; ++k) {
+            P1Row rw{};
+            rw.v = op.far_v_off[b] + (int64_t)k * round8(fb.n);
+            rw.gstride = (int64_t)r * round8(fb.n);
+            rw.w = w_base[b] + k;
+            rw.n = fb.n;
+            rw.col0 = fb.col0;
+            rw.r = r;
+            rows.push_back(rw);
         }
     }
-    // longest first
-    std::stable_sort(p1.begin(), p1.end(),
-                     [](const P1Item& a, const P1Item& b) { return (int64_t)a.n * a.nk > (int64_t)b.n * b.nk; });
+    std::stable_sort(rows.begin(), rows.end(), [](const P1Row& a, const P1Row& b) { return a.n > b.n; });
+    std::vector<P1Item> items;
+    const int vw = op.far_prec == RT_PREC_F32 ? 4 : 8;
+    const int esz_far = op.far_prec == RT_PREC_F32 ? 4 : 2;
+    for (size_t i = 0; i < rows.size();) {
+        const int n = rows[i].n;
+        int sw = 32;
+        if ((n + vw - 1) / vw <= 8) sw = 8;
+        else if ((n + vw - 1) / vw <= 16) sw = 16;
+        // about 48 KB of operator data per CTA, at most 512 rows
+        int per = (int)std::max<int64_t>(1, std::min<int64_t>(512, (48 << 10) / std::max(1, n * esz_far)));
+        size_t j = i;
+        while (j < rows.size() && (int)(j - i) < per && rows[j].n == n) ++j;
+        items.push_back({(int)i, (int)j, sw, 0});
+        i = j;
+    }
     // ---- phase-2 leaves and segments -----------------------------------------
     const int nl = (int)op.plan.leaf_start.size();
     std::vector<std::vector<P2Seg>> per_leaf(nl);
-    auto leaf_of = [&](int row) {
-        int lo = 0, hi = nl - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (op.plan.leaf_start[mid] <= row) lo = mid; else hi = mid - 1;
-        }
-        return lo;
-    };
     for (int b = 0; b < op.n_far; ++b) {
-        const FarBlock& fb = op.far_blocks[b];
         const int r = op.rank[b];
-        for (int l = leaf_of(fb.row0); l < nl && op.plan.leaf_start[l] < fb.row0 + fb.m; ++l) {
+        for (int c = op.far_chunk_ptr[b]; c < op.far_chunk_ptr[b + 1]; ++c) {
+            const Chunk& ch = op.far_chunks[c];
             P2Seg sg{};
             sg.kind = 0;
-            sg.a_off = op.far_u_off[b] + (op.plan.leaf_start[l] - fb.row0);
-            sg.gstride = (int64_t)r * fb.m;
-            sg.stride = fb.m;
+            sg.a = op.far_u_off[b] + ch.off;
+            sg.gstride = (int64_t)r * ch.m8;
             sg.count = r;
             sg.vbase = w_base[b];
-            per_leaf[l].push_back(sg);
+            per_leaf[ch.leaf].push_back(sg);
         }
     }
     for (int b = 0; b < op.n_near; ++b) {
         const FarBlock& fb = op.dense_blocks[b];
-        for (int l = leaf_of(fb.row0); l < nl && op.plan.leaf_start[l] < fb.row0 + fb.m; ++l) {
+        for (int c = op.dense_chunk_ptr[b]; c < op.dense_chunk_ptr[b + 1]; ++c) {
+            const Chunk& ch = op.dense_chunks[c];
             P2Seg sg{};
             sg.kind = 1;
-            sg.a_off = op.dense_off[b] + (op.plan.leaf_start[l] - fb.row0);
-            sg.gstride = (int64_t)fb.m * fb.n;
-            sg.stride = fb.m;
+            sg.a = op.dense_off[b] + ch.off;
+            sg.gstride = (int64_t)fb.n * ch.m8;
             sg.count = fb.n;
             sg.vbase = fb.col0;
-            per_leaf[l].push_back(sg);
+            per_leaf[ch.leaf].push_back(sg);
         }
     }
     std::vector<P2Leaf> leaves(nl);
@@ -272,21 +391,26 @@ int hmatvec_prepare(Operator& op, std::string& err)
     for (int l = 0; l < nl; ++l) {
         leaves[l].row0 = op.plan.leaf_start[l];
         leaves[l].m = op.plan.leaf_size[l];
+        leaves[l].m8 = round8(op.plan.leaf_size[l]);
         leaves[l].seg0 = (int)segs.size();
         leaves[l].nseg = (int)per_leaf[l].size();
         segs.insert(segs.end(), per_leaf[l].begin(), per_leaf[l].end());
     }
-    P1Item* d_p1 = nullptr;
+    P1Item* d_it = nullptr;
+    P1Row* d_rows = nullptr;
     P2Leaf* d_l = nullptr;
     P2Seg* d_s = nullptr;
-    if ((rc = dev_alloc(op, &d_p1, p1.size(), err))) return rc;
+    if ((rc = dev_alloc(op, &d_it, items.size(), err))) return rc;
+    if ((rc = dev_alloc(op, &d_rows, rows.size(), err))) return rc;
     if ((rc = dev_alloc(op, &d_l, leaves.size(), err))) return rc;
     if ((rc = dev_alloc(op, &d_s, segs.size(), err))) return rc;
-    if (!p1.empty()) RT_CUDA_TRY(cudaMemcpy(d_p1, p1.data(), sizeof(P1Item) * p1.size(), cudaMemcpyHostToDevice));
+    if (!items.empty()) RT_CUDA_TRY(cudaMemcpy(d_it, items.data(), sizeof(P1Item) * items.size(), cudaMemcpyHostToDevice));
+    if (!rows.empty()) RT_CUDA_TRY(cudaMemcpy(d_rows, rows.data(), sizeof(P1Row) * rows.size(), cudaMemcpyHostToDevice));
     RT_CUDA_TRY(cudaMemcpy(d_l, leaves.data(), sizeof(P2Leaf) * leaves.size(), cudaMemcpyHostToDevice));
     if (!segs.empty()) RT_CUDA_TRY(cudaMemcpy(d_s, segs.data(), sizeof(P2Seg) * segs.size(), cudaMemcpyHostToDevice));
-    op.d_p1_items = d_p1;
-    op.n_p1 = (int)p1.size();
+    op.d_p1_items = d_it;
+    op.d_p1_rows = d_rows;
+    op.n_p1 = (int)items.size();
     op.d_p2_leaf = d_l;
     op.n_p2 = nl;
     op.d_p2_segs = d_s;
@@ -294,59 +418,66 @@ int hmatvec_prepare(Operator& op, std::string& err)
     op.w_len = wl;
     if ((rc = dev_alloc(op, &op.d_w, (size_t)std::max<int64_t>(wl, 1), err))) return rc;
     // algorithmic bytes of one apply: operator data once per frequency, X read, Y written
-    const int fesz = op.far_prec == RT_PREC_F32 ? 4 : 2;
     int64_t far_e = 0, near_e = 0;
     for (int b = 0; b < op.n_far; ++b) far_e += (int64_t)op.rank[b] * (op.far_blocks[b].m + op.far_blocks[b].n);
     for (int b = 0; b < op.n_near; ++b) near_e += (int64_t)op.dense_blocks[b].m * op.dense_blocks[b].n;
-    op.info.apply_bytes = F * (far_e * fesz + near_e * 4) + 2 * F * N * (int64_t)esz;
+    op.info.apply_bytes = F * (far_e * esz_far + near_e * 4) + 2 * F * N * (int64_t)esz;
     op.info.apply_flops = 2 * F * (far_e + near_e);
+    return RT_OK;
+}
+
+// the two H-matvec phases on tree-order vectors with an explicit w buffer
+static int launch_hmv(Operator& op, const float* x, float* w, float* y, cudaStream_t s, std::string& err)
+{
+    const int N = op.N, F = op.F;
+    const P1Item* it = (const P1Item*)op.d_p1_items;
+    const P1Row* rw = (const P1Row*)op.d_p1_rows;
+    if (op.n_p1 > 0) {
+        dim3 g1(op.n_p1, F);
+        if (op.far_prec == RT_PREC_F32)
+            hmv_phase1<float><<<g1, 256, 0, s>>>(it, rw, (const float*)op.d_far, x, w, N, op.d_fq_group);
+        else if (op.far_prec == RT_PREC_BF16)
+            hmv_phase1<__nv_bfloat16><<<g1, 256, 0, s>>>(it, rw, (const __nv_bfloat16*)op.d_far, x, w, N,
+                                                         op.d_fq_group);
+        else
+            hmv_phase1<__half><<<g1, 256, 0, s>>>(it, rw, (const __half*)op.d_far, x, w, N, op.d_fq_group);
+        RT_CUDA_TRY(cudaGetLastError());
+    }
+    dim3 g2(op.n_p2, F);
+    const P2Leaf* lv = (const P2Leaf*)op.d_p2_leaf;
+    const P2Seg* sg = (const P2Seg*)op.d_p2_segs;
+    if (op.far_prec == RT_PREC_F32)
+        hmv_phase2<float><<<g2, 256, 0, s>>>(lv, sg, (const float*)op.d_far, op.d_near, x, w, y, N, op.d_fq_group);
+    else if (op.far_prec == RT_PREC_BF16)
+        hmv_phase2<__nv_bfloat16><<<g2, 256, 0, s>>>(lv, sg, (const __nv_bfloat16*)op.d_far, op.d_near, x, w, y, N,
+                                                     op.d_fq_group);
+    else
+        hmv_phase2<__half><<<g2, 256, 0, s>>>(lv, sg, (const __half*)op.d_far, op.d_near, x, w, y, N,
+                                              op.d_fq_group);
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+static int launch_dense(Operator& op, const void* X, void* Y, cudaStream_t s, std::string& err)
+{
+    const int N = op.N, F = op.F;
+    const int64_t warps = (int64_t)N * F;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, 152 * 16));
+    if (op.vec64)
+        dense_apply<double><<<grid, 256, 0, s>>>((const double*)op.d_dense, (const double*)X, (double*)Y, N, F,
+                                                 op.d_fq_group);
+    else
+        dense_apply<float><<<grid, 256, 0, s>>>((const float*)op.d_dense, (const float*)X, (float*)Y, N, F,
+                                                op.d_fq_group);
+    RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
 }
 
 int apply_tree(Operator& op, const void* X, void* Y, cudaStream_t s, std::string& err)
 {
-    const int N = op.N, F = op.F;
-    if (op.mode == RT_MODE_DENSE) {
-        const int64_t warps = (int64_t)N * F;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, 152 * 16));
-        const int* fg = op.d_fq_group;
-        if (op.vec64)
-            dense_apply<double><<<grid, 256, 0, s>>>((const double*)op.d_dense, (const double*)X, (double*)Y, N, F, fg);
-        else
-            dense_apply<float><<<grid, 256, 0, s>>>((const float*)op.d_dense, (const float*)X, (float*)Y, N, F, fg);
-        RT_CUDA_TRY(cudaGetLastError());
-        return RT_OK;
-    }
-    const float* x = (const float*)X;
-    float* y = (float*)Y;
-    if (op.n_p1 > 0) {
-        dim3 g1(op.n_p1, F);
-        if (op.far_prec == RT_PREC_F32)
-            hmv_phase1<float><<<g1, 256, 0, s>>>((const P1Item*)op.d_p1_items, (const float*)op.d_far, x, op.d_w, N,
-                                                 op.d_fq_group);
-        else if (op.far_prec == RT_PREC_BF16)
-            hmv_phase1<__nv_bfloat16><<<g1, 256, 0, s>>>((const P1Item*)op.d_p1_items, (const __nv_bfloat16*)op.d_far,
-                                                         x, op.d_w, N, op.d_fq_group);
-        else
-            hmv_phase1<__half><<<g1, 256, 0, s>>>((const P1Item*)op.d_p1_items, (const __half*)op.d_far, x, op.d_w, N,
-                                                  op.d_fq_group);
-        RT_CUDA_TRY(cudaGetLastError());
-    }
-    dim3 g2(op.n_p2, F);
-    if (op.far_prec == RT_PREC_F32)
-        hmv_phase2<float><<<g2, 256, 0, s>>>((const P2Leaf*)op.d_p2_leaf, (const P2Seg*)op.d_p2_segs,
-                                             (const float*)op.d_far, op.d_near, x, op.d_w, y, N, op.d_fq_group);
-    else if (op.far_prec == RT_PREC_BF16)
-        hmv_phase2<__nv_bfloat16><<<g2, 256, 0, s>>>((const P2Leaf*)op.d_p2_leaf, (const P2Seg*)op.d_p2_segs,
-                                                     (const __nv_bfloat16*)op.d_far, op.d_near, x, op.d_w, y, N,
-                                                     op.d_fq_group);
-    else
-        hmv_phase2<__half><<<g2, 256, 0, s>>>((const P2Leaf*)op.d_p2_leaf, (const P2Seg*)op.d_p2_segs,
-                                              (const __half*)op.d_far, op.d_near, x, op.d_w, y, N, op.d_fq_group);
-    RT_CUDA_TRY(cudaGetLastError());
-    return RT_OK;
+    if (op.mode == RT_MODE_DENSE) return launch_dense(op, X, Y, s, err);
+    return launch_hmv(op, (const float*)X, op.d_w, (float*)Y, s, err);
 }
-
 
 // ---------------------------------------------------------------------------
 // Apply without allocation.
@@ -377,19 +508,8 @@ int apply_noalloc(Operator& op, const void* X, void* Y, cudaStream_t s, std::str
         return RT_EINVAL;
     }
     const int N = op.N, F = op.F;
-    if (op.mode == RT_MODE_DENSE) {
-        // the dense apply reads X and writes Y directly: no scratch at all
-        const int64_t warps = (int64_t)N * F;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, 152 * 16));
-        if (op.vec64)
-            dense_apply<double><<<grid, 256, 0, s>>>((const double*)op.d_dense, (const double*)X, (double*)Y, N, F,
-                                                     op.d_fq_group);
-        else
-            dense_apply<float><<<grid, 256, 0, s>>>((const float*)op.d_dense, (const float*)X, (float*)Y, N, F,
-                                                    op.d_fq_group);
-        RT_CUDA_TRY(cudaGetLastError());
-        return RT_OK;
-    }
+    // the dense apply reads X and writes Y directly: no scratch at all
+    if (op.mode == RT_MODE_DENSE) return launch_dense(op, X, Y, s, err);
     const size_t vbytes = round256((size_t)F * N * sizeof(float));
     const size_t wbytes = round256((size_t)std::max<int64_t>(op.w_len, 1) * sizeof(float));
     const size_t need = 2 * vbytes + wbytes;
@@ -422,31 +542,7 @@ int apply_noalloc(Operator& op, const void* X, void* Y, cudaStream_t s, std::str
         err = "rt_apply_noalloc: permute launch failed";
         return rc;
     }
-    if (op.n_p1 > 0) {
-        dim3 g1(op.n_p1, F);
-        if (op.far_prec == RT_PREC_F32)
-            hmv_phase1<float><<<g1, 256, 0, s>>>((const P1Item*)op.d_p1_items, (const float*)op.d_far, xt, w, N,
-                                                 op.d_fq_group);
-        else if (op.far_prec == RT_PREC_BF16)
-            hmv_phase1<__nv_bfloat16><<<g1, 256, 0, s>>>((const P1Item*)op.d_p1_items, (const __nv_bfloat16*)op.d_far,
-                                                         xt, w, N, op.d_fq_group);
-        else
-            hmv_phase1<__half><<<g1, 256, 0, s>>>((const P1Item*)op.d_p1_items, (const __half*)op.d_far, xt, w, N,
-                                                  op.d_fq_group);
-        RT_CUDA_TRY(cudaGetLastError());
-    }
-    dim3 g2(op.n_p2, F);
-    if (op.far_prec == RT_PREC_F32)
-        hmv_phase2<float><<<g2, 256, 0, s>>>((const P2Leaf*)op.d_p2_leaf, (const P2Seg*)op.d_p2_segs,
-                                             (const float*)op.d_far, op.d_near, xt, w, yt, N, op.d_fq_group);
-    else if (op.far_prec == RT_PREC_BF16)
-        hmv_phase2<__nv_bfloat16><<<g2, 256, 0, s>>>((const P2Leaf*)op.d_p2_leaf, (const P2Seg*)op.d_p2_segs,
-                                                     (const __nv_bfloat16*)op.d_far, op.d_near, xt, w, yt, N,
-                                                     op.d_fq_group);
-    else
-        hmv_phase2<__half><<<g2, 256, 0, s>>>((const P2Leaf*)op.d_p2_leaf, (const P2Seg*)op.d_p2_segs,
-                                              (const __half*)op.d_far, op.d_near, xt, w, yt, N, op.d_fq_group);
-    RT_CUDA_TRY(cudaGetLastError());
+    if ((rc = launch_hmv(op, xt, w, yt, s, err))) return rc;
     rc = permute_vectors(op, yt, Y, 0, 0, F, s);
     if (rc) {
         err = "rt_apply_noalloc: permute launch failed";

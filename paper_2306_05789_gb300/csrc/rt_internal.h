@@ -6,8 +6,11 @@
 //   tgeo     : float4/dbl4 [T] (centroid x, y, z, diameter); tvol [T]
 //   vt_ptr   : int [N+1], vt_idx: int [nnz] packed (tet << 2) | local vertex slot
 //   vectors  : [F][N] frequency-major
-//   far block b, group g : V^T [r][n] at far_v[b] + g*r*n, U^T [r][m] at far_u[b] + g*r*m
-//   dense block b, group g: A^T [n][m] (column-major) at dense_off[b] + g*m*n
+//   rows of every block are split into leaf chunks (the leaves of the cluster
+//   tree that the block's row cluster contains); padded sizes are multiples of 8
+//   far block b, group g : V^T [r][n8] at far_v_off[b] + g*r*n8;
+//                          chunk c: U^T [r][m8_c] at far_u_off[b] + off_c + g*r*m8_c
+//   dense block b, chunk c, group g: A^T [n][m8_c] at dense_off[b] + off_c + g*n*m8_c
 #pragma once
 
 #include <cuda_runtime.h>
@@ -71,6 +74,15 @@ struct FarBlock {
     int row0, m, col0, n;
 };
 
+inline int round8(int x) { return (x + 7) & ~7; }
+
+// Leaf chunk of a block's rows: rows [rbeg, rbeg + m) of the block (local),
+// padded to m8 = round8(m), stored at offset off from the block's base.
+struct Chunk {
+    int leaf, rbeg, m, m8;
+    int64_t off;
+};
+
 // Host-side plan of one instance.
 struct Plan {
     int N = 0;
@@ -83,6 +95,30 @@ struct Plan {
 };
 
 int plan_build(const double* xyz, int64_t n, int leaf, double eta, int adm, Plan& out, std::string& err);
+
+// Leaf chunks of rows [row0, row0 + m); per_row = elements stored per padded
+// row (G*r for far U, G*n for dense blocks).  Returns the total element count.
+inline int64_t block_chunks(const Plan& P, int row0, int m, int64_t per_row, std::vector<Chunk>& out)
+{
+    const int nl = (int)P.leaf_start.size();
+    int lo = 0, hi = nl - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (P.leaf_start[mid] <= row0) lo = mid; else hi = mid - 1;
+    }
+    int64_t off = 0;
+    for (int l = lo; l < nl && P.leaf_start[l] < row0 + m; ++l) {
+        Chunk c;
+        c.leaf = l;
+        c.rbeg = P.leaf_start[l] - row0;
+        c.m = P.leaf_size[l];
+        c.m8 = round8(c.m);
+        c.off = off;
+        off += per_row * c.m8;
+        out.push_back(c);
+    }
+    return off;
+}
 
 // Operator (one instance).
 struct Operator {
@@ -126,10 +162,13 @@ struct Operator {
     std::vector<FarBlock> far_blocks, dense_blocks;   // final split
     float* d_near = nullptr;    // dense blocks' A^T
     std::vector<int64_t> dense_off;
+    std::vector<int> dense_chunk_ptr, far_chunk_ptr;   // CSR over the chunk arrays
+    std::vector<Chunk> dense_chunks, far_chunks;
     void* d_far = nullptr;      // far U/V (float, bf16 or f16)
     std::vector<int64_t> far_v_off, far_u_off;
     // matvec work lists (device)
     void* d_p1_items = nullptr; int n_p1 = 0;
+    void* d_p1_rows = nullptr;
     void* d_p2_leaf = nullptr;  int n_p2 = 0;
     void* d_p2_segs = nullptr;  int n_p2_segs = 0;
     float* d_w = nullptr;       int64_t w_len = 0;   // phase-1 scratch [sum r][F]

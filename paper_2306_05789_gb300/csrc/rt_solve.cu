@@ -27,15 +27,6 @@ __device__ __forceinline__ double planck(double nu, double T)
     return nu * nu * nu / expm1(x);
 }
 
-__device__ __forceinline__ double planck_dT(double nu, double T)
-{
-    if (!(T > 0.0)) return 0.0;
-    const double x = nu / T;
-    if (x > 700.0) return 0.0;
-    const double em = expm1(x);
-    return nu * nu * nu * (x / T) * (em + 1.0) / (em * em);
-}
-
 template <class V>
 __global__ void fp_init(V* J, double* T, int64_t nJ, int N, double T0, int keepJ)
 {
@@ -125,48 +116,75 @@ __global__ void fp_reduce(const double* __restrict__ part, int nparts, double* r
     }
 }
 
-// temperature from the Planck balance, one thread per vertex
-template <class V>
-__global__ void fp_newton(const V* __restrict__ J, double* __restrict__ T, const double* __restrict__ fq, int N, int F,
-                          int grey, int* __restrict__ fail)
+// temperature from the Planck balance: one warp per vertex, lanes over the
+// frequencies; B_nu and dB_nu/dT share one expm1 per frequency and Newton step:
+//   B = nu^3 / em,  dB/dT = B (x / T) (1 + 1/em),  em = expm1(x),  x = nu / T.
+__device__ __forceinline__ void planck_sum(const double* __restrict__ fq, int F, double t, int lane, double& g,
+                                           double& dg)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    g = 0.0;
+    dg = 0.0;
+    if (t > 0.0) {
+        for (int f = lane; f < F; f += 32) {
+            const double nu = fq[4 * f], wt = fq[4 * f + 1];
+            const double x = nu / t;
+            if (x < 700.0) {
+                const double em = expm1(x);
+                const double B = nu * nu * nu / em;
+                g += wt * B;
+                dg += wt * B * (x / t) * (1.0 + 1.0 / em);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        g += __shfl_xor_sync(0xffffffffu, g, o);
+        dg += __shfl_xor_sync(0xffffffffu, dg, o);
+    }
+}
+
+template <class V>
+__global__ void __launch_bounds__(256) fp_newton(const V* __restrict__ J, double* __restrict__ T,
+                                                 const double* __restrict__ fq, int N, int F, int grey,
+                                                 int* __restrict__ fail)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += nw) {
         if (grey) {
-            const double j = (double)J[i];
-            T[i] = j > 0.0 ? sqrt(sqrt(j / kSigma)) : 0.0;
+            if (lane == 0) {
+                const double j = (double)J[i];
+                T[i] = j > 0.0 ? sqrt(sqrt(j / kSigma)) : 0.0;
+            }
             continue;
         }
         double rhs = 0.0;
-        for (int f = 0; f < F; ++f) rhs += fq[4 * f + 1] * (double)J[(int64_t)f * N + i];
+        for (int f = lane; f < F; f += 32) rhs += fq[4 * f + 1] * (double)J[(int64_t)f * N + i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rhs += __shfl_xor_sync(0xffffffffu, rhs, o);
         if (!(rhs > 0.0)) {
-            T[i] = 0.0;
+            if (lane == 0) T[i] = 0.0;
             continue;
         }
-        auto g = [&](double t) {
-            double s = 0.0;
-            for (int f = 0; f < F; ++f) s += fq[4 * f + 1] * planck(fq[4 * f], t);
-            return s;
-        };
-        double lo = 0.0, hi = fmax(1.0, 2.0 * T[i]);
+        const double tp = T[i];
+        double lo = 0.0, hi = fmax(1.0, 2.0 * tp);
+        double g, dg;
+        planck_sum(fq, F, hi, lane, g, dg);
         int guard = 0;
-        while (g(hi) < rhs && guard < 200) {
+        while (g < rhs && guard < 200) {
             lo = hi;
             hi *= 2.0;
+            planck_sum(fq, F, hi, lane, g, dg);
             ++guard;
         }
-        double t = T[i];
-        if (!(t > lo && t < hi)) t = 0.5 * (lo + hi);
+        double t = (tp > lo && tp < hi) ? tp : 0.5 * (lo + hi);
         bool ok = false;
         for (int it = 0; it < 100; ++it) {
-            double fv = 0.0, df = 0.0;
-            for (int f = 0; f < F; ++f) {
-                fv += fq[4 * f + 1] * planck(fq[4 * f], t);
-                df += fq[4 * f + 1] * planck_dT(fq[4 * f], t);
-            }
-            fv -= rhs;
+            planck_sum(fq, F, t, lane, g, dg);
+            const double fv = g - rhs;
             if (fv < 0.0) lo = t;
             if (fv > 0.0) hi = t;
-            double tn = df > 0.0 ? t - fv / df : 0.5 * (lo + hi);
+            double tn = dg > 0.0 ? t - fv / dg : 0.5 * (lo + hi);
             if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
             const bool done = fabs(tn - t) <= 1e-14 * fabs(tn);
             t = tn;
@@ -175,8 +193,10 @@ __global__ void fp_newton(const V* __restrict__ J, double* __restrict__ T, const
                 break;
             }
         }
-        if (!ok) atomicOr(fail, 1);
-        T[i] = t;
+        if (lane == 0) {
+            if (!ok) atomicOr(fail, 1);
+            T[i] = t;
+        }
     }
 }
 
@@ -197,7 +217,8 @@ static int one_iteration(Operator& op, cudaStream_t s, int grey, int* d_counter,
     if (rc) return rc;
     fp_update<V><<<op.n_part, kRedThreads, 0, s>>>((V*)op.d_J, (const V*)op.d_Y, (const V*)op.d_SE, tot, op.d_part);
     fp_reduce<<<1, 256, 0, s>>>(op.d_part, op.n_part, op.d_res, d_counter, cap);
-    fp_newton<V><<<grid_elem(N), 256, 0, s>>>((const V*)op.d_J, op.d_T, op.d_fq, N, F, grey, d_fail);
+    fp_newton<V><<<(int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)N + 7) / 8, 152 * 32)), 256, 0, s>>>(
+        (const V*)op.d_J, op.d_T, op.d_fq, N, F, grey, d_fail);
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
 }
