@@ -58,6 +58,15 @@ extern "C" {
 #define RT_PREC_BF16 2
 #define RT_PREC_F16 3
 
+/* evaluation of the n-point Gauss sum along a segment (n >= 16) for the
+ * sin-product kappa: RT_LINE_CLOSED uses the exact trigonometric identity
+ * (product-to-sum; the Gauss sum of a sinusoid is its midpoint value times
+ * sum_g w_g cos(beta (u_g - 1/2)) = sinc(beta/2) within the Gauss truncation
+ * error, below 2e-14 for segments with |dx|+|dy|+|dz| <= 3); RT_LINE_NODES
+ * sums the kappa samples node by node.  Both compute the same sum. */
+#define RT_LINE_CLOSED 0
+#define RT_LINE_NODES 1
+
 /* admissibility readings of max(R1,R2) < eta |x1 - x2| (Section 2.1) */
 #define RT_ADM_GAP 0    /* |x1 - x2| = distance between the clusters' bounding spheres (|c1-c2| - R1 - R2) */
 #define RT_ADM_CENTER 1 /* |x1 - x2| = distance between the cluster centroids (literal) */
@@ -127,6 +136,7 @@ typedef struct {
     int gauss_pts;   /* Gauss-Legendre points per line integral (1..32, e.g. 16) */
     int rank_max;    /* ACA rank limit before a block is stored dense (0 = 512) */
     int adm;         /* RT_ADM_GAP (default) or RT_ADM_CENTER */
+    int line_eval;   /* RT_LINE_CLOSED (default) or RT_LINE_NODES (FP32 paths) */
 } rt_hparams;
 
 typedef struct rt_operator rt_operator;

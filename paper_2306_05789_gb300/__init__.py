@@ -27,6 +27,7 @@ RT_KAPPA_CONST, RT_KAPPA_SINPROD = 0, 1
 RT_MODE_DENSE, RT_MODE_HMATRIX = 0, 1
 RT_PREC_F64, RT_PREC_F32, RT_PREC_BF16, RT_PREC_F16 = 0, 1, 2, 3
 RT_ADM_GAP, RT_ADM_CENTER = 0, 1
+RT_LINE_CLOSED, RT_LINE_NODES = 0, 1
 
 _c_i64 = ctypes.c_int64
 _c_int = ctypes.c_int
@@ -57,7 +58,8 @@ class RtProblem(ctypes.Structure):
 
 class RtHparams(ctypes.Structure):
     _fields_ = [("mode", _c_int), ("prec", _c_int), ("far_prec", _c_int), ("aca_eps", _c_dbl), ("leaf", _c_int),
-                ("eta", _c_dbl), ("gauss_pts", _c_int), ("rank_max", _c_int), ("adm", _c_int)]
+                ("eta", _c_dbl), ("gauss_pts", _c_int), ("rank_max", _c_int), ("adm", _c_int),
+                ("line_eval", _c_int)]
 
 
 class RtInfo(ctypes.Structure):
@@ -141,10 +143,10 @@ def _stream_ptr(stream):
 
 
 def hparams(mode=RT_MODE_HMATRIX, prec=None, far_prec=RT_PREC_F32, aca_eps=1e-4, leaf=64, eta=2.0, gauss_pts=16,
-            rank_max=0, adm=RT_ADM_GAP) -> RtHparams:
+            rank_max=0, adm=RT_ADM_GAP, line_eval=RT_LINE_CLOSED) -> RtHparams:
     if prec is None:
         prec = RT_PREC_F32
-    return RtHparams(mode, prec, far_prec, aca_eps, leaf, eta, gauss_pts, rank_max, adm)
+    return RtHparams(mode, prec, far_prec, aca_eps, leaf, eta, gauss_pts, rank_max, adm, line_eval)
 
 
 class _ProblemArgs:

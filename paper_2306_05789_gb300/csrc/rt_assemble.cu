@@ -507,6 +507,228 @@ int assemble_source(Operator& op, cudaStream_t s, std::string& err)
 }
 
 // ---------------------------------------------------------------------------
+// Row evaluation over a column cluster: G_g[i, j] for every column j of a
+// sub-cluster (at most kSubCols consecutive tree-order columns).  Each
+// tetrahedron touching the sub-cluster is visited once: every quadrature
+// point's kernel value feeds the (up to 4) hat functions of the tetrahedron's
+// vertices that lie in the sub-cluster -- the same sums as entry_warp, in a
+// different order, with each point evaluated once instead of once per vertex.
+// One CTA per (row, sub-cluster); the row segment accumulates in shared
+// memory [G][n] (float atomics, so the summation order is not fixed).
+// ---------------------------------------------------------------------------
+struct RowItem {
+    int b;            // ACA block (row = i + istar[b]) or -1 (row = i)
+    int i;
+    int col0, n;      // sub-cluster columns
+    int tet0, ntet;   // its tetrahedra in the sub-cluster tet list
+    int64_t out;      // output offset of (column col0, group 0)
+    int64_t gs, js;   // group and column strides of the output
+};
+
+// MG > 0: the four vertex sums of a tetrahedron accumulate in registers for
+// all groups and are flushed once per tetrahedron; MG == 0 (more than 16
+// groups): every point is added to shared memory directly.  Tetrahedra are
+// handed out through a shared counter so that the few tetrahedra near x_i
+// (14-point rules) do not hold up a fixed partition.
+template <int MG>
+__global__ void __launch_bounds__(256) row_cluster_kernel(KernelParams P, const RowItem* __restrict__ items,
+                                                          const int* __restrict__ sub_tets,
+                                                          const int* __restrict__ istar, float* __restrict__ out)
+{
+    extern __shared__ float acc[];   // [G][n]
+    __shared__ int s_next;
+    const RowItem it = items[blockIdx.x];
+    const int i = it.b >= 0 ? it.i + istar[it.b] : it.i;
+    const int G = P.G, n = it.n;
+    for (int k = threadIdx.x; k < G * n; k += blockDim.x) acc[k] = 0.f;
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
+    const Vec3<float> xi = load_xyz<float>(P, i);
+    Vec3<float> xb = xi;
+    if (P.has_wall) xb = mirror_point<float>(P, xi);
+    const float inv4pi = (float)(1.0 / (4.0 * kPi));
+    for (;;) {
+        const int t = atomicAdd(&s_next, 1);
+        if (t >= it.ntet) break;
+        const int tet = sub_tets[it.tet0 + t];
+        const int4 tv = P.tet[tet];
+        const int jj[4] = {tv.x - it.col0, tv.y - it.col0, tv.z - it.col0, tv.w - it.col0};
+        const bool in0 = (unsigned)jj[0] < (unsigned)n, in1 = (unsigned)jj[1] < (unsigned)n,
+                   in2 = (unsigned)jj[2] < (unsigned)n, in3 = (unsigned)jj[3] < (unsigned)n;
+        const Vec3<float> v0 = load_xyz<float>(P, tv.x), v1 = load_xyz<float>(P, tv.y), v2 = load_xyz<float>(P, tv.z),
+                          v3 = load_xyz<float>(P, tv.w);
+        Vec3<float> cen;
+        float diam, vol;
+        load_tgeo<float>(P, tet, cen, diam, vol);
+        const float lim = 4.f * diam * diam;
+        const int nd = dist2<float>(xi, cen) < lim ? 14 : 4;
+        const int nr = P.has_wall ? (dist2<float>(xb, cen) < lim ? 14 : 4) : 0;
+        float a0[MG > 0 ? MG : 1], a1[MG > 0 ? MG : 1], a2[MG > 0 ? MG : 1], a3[MG > 0 ? MG : 1];
+        if constexpr (MG > 0) {
+#pragma unroll
+            for (int g = 0; g < MG; ++g) a0[g] = a1[g] = a2[g] = a3[g] = 0.f;
+        }
+        for (int q = 0; q < nd + nr; ++q) {
+            const bool refl = q >= nd;
+            const int qq = refl ? q - nd : q;
+            const int row = ((refl ? nr : nd) == 14 ? 4 : 0) + qq;
+            const float b0 = tet_b<float>(row, 0), b1 = tet_b<float>(row, 1), b2 = tet_b<float>(row, 2),
+                        b3 = tet_b<float>(row, 3);
+            Vec3<float> y;
+            y.x = b0 * v0.x + b1 * v1.x + b2 * v2.x + b3 * v3.x;
+            y.y = b0 * v0.y + b1 * v1.y + b2 * v2.y + b3 * v3.y;
+            y.z = b0 * v0.z + b1 * v1.z + b2 * v2.z + b3 * v3.z;
+            float r2, tau;
+            if (!refl) {
+                r2 = dist2<float>(xi, y);
+                tau = optical_depth<float>(P, xi, y);
+            } else {
+                const Vec3<float> xp = wall_point<float>(P, xb, y);
+                r2 = dist2<float>(xb, y);
+                tau = optical_depth<float>(P, xi, xp) + optical_depth<float>(P, xp, y);
+            }
+            float w = vol * tet_w<float>(row) * kappa_at<float>(P, y.x, y.y, y.z) * inv4pi / r2;
+            if (refl) w *= (float)P.R0;
+            if constexpr (MG > 0) {
+#pragma unroll
+                for (int g = 0; g < MG; ++g)
+                    if (g < G) {
+                        const float cg = P.cf[g];
+                        const float val = w * cg * expf(-cg * tau);
+                        a0[g] += val * b0;
+                        a1[g] += val * b1;
+                        a2[g] += val * b2;
+                        a3[g] += val * b3;
+                    }
+            } else {
+                for (int g = 0; g < G; ++g) {
+                    const float cg = P.cf[g];
+                    const float val = w * cg * expf(-cg * tau);
+                    float* a = acc + g * n;
+                    if (in0) atomicAdd(a + jj[0], val * b0);
+                    if (in1) atomicAdd(a + jj[1], val * b1);
+                    if (in2) atomicAdd(a + jj[2], val * b2);
+                    if (in3) atomicAdd(a + jj[3], val * b3);
+                }
+            }
+        }
+        if constexpr (MG > 0) {
+#pragma unroll
+            for (int g = 0; g < MG; ++g)
+                if (g < G) {
+                    float* a = acc + g * n;
+                    if (in0) atomicAdd(a + jj[0], a0[g]);
+                    if (in1) atomicAdd(a + jj[1], a1[g]);
+                    if (in2) atomicAdd(a + jj[2], a2[g]);
+                    if (in3) atomicAdd(a + jj[3], a3[g]);
+                }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < G * n; k += blockDim.x) {
+        const int g = k / n, j = k - g * n;
+        out[it.out + g * it.gs + j * it.js] = acc[k];
+    }
+}
+
+// sub-clusters of every column cluster and the tetrahedra touching each
+int prepare_row_eval(Operator& op, std::string& err)
+{
+    const Plan& P = op.plan;
+    const int nc = (int)P.clusters.size();
+    op.sub_of_cluster_ptr.assign(nc + 1, 0);
+    op.sub_of_cluster.clear();
+    op.sub_start.clear();
+    op.sub_size.clear();
+    op.sub_tet_ptr.assign(1, 0);
+    std::vector<int> sub_id(nc, -1), tets, stamp(op.T, -1);
+    std::vector<char> used(nc, 0);
+    for (const FarBlock& b : P.far_blocks) used[b.sc] = 1;
+    for (const FarBlock& b : P.near_blocks) used[b.sc] = 1;
+    std::vector<std::vector<int>> subs(nc);
+    for (int c = 0; c < nc; ++c) {
+        if (!used[c]) continue;
+        std::vector<int> stack = {c};
+        while (!stack.empty()) {
+            const int k = stack.back();
+            stack.pop_back();
+            const ClusterNode& C = P.clusters[k];
+            if (C.size <= kSubCols || C.left < 0) {
+                if (C.size > kSubCols) {
+                    err = "cluster leaf larger than the row-evaluation width";
+                    return RT_EINVAL;
+                }
+                subs[c].push_back(k);
+            } else {
+                stack.push_back(C.right);
+                stack.push_back(C.left);
+            }
+        }
+    }
+    for (int c = 0; c < nc; ++c) {
+        for (int k : subs[c]) {
+            if (sub_id[k] < 0) {
+                sub_id[k] = (int)op.sub_start.size();
+                const ClusterNode& C = P.clusters[k];
+                op.sub_start.push_back(C.start);
+                op.sub_size.push_back(C.size);
+                for (int v = C.start; v < C.start + C.size; ++v)
+                    for (int e = op.h_vt_ptr[v]; e < op.h_vt_ptr[v + 1]; ++e) {
+                        const int t = op.h_vt_idx[e] >> 2;
+                        if (stamp[t] != sub_id[k]) {
+                            stamp[t] = sub_id[k];
+                            tets.push_back(t);
+                        }
+                    }
+                op.sub_tet_ptr.push_back((int)tets.size());
+            }
+            op.sub_of_cluster.push_back(sub_id[k]);
+        }
+        op.sub_of_cluster_ptr[c + 1] = (int)op.sub_of_cluster.size();
+    }
+    int rc = dev_alloc(op, &op.d_sub_tets, tets.size(), err);
+    if (rc) return rc;
+    RT_CUDA_TRY(cudaMemcpy(op.d_sub_tets, tets.data(), sizeof(int) * tets.size(), cudaMemcpyHostToDevice));
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !attr_set[dev]) {
+        const int bytes = (int)(kMaxGroups * kSubCols * sizeof(float));
+        RT_CUDA_TRY(cudaFuncSetAttribute(row_cluster_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        RT_CUDA_TRY(cudaFuncSetAttribute(row_cluster_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        RT_CUDA_TRY(cudaFuncSetAttribute(row_cluster_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        RT_CUDA_TRY(cudaFuncSetAttribute(row_cluster_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        RT_CUDA_TRY(cudaFuncSetAttribute(row_cluster_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        attr_set[dev] = true;
+    }
+    return RT_OK;
+}
+
+static int launch_rows(Operator& op, const std::vector<RowItem>& items, const int* istar, float* out, cudaStream_t s,
+                       std::string& err)
+{
+    if (items.empty()) return RT_OK;
+    RowItem* d = nullptr;
+    RT_CUDA_TRY(cudaMallocAsync((void**)&d, sizeof(RowItem) * items.size(), s));
+    RT_CUDA_TRY(cudaMemcpyAsync(d, items.data(), sizeof(RowItem) * items.size(), cudaMemcpyHostToDevice, s));
+    int maxn = 0;
+    for (const RowItem& it : items) maxn = std::max(maxn, it.n);
+    const size_t smem = (size_t)op.G * maxn * sizeof(float);
+    for (size_t k0 = 0; k0 < items.size(); k0 += (size_t)1 << 30) {
+        const int cnt = (int)std::min<size_t>(items.size() - k0, (size_t)1 << 30);
+        const int G = op.G;
+        if (G <= 1) row_cluster_kernel<1><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
+        else if (G <= 4) row_cluster_kernel<4><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
+        else if (G <= 8) row_cluster_kernel<8><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
+        else if (G <= 16) row_cluster_kernel<16><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
+        else row_cluster_kernel<0><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
+    }
+    RT_CUDA_TRY(cudaGetLastError());
+    RT_CUDA_TRY(cudaFreeAsync(d, s));
+    return RT_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Batched partially pivoted ACA (Section 2.1), pivots shared by all groups.
 //
 // Every admissible block b (m x n) is approximated for all groups g at once:
@@ -662,7 +884,7 @@ struct DotItem {
     int l;
 };
 
-// one warp per (block, l); lanes stride over rows / columns; FP64 sums
+// one warp per (block, l); lanes stride over rows / columns
 __global__ void __launch_bounds__(256) aca_dots(AcaDev D, const AcaActive* act, const DotItem* items, int nitems)
 {
     const int lane = threadIdx.x & 31;
@@ -679,9 +901,11 @@ __global__ void __launch_bounds__(256) aca_dots(AcaDev D, const AcaActive* act, 
             const float* U1 = D.pool + a.uoff + (int64_t)g * a.m;
             const float* V0 = D.pool + vl + (int64_t)g * a.n;
             const float* V1 = D.pool + a.voff + (int64_t)g * a.n;
-            double su = 0.0, sv = 0.0;
-            for (int i = lane; i < a.m; i += 32) su += (double)U0[i] * (double)U1[i];
-            for (int j = lane; j < a.n; j += 32) sv += (double)V0[j] * (double)V1[j];
+            // FP32 partial sums per lane (short: length/32 terms), FP64 across lanes
+            float pu = 0.f, pv = 0.f;
+            for (int i = lane; i < a.m; i += 32) pu += U0[i] * U1[i];
+            for (int j = lane; j < a.n; j += 32) pv += V0[j] * V1[j];
+            double su = pu, sv = pv;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 su += __shfl_xor_sync(0xffffffffu, su, o);
@@ -948,14 +1172,30 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
             }
             const int na = (int)act.size();
             RT_CUDA_TRY(cudaMemcpyAsync(d_act, act.data(), sizeof(AcaActive) * na, cudaMemcpyHostToDevice, s));
-            // 1. pivot rows
+            // 1. pivot rows: one CTA per (block, sub-cluster of its columns)
             {
-                int grid = grid_for(fr);
-#define RT_LAUNCH_ACA(MG) \
-    aca_entries_kernel<MG><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, d_act, na, fr, 0, D.istar, D.jstar, rowbuf)
-                RT_DISPATCH_MG(G, RT_LAUNCH_ACA);
-#undef RT_LAUNCH_ACA
-                RT_CUDA_TRY(cudaGetLastError());
+                std::vector<RowItem> ritems;
+                for (const AcaActive& a : act) {
+                    const FarBlock& fb = farb[a.b];
+                    for (int e = op.sub_of_cluster_ptr[fb.sc]; e < op.sub_of_cluster_ptr[fb.sc + 1]; ++e) {
+                        const int sb = op.sub_of_cluster[e];
+                        RowItem it{};
+                        it.b = a.b;
+                        it.i = fb.row0;
+                        it.col0 = op.sub_start[sb];
+                        it.n = op.sub_size[sb];
+                        it.tet0 = op.sub_tet_ptr[sb];
+                        it.ntet = op.sub_tet_ptr[sb + 1] - op.sub_tet_ptr[sb];
+                        it.out = a.rbuf + (op.sub_start[sb] - fb.col0);
+                        it.gs = fb.n;
+                        it.js = 1;
+                        ritems.push_back(it);
+                    }
+                }
+                if ((rc = launch_rows(op, ritems, D.istar, rowbuf, s, err))) {
+                    cleanup();
+                    return rc;
+                }
             }
             const int eg_r = (int)std::min<int64_t>((fr + 255) / 256, (int64_t)sms * 32);
             aca_row_residual<<<std::max(1, eg_r), 256, 0, s>>>(D, d_act, na, fr, rowbuf);
@@ -1102,24 +1342,31 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
     if (op.n_near > 0) {
         if ((rc = dev_alloc(op, &op.d_near, (size_t)near_elems, err))) return rc;
         RT_CUDA_TRY(cudaMemsetAsync(op.d_near, 0, sizeof(float) * (size_t)near_elems, s));
-        std::vector<EntrySpan> spans;
+        std::vector<RowItem> ritems;
         for (int k = 0; k < op.n_near; ++k) {
             const FarBlock& fb = op.dense_blocks[k];
             for (int c = op.dense_chunk_ptr[k]; c < op.dense_chunk_ptr[k + 1]; ++c) {
                 const Chunk& ch = op.dense_chunks[c];
-                EntrySpan sp{};
-                sp.i0 = fb.row0 + ch.rbeg;
-                sp.ni = ch.m;
-                sp.j0 = fb.col0;
-                sp.nj = fb.n;
-                sp.base = op.dense_off[k] + ch.off;
-                sp.gs = (int64_t)fb.n * ch.m8;
-                sp.is = 1;
-                sp.js = ch.m8;
-                spans.push_back(sp);
+                for (int ii = 0; ii < ch.m; ++ii)
+                    for (int e = op.sub_of_cluster_ptr[fb.sc]; e < op.sub_of_cluster_ptr[fb.sc + 1]; ++e) {
+                        const int sb = op.sub_of_cluster[e];
+                        RowItem it{};
+                        it.b = -1;
+                        it.i = fb.row0 + ch.rbeg + ii;
+                        it.col0 = op.sub_start[sb];
+                        it.n = op.sub_size[sb];
+                        it.tet0 = op.sub_tet_ptr[sb];
+                        it.ntet = op.sub_tet_ptr[sb + 1] - op.sub_tet_ptr[sb];
+                        it.out = op.dense_off[k] + ch.off + ii + (int64_t)(op.sub_start[sb] - fb.col0) * ch.m8;
+                        it.gs = (int64_t)fb.n * ch.m8;
+                        it.js = ch.m8;
+                        ritems.push_back(it);
+                    }
             }
         }
-        if ((rc = launch_spans<float, float>(op, spans, op.d_near, s, err))) return rc;
+        if ((rc = launch_rows(op, ritems, nullptr, op.d_near, s, err))) return rc;
+        for (int k = 0; k < op.n_near; ++k)
+            op.info.entries_evaluated += (int64_t)op.dense_blocks[k].m * op.dense_blocks[k].n;
     }
     RT_CUDA_TRY(cudaStreamSynchronize(s));
     cudaEventRecord(ev1, s);

@@ -88,6 +88,7 @@ int validate(const rt_problem* P, const rt_hparams* H)
         if (H->adm != RT_ADM_GAP && H->adm != RT_ADM_CENTER) return fail(RT_EINVAL, "adm must be RT_ADM_GAP or RT_ADM_CENTER");
     }
     if (H->gauss_pts < 1 || H->gauss_pts > rt::kMaxGauss) return fail(RT_EINVAL, "gauss_pts must be in [1, 32]");
+    if (H->line_eval != RT_LINE_CLOSED && H->line_eval != RT_LINE_NODES) return fail(RT_EINVAL, "line_eval");
     if (M.n_vert * (int64_t)M.n_vert * Fq.F > ((int64_t)1 << 40) && H->mode == RT_MODE_DENSE)
         return fail(RT_EINVAL, "dense operator too large");
     return RT_OK;
@@ -166,6 +167,7 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
         for (int64_t k = 0; k < N; ++k) op.plan.perm[k] = op.plan.iperm[k] = (int)k;
         op.plan.leaf_start.push_back(0);
         op.plan.leaf_size.push_back((int)N);
+        op.plan.clusters.push_back({0, (int)N, -1, -1});
     }
     const std::vector<int>& perm = op.plan.perm;
     const std::vector<int>& iperm = op.plan.iperm;
@@ -246,6 +248,8 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
     if ((rc = upload(op, &op.d_tvol32, tv32, err))) return rc;
     if ((rc = upload(op, &op.d_vt_ptr, cnt, err))) return rc;
     if ((rc = upload(op, &op.d_vt_idx, vt_idx, err))) return rc;
+    op.h_vt_ptr = std::move(cnt);
+    op.h_vt_idx = std::move(vt_idx);
     if ((rc = upload(op, &op.d_perm, perm, err))) return rc;
     if ((rc = upload(op, &op.d_iperm, iperm, err))) return rc;
     if ((rc = upload(op, &op.d_emit, emit, err))) return rc;
@@ -274,6 +278,7 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
         kp.cf[g] = (float)op.gc[g];
     }
     kp.ngauss = op.ngauss;
+    kp.line_closed = (H->line_eval == RT_LINE_CLOSED && op.ngauss >= 16) ? 1 : 0;
     kp.xyz32 = op.d_xyz32;
     kp.xyz64 = op.d_xyz64;
     kp.tet = op.d_tet;
@@ -300,6 +305,7 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
         op.info.ms_near = ms;
         op.n_near = 1;
     } else {
+        if ((rc = prepare_row_eval(op, err))) return rc;
         if ((rc = assemble_hmatrix(op, s, err))) return rc;
     }
     cudaEventDestroy(e0);

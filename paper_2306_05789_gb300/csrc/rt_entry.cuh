@@ -62,8 +62,31 @@ __device__ __forceinline__ float tet_w<float>(int q) { return c_tet_wf[q]; }
 template <>
 __device__ __forceinline__ double tet_w<double>(int q) { return c_tet_w[q]; }
 
-__device__ __forceinline__ float sinpi_r(float x) { return sinpif(x); }
-__device__ __forceinline__ double sinpi_r(double x) { return sinpi(x); }
+// sin(2 pi x) in FP32 for the sin-product kappa: 2x = n + t with n = rint(2x)
+// and t in [-1/2, 1/2], sin(pi (n + t)) = (-1)^n sin(pi t), and sin(pi t) by
+// its Taylor series through t^11 (truncation below 6e-8 for |t| <= 1/2).
+__device__ __forceinline__ float sin2pi(float x)
+{
+    constexpr double pi = kPi;
+    constexpr float c1 = (float)pi;
+    constexpr float c3 = (float)(-pi * pi * pi / 6.0);
+    constexpr float c5 = (float)(pi * pi * pi * pi * pi / 120.0);
+    constexpr float c7 = (float)(-pi * pi * pi * pi * pi * pi * pi / 5040.0);
+    constexpr float c9 = (float)(pi * pi * pi * pi * pi * pi * pi * pi * pi / 362880.0);
+    constexpr float c11 = (float)(-pi * pi * pi * pi * pi * pi * pi * pi * pi * pi * pi / 39916800.0);
+    const float r = 2.0f * x;
+    const float n = rintf(r);
+    const float t = r - n;
+    const float t2 = t * t;
+    float p = fmaf(c11, t2, c9);
+    p = fmaf(p, t2, c7);
+    p = fmaf(p, t2, c5);
+    p = fmaf(p, t2, c3);
+    p = fmaf(p, t2, c1);
+    const float v = p * t;
+    return (((int)n) & 1) ? -v : v;
+}
+__device__ __forceinline__ double sin2pi(double x) { return sinpi(2.0 * x); }
 __device__ __forceinline__ float exp_r(float x) { return expf(x); }
 __device__ __forceinline__ double exp_r(double x) { return exp(x); }
 __device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
@@ -135,8 +158,36 @@ __device__ __forceinline__ R kappa_at(const KernelParams& P, R x, R y, R z)
 {
     R k = kp_k0<R>(P);
     if (P.kappa_kind == RT_KAPPA_SINPROD)
-        k += kp_amp<R>(P) * sinpi_r(R(2) * x) * sinpi_r(R(2) * y) * sinpi_r(R(2) * z);
+        k += kp_amp<R>(P) * sin2pi(x) * sin2pi(y) * sin2pi(z);
     return k;
+}
+
+// sin(pi s) / (pi s) in FP32
+__device__ __forceinline__ float sinc_pi(float s)
+{
+    const float ps = (float)kPi * s;
+    if (fabsf(s) < 1e-3f) {
+        const float p2 = ps * ps;
+        return 1.f - p2 * (1.f / 6.f) + p2 * p2 * (1.f / 120.f);
+    }
+    return sin2pi(0.5f * s) / ps;
+}
+
+// The Gauss sum sum_g w_g kappa(a + u_g d) for kappa = k0 + amp sin(2 pi x)
+// sin(2 pi y) sin(2 pi z), evaluated exactly: sinA sinB sinC =
+// 1/4 [sin(A+B-C) + sin(B+C-A) + sin(C+A-B) - sin(A+B+C)] turns the samples
+// into four sinusoids sin(alpha + beta u) of the node u, and for a rule
+// symmetric about 1/2, sum_g w_g sin(alpha + beta u_g) = sin(alpha + beta/2)
+// C(beta) with C(beta) = sum_g w_g cos(beta (u_g - 1/2)).  C equals
+// sin(beta/2)/(beta/2) up to the rule's error on cos, below 2e-14 for n >= 16
+// nodes and |beta| <= 6 pi, i.e. |dx| + |dy| + |dz| <= 3.
+__device__ __forceinline__ float gauss_sum_sinprod(const KernelParams& P, const Vec3<float>& a, float dx, float dy,
+                                                   float dz)
+{
+    const float mx = a.x + 0.5f * dx, my = a.y + 0.5f * dy, mz = a.z + 0.5f * dz;
+    const float S = sin2pi(mx + my - mz) * sinc_pi(dx + dy - dz) + sin2pi(-mx + my + mz) * sinc_pi(-dx + dy + dz) +
+                    sin2pi(mx - my + mz) * sinc_pi(dx - dy + dz) - sin2pi(mx + my + mz) * sinc_pi(dx + dy + dz);
+    return P.k0f + 0.25f * P.ampf * S;
 }
 
 // int_[a,b] kappa = |b-a| sum_g (w_g/2) kappa(a + u_g (b-a)).  For constant
@@ -147,6 +198,9 @@ __device__ __forceinline__ R optical_depth(const KernelParams& P, const Vec3<R>&
     R dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
     R L = sqrt_r(dx * dx + dy * dy + dz * dz);
     if (P.kappa_kind != RT_KAPPA_SINPROD) return kp_k0<R>(P) * L;
+    if constexpr (sizeof(R) == 4) {
+        if (P.line_closed && fabsf(dx) + fabsf(dy) + fabsf(dz) <= 3.0f) return L * gauss_sum_sinprod(P, a, dx, dy, dz);
+    }
     R s = R(0);
     for (int g = 0; g < P.ngauss; ++g) {
         R u = gauss_u<R>(P, g);

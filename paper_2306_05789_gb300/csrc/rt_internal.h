@@ -25,6 +25,7 @@ namespace rt {
 
 constexpr int kMaxGroups = 64;
 constexpr int kMaxGauss = 32;
+constexpr int kSubCols = 256;   // columns per sub-cluster in row evaluations
 constexpr double kPi = 3.14159265358979323846;
 
 struct alignas(16) dbl4 {
@@ -46,6 +47,7 @@ struct KernelParams {
     double c[kMaxGroups];
     float cf[kMaxGroups];
     int ngauss;
+    int line_closed;    // closed-form Gauss sums for the sin-product kappa (FP32 paths)
     // Gauss-Legendre nodes mapped to [0,1] (u = (1+t)/2) and half weights
     float gu32[kMaxGauss], gw32[kMaxGauss];
     double gu64[kMaxGauss], gw64[kMaxGauss];
@@ -72,6 +74,12 @@ struct EntrySpan {
 // One far (admissible) block in tree order.
 struct FarBlock {
     int row0, m, col0, n;
+    int tc, sc;   // row and column cluster ids in Plan::clusters
+};
+
+// Node of the cluster tree: points [start, start + size) in tree order.
+struct ClusterNode {
+    int start, size, left, right;
 };
 
 inline int round8(int x) { return (x + 7) & ~7; }
@@ -90,6 +98,7 @@ struct Plan {
     std::vector<int> perm;      // tree position -> original vertex id
     std::vector<int> iperm;     // original vertex id -> tree position
     std::vector<int> leaf_start, leaf_size;   // leaves in tree order
+    std::vector<ClusterNode> clusters;        // every node of the cluster tree (0 = root)
     std::vector<FarBlock> near_blocks;        // dense leaf blocks
     std::vector<FarBlock> far_blocks;         // admissible blocks
 };
@@ -184,6 +193,12 @@ struct Operator {
     // frequency tables on device
     double* d_fq = nullptr;     // [F][4]: nu, w*c*(1-a), a, group
     int* d_fq_group = nullptr;  // [F] group of each frequency
+    // row evaluation over column clusters: sub-clusters of at most kSubCols
+    // columns, each with the list of tetrahedra touching its vertices (CSR)
+    std::vector<int> sub_of_cluster_ptr, sub_of_cluster;   // per cluster: its sub-clusters
+    std::vector<int> sub_start, sub_size, sub_tet_ptr;     // per sub-cluster
+    int* d_sub_tets = nullptr;
+    std::vector<int> h_vt_ptr, h_vt_idx;                   // host copy of the vertex -> tetrahedra CSR
     // stats
     rt_info info{};
     std::vector<void*> allocations;
@@ -195,6 +210,7 @@ void gauss_legendre_nodes(int n, std::vector<double>& t, std::vector<double>& w)
 int assemble_dense(Operator& op, cudaStream_t s, std::string& err);
 int assemble_source(Operator& op, cudaStream_t s, std::string& err);
 int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err);
+int prepare_row_eval(Operator& op, std::string& err);
 int eval_entries(Operator& op, int group, int64_t count, const int32_t* rows, const int32_t* cols, double* out,
                  cudaStream_t s, std::string& err);
 int hmatvec_prepare(Operator& op, std::string& err);

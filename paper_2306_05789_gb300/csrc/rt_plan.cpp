@@ -94,12 +94,12 @@ void block_recursion(const std::vector<Cluster>& cl, double eta, int adm, int t,
     if (adm == RT_ADM_GAP) d -= T.R + S.R;
     const bool admissible = d > 0.0 && std::max(T.R, S.R) < eta * d;
     if (admissible) {
-        farb.push_back({T.start, T.size, S.start, S.size});
+        farb.push_back({T.start, T.size, S.start, S.size, t, s});
         return;
     }
     bool tl = T.left < 0, sl = S.left < 0;
     if (tl && sl) {
-        nearb.push_back({T.start, T.size, S.start, S.size});
+        nearb.push_back({T.start, T.size, S.start, S.size, t, s});
         return;
     }
     if (tl) {
@@ -149,6 +149,8 @@ int plan_build(const double* xyz, int64_t n, int leaf, double eta, int adm, Plan
     out.perm = B.idx;
     out.iperm.assign(n, 0);
     for (int64_t k = 0; k < n; ++k) out.iperm[out.perm[k]] = (int)k;
+    out.clusters.reserve(B.cl.size());
+    for (const Cluster& C : B.cl) out.clusters.push_back({C.start, C.size, C.left, C.right});
     for (const Cluster& C : B.cl)
         if (C.left < 0) {
             out.leaf_start.push_back(C.start);

@@ -55,10 +55,11 @@ def rel_l2(a, b):
 # ---------------------------------------------------------------------------
 # entries and source
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("prec", [rt.RT_PREC_F64, rt.RT_PREC_F32])
-def test_entries_match_oracle_rows(prec):
+@pytest.mark.parametrize("prec,line", [(rt.RT_PREC_F64, rt.RT_LINE_NODES), (rt.RT_PREC_F32, rt.RT_LINE_CLOSED),
+                                       (rt.RT_PREC_F32, rt.RT_LINE_NODES)])
+def test_entries_match_oracle_rows(prec, line):
     p = W.cube_problem(7, W.sinprod_kappa(0.5), W.midpoint_freqs(3, albedo=0.3), R0=0.5)
-    op = rt.rt_build_operator(p, dense_hp(prec))
+    op = rt.rt_build_operator(p, rt.hparams(mode=rt.RT_MODE_DENSE, prec=prec, line_eval=line))
     rows = np.array([0, 3, 48, 171, 342], dtype=np.int32)
     R = O.G_rows(p, rows)                      # [r, G, N]
     c, _ = O.groups_of(p.freqs)
@@ -90,6 +91,21 @@ def test_source_matches_oracle(prec):
     else:
         np.testing.assert_allclose(got, ref, rtol=2e-5, atol=1e-6 * np.abs(ref).max())
     op.free()
+
+
+def test_closed_form_and_node_sums_agree_in_fp32():
+    """The two evaluations of the Gauss sums give the same H-matrix apply to FP32 rounding."""
+    p = W.cube_problem(10, W.sinprod_kappa(0.5), W.midpoint_freqs(2, albedo=0.3), R0=0.5)
+    X = torch.tensor(W.rand_vectors((2, p.N), seed=5), dtype=torch.float32, device=DEV)
+    Ys = []
+    for line in (rt.RT_LINE_CLOSED, rt.RT_LINE_NODES):
+        op = rt.rt_build_operator(p, rt.hparams(leaf=32, line_eval=line))
+        Y = torch.zeros_like(X)
+        op.apply(X, Y)
+        torch.cuda.synchronize()
+        Ys.append(Y.cpu().numpy())
+        op.free()
+    assert rel_l2(Ys[0], Ys[1]) < 2e-5
 
 
 def test_source_grey_with_emitter_and_wall_vertices():
@@ -186,6 +202,22 @@ def test_hmatrix_apply_matches_dense_oracle(n, leaf, F):
         ref = O.DenseOperator(p).apply(X)
         err = rel_l2(Y.cpu().numpy(), ref)
         assert err < 1e-4, (kind, err, info)
+    op.free()
+
+
+def test_single_dense_leaf_matches_oracle_to_fp32():
+    """A mesh that fits in one leaf is one dense block, filled by the row-over-cluster
+    evaluation (each tetrahedron's quadrature points shared by its vertices): FP32 accuracy."""
+    p = W.cube_problem(5, W.sinprod_kappa(0.5), W.midpoint_freqs(3, albedo=0.3), R0=0.5)
+    op = rt.rt_build_operator(p, rt.hparams(leaf=128))
+    info = op.info()
+    assert info["n_far"] == 0 and info["n_near"] == 1
+    X = W.rand_vectors((3, p.N), seed=4)
+    Xd = torch.tensor(X, dtype=torch.float32, device=DEV)
+    Y = torch.zeros_like(Xd)
+    op.apply(Xd, Y)
+    torch.cuda.synchronize()
+    assert rel_l2(Y.cpu().numpy(), O.DenseOperator(p).apply(X)) < 2e-6
     op.free()
 
 
