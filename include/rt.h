@@ -137,6 +137,9 @@ typedef struct {
     int rank_max;    /* ACA rank limit before a block is stored dense (0 = 512) */
     int adm;         /* RT_ADM_GAP (default) or RT_ADM_CENTER */
     int line_eval;   /* RT_LINE_CLOSED (default) or RT_LINE_NODES (FP32 paths) */
+    int refine;      /* with a BF16/FP16 far field: also keep an FP32 copy for refinement sweeps */
+    int tensor_cores; /* 0: use the tcgen05 apply when eligible (one operator group, F a multiple
+                         of 16 up to 256, BF16/FP16 far field, leaves <= 128); 1: CUDA cores only */
 } rt_hparams;
 
 typedef struct rt_operator rt_operator;
@@ -166,6 +169,9 @@ typedef struct {
     double T0;
     int use_J0;
     int use_graph;   /* capture check_every iterations in a CUDA graph */
+    double refine_tol; /* operator built with refine: iterate on the BF16/FP16 far field until the
+                          residual is <= refine_tol, then on the FP32 copy down to tol (0: FP32 copy
+                          from the start) */
 } rt_solve_opts;
 
 typedef struct {

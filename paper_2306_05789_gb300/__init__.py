@@ -59,7 +59,7 @@ class RtProblem(ctypes.Structure):
 class RtHparams(ctypes.Structure):
     _fields_ = [("mode", _c_int), ("prec", _c_int), ("far_prec", _c_int), ("aca_eps", _c_dbl), ("leaf", _c_int),
                 ("eta", _c_dbl), ("gauss_pts", _c_int), ("rank_max", _c_int), ("adm", _c_int),
-                ("line_eval", _c_int)]
+                ("line_eval", _c_int), ("refine", _c_int), ("tensor_cores", _c_int)]
 
 
 class RtInfo(ctypes.Structure):
@@ -77,7 +77,7 @@ class RtInfo(ctypes.Structure):
 
 class RtSolveOpts(ctypes.Structure):
     _fields_ = [("tol", _c_dbl), ("max_iter", _c_int), ("check_every", _c_int), ("T0", _c_dbl), ("use_J0", _c_int),
-                ("use_graph", _c_int)]
+                ("use_graph", _c_int), ("refine_tol", _c_dbl)]
 
 
 class RtSolveStats(ctypes.Structure):
@@ -143,10 +143,11 @@ def _stream_ptr(stream):
 
 
 def hparams(mode=RT_MODE_HMATRIX, prec=None, far_prec=RT_PREC_F32, aca_eps=1e-4, leaf=64, eta=2.0, gauss_pts=16,
-            rank_max=0, adm=RT_ADM_GAP, line_eval=RT_LINE_CLOSED) -> RtHparams:
+            rank_max=0, adm=RT_ADM_GAP, line_eval=RT_LINE_CLOSED, refine=0, tensor_cores=0) -> RtHparams:
     if prec is None:
         prec = RT_PREC_F32
-    return RtHparams(mode, prec, far_prec, aca_eps, leaf, eta, gauss_pts, rank_max, adm, line_eval)
+    return RtHparams(mode, prec, far_prec, aca_eps, leaf, eta, gauss_pts, rank_max, adm, line_eval, refine,
+                     tensor_cores)
 
 
 class _ProblemArgs:
@@ -215,10 +216,10 @@ class Operator:
                                      _P(cols.data_ptr()), _P(out.data_ptr()), _stream_ptr(stream)))
 
     def solve_fixed_point(self, J, T, tol=1e-10, max_iter=500, check_every=1, T0=0.0, use_J0=False,
-                          use_graph=True, stream=None, raise_on_noconv=True) -> dict:
+                          use_graph=True, stream=None, raise_on_noconv=True, refine_tol=0.0) -> dict:
         """rt_solve_fixed_point: J [F, N] and T [N] (float64) receive the final iterate."""
         o = RtSolveOpts(float(tol), int(max_iter), int(check_every), float(T0), 1 if use_J0 else 0,
-                        1 if use_graph else 0)
+                        1 if use_graph else 0, float(refine_tol))
         st = RtSolveStats()
         rc = lib().rt_solve_fixed_point(self.h, ctypes.byref(o), _P(J.data_ptr()), _P(T.data_ptr()),
                                         ctypes.byref(st), _stream_ptr(stream))

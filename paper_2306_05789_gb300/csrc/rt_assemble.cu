@@ -1316,6 +1316,17 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
             aca_pack<__nv_bfloat16><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, (__nv_bfloat16*)d);
         else aca_pack<__half><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, (__half*)d);
         RT_CUDA_TRY(cudaGetLastError());
+        if (op.refine && op.far_prec != RT_PREC_F32) {
+            // FP32 copy of the far field in the same layout, for refinement sweeps
+            if ((rc = dev_alloc(op, &op.d_far32, (size_t)far_elems, err))) {
+                if (pool) cudaFree(pool);
+                cleanup();
+                return rc;
+            }
+            RT_CUDA_TRY(cudaMemsetAsync(op.d_far32, 0, sizeof(float) * (size_t)far_elems, s));
+            aca_pack<float><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, op.d_far32);
+            RT_CUDA_TRY(cudaGetLastError());
+        }
         RT_CUDA_TRY(cudaStreamSynchronize(s));
         cudaFree(d_items);
         cudaFree(d_chunks);

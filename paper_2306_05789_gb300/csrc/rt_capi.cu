@@ -124,6 +124,8 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
     op.leaf = H->leaf;
     op.eta = H->eta;
     op.adm = H->adm;
+    op.tc_off = H->tensor_cores == 1;
+    op.refine = H->mode == RT_MODE_HMATRIX && H->refine && H->far_prec != RT_PREC_F32;
     op.ngauss = H->gauss_pts;
     op.rank_max = H->rank_max > 0 ? H->rank_max : 512;
     op.grey = P->grey ? 1 : 0;

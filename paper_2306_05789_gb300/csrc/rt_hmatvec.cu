@@ -423,6 +423,9 @@ int hmatvec_prepare(Operator& op, std::string& err)
     for (int b = 0; b < op.n_near; ++b) near_e += (int64_t)op.dense_blocks[b].m * op.dense_blocks[b].n;
     op.info.apply_bytes = F * (far_e * esz_far + near_e * 4) + 2 * F * N * (int64_t)esz;
     op.info.apply_flops = 2 * F * (far_e + near_e);
+    if ((rc = tc_prepare(op, err))) return rc;
+    if (op.tc_enabled)   // one operator serves all F right-hand sides: its data is read once per apply
+        op.info.apply_bytes = far_e * esz_far + near_e * 4 + 2 * F * N * (int64_t)esz;
     return RT_OK;
 }
 
@@ -430,29 +433,31 @@ int hmatvec_prepare(Operator& op, std::string& err)
 static int launch_hmv(Operator& op, const float* x, float* w, float* y, cudaStream_t s, std::string& err)
 {
     const int N = op.N, F = op.F;
+    const int far_prec = (op.use_far32 && op.d_far32) ? RT_PREC_F32 : op.far_prec;
+    const void* farp = (op.use_far32 && op.d_far32) ? (const void*)op.d_far32 : op.d_far;
     const P1Item* it = (const P1Item*)op.d_p1_items;
     const P1Row* rw = (const P1Row*)op.d_p1_rows;
     if (op.n_p1 > 0) {
         dim3 g1(op.n_p1, F);
-        if (op.far_prec == RT_PREC_F32)
-            hmv_phase1<float><<<g1, 256, 0, s>>>(it, rw, (const float*)op.d_far, x, w, N, op.d_fq_group);
-        else if (op.far_prec == RT_PREC_BF16)
-            hmv_phase1<__nv_bfloat16><<<g1, 256, 0, s>>>(it, rw, (const __nv_bfloat16*)op.d_far, x, w, N,
+        if (far_prec == RT_PREC_F32)
+            hmv_phase1<float><<<g1, 256, 0, s>>>(it, rw, (const float*)farp, x, w, N, op.d_fq_group);
+        else if (far_prec == RT_PREC_BF16)
+            hmv_phase1<__nv_bfloat16><<<g1, 256, 0, s>>>(it, rw, (const __nv_bfloat16*)farp, x, w, N,
                                                          op.d_fq_group);
         else
-            hmv_phase1<__half><<<g1, 256, 0, s>>>(it, rw, (const __half*)op.d_far, x, w, N, op.d_fq_group);
+            hmv_phase1<__half><<<g1, 256, 0, s>>>(it, rw, (const __half*)farp, x, w, N, op.d_fq_group);
         RT_CUDA_TRY(cudaGetLastError());
     }
     dim3 g2(op.n_p2, F);
     const P2Leaf* lv = (const P2Leaf*)op.d_p2_leaf;
     const P2Seg* sg = (const P2Seg*)op.d_p2_segs;
-    if (op.far_prec == RT_PREC_F32)
-        hmv_phase2<float><<<g2, 256, 0, s>>>(lv, sg, (const float*)op.d_far, op.d_near, x, w, y, N, op.d_fq_group);
-    else if (op.far_prec == RT_PREC_BF16)
-        hmv_phase2<__nv_bfloat16><<<g2, 256, 0, s>>>(lv, sg, (const __nv_bfloat16*)op.d_far, op.d_near, x, w, y, N,
+    if (far_prec == RT_PREC_F32)
+        hmv_phase2<float><<<g2, 256, 0, s>>>(lv, sg, (const float*)farp, op.d_near, x, w, y, N, op.d_fq_group);
+    else if (far_prec == RT_PREC_BF16)
+        hmv_phase2<__nv_bfloat16><<<g2, 256, 0, s>>>(lv, sg, (const __nv_bfloat16*)farp, op.d_near, x, w, y, N,
                                                      op.d_fq_group);
     else
-        hmv_phase2<__half><<<g2, 256, 0, s>>>(lv, sg, (const __half*)op.d_far, op.d_near, x, w, y, N,
+        hmv_phase2<__half><<<g2, 256, 0, s>>>(lv, sg, (const __half*)farp, op.d_near, x, w, y, N,
                                               op.d_fq_group);
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
@@ -476,6 +481,7 @@ static int launch_dense(Operator& op, const void* X, void* Y, cudaStream_t s, st
 int apply_tree(Operator& op, const void* X, void* Y, cudaStream_t s, std::string& err)
 {
     if (op.mode == RT_MODE_DENSE) return launch_dense(op, X, Y, s, err);
+    if (op.tc_enabled && !op.use_far32) return tc_apply(op, (const float*)X, (float*)Y, s, err);
     return launch_hmv(op, (const float*)X, op.d_w, (float*)Y, s, err);
 }
 

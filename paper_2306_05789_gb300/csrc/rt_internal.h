@@ -174,6 +174,9 @@ struct Operator {
     std::vector<int> dense_chunk_ptr, far_chunk_ptr;   // CSR over the chunk arrays
     std::vector<Chunk> dense_chunks, far_chunks;
     void* d_far = nullptr;      // far U/V (float, bf16 or f16)
+    float* d_far32 = nullptr;   // FP32 copy of a BF16/FP16 far field (refinement), same layout
+    int refine = 0;
+    int use_far32 = 0;          // apply with the FP32 copy (set by the solver)
     std::vector<int64_t> far_v_off, far_u_off;
     // matvec work lists (device)
     void* d_p1_items = nullptr; int n_p1 = 0;
@@ -199,6 +202,15 @@ struct Operator {
     std::vector<int> sub_start, sub_size, sub_tet_ptr;     // per sub-cluster
     int* d_sub_tets = nullptr;
     std::vector<int> h_vt_ptr, h_vt_idx;                   // host copy of the vertex -> tetrahedra CSR
+    // tensor-core multi-right-hand-side apply (one operator group, F % 16 == 0)
+    int tc_enabled = 0;
+    int tc_off = 0;     // tensor cores disabled by the caller
+    void *tc_blocks = nullptr, *tc_leaf_far = nullptr, *tc_leaf_near = nullptr;
+    void *tc_segs_far = nullptr, *tc_segs_near = nullptr, *tc_xsplit = nullptr;
+    int tc_nblocks = 0;
+    int64_t tc_wlen = 0;
+    float* tc_w = nullptr;
+    int* tc_err = nullptr;
     // stats
     rt_info info{};
     std::vector<void*> allocations;
@@ -220,6 +232,9 @@ int permute_vectors(Operator& op, const void* in, void* out, int to_tree, int is
 // rt_apply with its scratch in a file-scope device array (no allocation)
 int apply_noalloc(Operator& op, const void* X, void* Y, cudaStream_t s, std::string& err);
 size_t apply_noalloc_limit();
+int tc_prepare(Operator& op, std::string& err);
+int tc_apply(Operator& op, const float* X, float* Y, cudaStream_t s, std::string& err);
+int tc_check_error(Operator& op, std::string& err);
 int solve_fixed_point(Operator& op, const rt_solve_opts& o, void* J, double* T, rt_solve_stats& st,
                       cudaStream_t s, std::string& err);
 

@@ -270,11 +270,14 @@ static int solve_impl(Operator& op, const rt_solve_opts& o, void* J_out, double*
     double last = INFINITY;
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
-    int graph_len = 0;
+    int graph_len = 0, graph_far32 = -1;
+    // operators with an FP32 refinement copy start on the low-precision far
+    // field and switch once the residual reaches refine_tol
+    op.use_far32 = (op.d_far32 && !(o.refine_tol > 0.0)) ? 1 : 0;
     while (iters < cap && !converged) {
         const int todo = std::min(every, cap - iters);
         if (o.use_graph) {
-            if (!gexec || graph_len != todo) {
+            if (!gexec || graph_len != todo || graph_far32 != op.use_far32) {
                 if (gexec) cudaGraphExecDestroy(gexec);
                 if (graph) cudaGraphDestroy(graph);
                 gexec = nullptr;
@@ -294,6 +297,7 @@ static int solve_impl(Operator& op, const rt_solve_opts& o, void* J_out, double*
                 }
                 RT_CUDA_TRY(cudaGraphInstantiate(&gexec, graph, 0));
                 graph_len = todo;
+                graph_far32 = op.use_far32;
             }
             RT_CUDA_TRY(cudaGraphLaunch(gexec, s));
         } else {
@@ -304,12 +308,14 @@ static int solve_impl(Operator& op, const rt_solve_opts& o, void* J_out, double*
         RT_CUDA_TRY(cudaStreamSynchronize(s));
         for (int k = 0; k < todo; ++k) {
             last = hres[iters + k];
-            if (last <= o.tol) converged = true;
+            if (last <= o.tol && (!op.d_far32 || op.use_far32)) converged = true;
         }
         iters += todo;
+        if (op.d_far32 && !op.use_far32 && last <= std::max(o.refine_tol, o.tol)) op.use_far32 = 1;
     }
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
+    op.use_far32 = 0;
     int fail = 0;
     RT_CUDA_TRY(cudaMemcpyAsync(&fail, d_ctr + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
     // results back to caller order
