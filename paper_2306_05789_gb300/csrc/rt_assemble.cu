@@ -985,20 +985,49 @@ struct PackItem {
     int c0, c1;     // chunk range [c0, c1) in the chunk array
 };
 
+// Each rank-1 term u v^T is stored as (s u)(v / s) with s chosen so that both
+// factors have the same largest magnitude (s = 1 for FP32): the product is
+// unchanged and 16-bit storage keeps both factors away from the subnormals.
 template <class T>
 __global__ void aca_pack(AcaDev D, const PackItem* items, int nitems, const Chunk* chunks, T* dst)
 {
+    __shared__ float red[2][32];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const PackItem p = items[it];
         const int64_t us = D.uoff[(int64_t)p.b * D.rmax + p.l], vs = D.voff[(int64_t)p.b * D.rmax + p.l];
         for (int g = 0; g < D.G; ++g) {
+            float su = 1.f;
+            if (sizeof(T) == 2) {
+                float mu = 0.f, mv = 0.f;
+                for (int i = threadIdx.x; i < p.m; i += blockDim.x) mu = fmaxf(mu, fabsf(D.pool[us + (int64_t)g * p.m + i]));
+                for (int j = threadIdx.x; j < p.n; j += blockDim.x) mv = fmaxf(mv, fabsf(D.pool[vs + (int64_t)g * p.n + j]));
+                for (int o = 16; o > 0; o >>= 1) {
+                    mu = fmaxf(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+                    mv = fmaxf(mv, __shfl_xor_sync(0xffffffffu, mv, o));
+                }
+                if ((threadIdx.x & 31) == 0) {
+                    red[0][threadIdx.x >> 5] = mu;
+                    red[1][threadIdx.x >> 5] = mv;
+                }
+                __syncthreads();
+                mu = 0.f;
+                mv = 0.f;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                    mu = fmaxf(mu, red[0][w]);
+                    mv = fmaxf(mv, red[1][w]);
+                }
+                __syncthreads();
+                if (mu > 0.f && mv > 0.f) su = sqrtf(mv / mu);
+            }
+            const float sv = 1.f / su;
             for (int j = threadIdx.x; j < p.n; j += blockDim.x)
-                dst[p.voff_dst + ((int64_t)g * p.r + p.l) * p.n8 + j] = to_store<T>(D.pool[vs + (int64_t)g * p.n + j]);
+                dst[p.voff_dst + ((int64_t)g * p.r + p.l) * p.n8 + j] =
+                    to_store<T>(sv * D.pool[vs + (int64_t)g * p.n + j]);
             for (int c = p.c0; c < p.c1; ++c) {
                 const Chunk ch = chunks[c];
                 for (int i = threadIdx.x; i < ch.m; i += blockDim.x)
                     dst[p.uoff_dst + ch.off + ((int64_t)g * p.r + p.l) * ch.m8 + i] =
-                        to_store<T>(D.pool[us + (int64_t)g * p.m + ch.rbeg + i]);
+                        to_store<T>(su * D.pool[us + (int64_t)g * p.m + ch.rbeg + i]);
             }
         }
     }

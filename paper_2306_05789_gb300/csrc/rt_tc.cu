@@ -145,6 +145,28 @@ __device__ __forceinline__ void st16(unsigned char* tile, int row, int k, T v)
     *reinterpret_cast<T*>(tile + tile_off(row, k)) = v;
 }
 
+// Copy rows [0, nrows) x 16-byte chunks [0, 8) of a K-major tile from global
+// memory (row r, chunk c at src + r * ld + 8 c elements; zero where the
+// predicate fails).  A warp handles 8 rows x 4 chunks per step, so each group
+// of 8 consecutive lanes stores 8 different rows of one chunk: 8 distinct
+// 16-byte bank groups in the no-swizzle layout (no conflicts), while every
+// row contributes a 64-byte contiguous run to the global load.
+template <class T, class Pred>
+__device__ __forceinline__ void stage_rows(unsigned char* tile, int nrows, const T* __restrict__ src, int64_t ld,
+                                           Pred valid)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int r_in = lane & 7, c_in = lane >> 3;
+    const int steps = (nrows >> 3) * 2;   // (8-row group, chunk half) pairs
+    for (int st = warp; st < steps; st += nw) {
+        const int row = (st >> 1) * 8 + r_in;
+        const int c = (st & 1) * 4 + c_in;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (valid(row, c)) v = __ldg(reinterpret_cast<const uint4*>(src + (int64_t)row * ld + 8 * c));
+        *reinterpret_cast<uint4*>(tile + tile_off(row, 8 * c)) = v;
+    }
+}
+
 }  // namespace tc
 
 // X (FP32, tree order, [F][N]) -> high and low 16-bit parts
@@ -161,16 +183,18 @@ __global__ void tc_split_kernel(const float* __restrict__ X, T* __restrict__ hi,
 
 struct TcBlock {
     int64_t v;      // element offset of V^T [r][n8]
-    int64_t w;      // w_base: W[f][r] at w + f*r + k
-    int n, n8, col0, r;
+    int64_t w;      // offset of the block's W16 [F][r16] (hi and lo arrays)
+    int n, n8, col0, r, r16, pad;
 };
 
-// phase 1: persistent CTAs walk the far blocks; one block = ceil(r/128) M tiles
+// phase 1: persistent CTAs walk the far blocks; one block = ceil(r/128) M tiles.
+// W_b = V_b^T X_c is written as 16-bit high and low parts, [F][r16] per block.
 template <class T>
 __global__ void __launch_bounds__(tc::kThreads) tc_phase1(const TcBlock* __restrict__ blocks, int nblocks,
                                                           const T* __restrict__ far, const T* __restrict__ xhi,
-                                                          const T* __restrict__ xlo, float* __restrict__ W, int N,
-                                                          int F, int* __restrict__ err)
+                                                          const T* __restrict__ xlo, T* __restrict__ whi,
+                                                          T* __restrict__ wlo, int N, int F, int xaligned,
+                                                          int* __restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     // [A: 128 x 64 | B_hi: F x 64 | B_lo: F x 64]
@@ -201,33 +225,51 @@ __global__ void __launch_bounds__(tc::kThreads) tc_phase1(const TcBlock* __restr
             const int mr = min(tc::kM, B.r - m0);
             int first = 1;
             for (int k0 = 0; k0 < B.n && ok; k0 += tc::kKT) {
-                // stage A: rows m0..m0+127 of V^T, columns k0..k0+63 (zero outside)
-                for (int e = tid; e < tc::kM * (tc::kKT / 8); e += tc::kThreads) {
-                    const int row = e >> 3, c = (e & 7) * 8, col = k0 + c;
-                    uint4 v = make_uint4(0, 0, 0, 0);
-                    if (row < mr && col < B.n8)
-                        v = *reinterpret_cast<const uint4*>(far + B.v + (int64_t)(m0 + row) * B.n8 + col);
-                    *reinterpret_cast<uint4*>(sA + tc::tile_off(row, c)) = v;
-                }
-                // stage B: right-hand side f, columns k0..k0+63 of the block (zero beyond n)
-                for (int e = tid; e < F * tc::kKT; e += tc::kThreads) {
-                    const int f = e / tc::kKT, c = e % tc::kKT, col = k0 + c;
-                    T h = tc::to16<T>(0.f), l = tc::to16<T>(0.f);
-                    if (col < B.n) {
-                        const int64_t idx = (int64_t)f * N + B.col0 + col;
-                        h = xhi[idx];
-                        l = xlo[idx];
+                // A: rows m0.. of V^T, columns k0..k0+63 (V rows are zero-padded to n8)
+                tc::stage_rows<T>(sA, tc::kM, far + B.v + (int64_t)m0 * B.n8 + k0, B.n8,
+                                  [&](int row, int c) { return row < mr && k0 + 8 * c < B.n8; });
+                // B: right-hand side f, columns k0..k0+63 of the block (zero beyond n)
+                if (xaligned && (B.col0 & 7) == 0) {   // 16-byte loads need 8-element aligned row starts
+                    const T* bh = xhi + B.col0 + k0;
+                    const T* bl = xlo + B.col0 + k0;
+                    const int full = (B.n - k0) >> 3;   // whole 8-element chunks inside the block
+                    tc::stage_rows<T>(sBh, F, bh, N, [&](int, int c) { return c < full; });
+                    tc::stage_rows<T>(sBl, F, bl, N, [&](int, int c) { return c < full; });
+                    // a partial last chunk (n not a multiple of 8): element-wise, after the
+                    // zero fill of that chunk above
+                    if (((B.n - k0) & 7) && full < 8) {
+                        __syncthreads();
+                        for (int e = tid; e < F * 8; e += tc::kThreads) {
+                            const int f = e >> 3, j = e & 7, col = k0 + 8 * full + j;
+                            T h = tc::to16<T>(0.f), l = tc::to16<T>(0.f);
+                            if (col < B.n) {
+                                h = xhi[(int64_t)f * N + B.col0 + col];
+                                l = xlo[(int64_t)f * N + B.col0 + col];
+                            }
+                            tc::st16<T>(sBh, f, 8 * full + j, h);
+                            tc::st16<T>(sBl, f, 8 * full + j, l);
+                        }
                     }
-                    tc::st16<T>(sBh, f, c, h);
-                    tc::st16<T>(sBl, f, c, l);
+                } else {
+                    for (int e = tid; e < F * tc::kKT; e += tc::kThreads) {
+                        const int f = e % F, c = e / F, col = k0 + c;
+                        T h = tc::to16<T>(0.f), l = tc::to16<T>(0.f);
+                        if (col < B.n) {
+                            const int64_t idx = (int64_t)f * N + B.col0 + col;
+                            h = xhi[idx];
+                            l = xlo[idx];
+                        }
+                        tc::st16<T>(sBh, f, c, h);
+                        tc::st16<T>(sBl, f, c, l);
+                    }
                 }
                 tc::fence_async_smem();
                 __syncthreads();
                 if (tid == 0) {
                     tc::tc_fence_after();
                     const uint32_t a0 = tc::smem_addr(sA), bh0 = tc::smem_addr(sBh), bl0 = tc::smem_addr(sBl);
-#pragma unroll
-                    for (int ks = 0; ks < tc::kKT / 16; ++ks) {
+                    const int nks = (min(tc::kKT, B.n - k0) + 15) / 16;
+                    for (int ks = 0; ks < nks; ++ks) {
                         const uint64_t da = tc::sdesc(a0 + ks * 2 * lbo, lbo, sbo);
                         tc::mma_f16(tmem, da, tc::sdesc(bh0 + ks * 2 * lbo, lbo, sbo), idesc, first ? 0u : 1u);
                         first = 0;
@@ -245,14 +287,19 @@ __global__ void __launch_bounds__(tc::kThreads) tc_phase1(const TcBlock* __restr
                 }
             }
             if (!ok) break;
-            // epilogue: thread of warp q holds TMEM lane (row) 32q + lane
+            // epilogue: thread of warp q holds TMEM lane (row k) 32q + lane; write W as hi + lo
             const int row = warp * 32 + lane;
             for (int c0 = 0; c0 < F; c0 += 16) {
                 float v[16];
                 tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
                 if (row < mr) {
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) W[B.w + (int64_t)(c0 + k) * B.r + m0 + row] = v[k];
+                    for (int k = 0; k < 16; ++k) {
+                        const T h = tc::to16<T>(v[k]);
+                        const int64_t idx = B.w + (int64_t)(c0 + k) * B.r16 + m0 + row;
+                        whi[idx] = h;
+                        wlo[idx] = tc::to16<T>(v[k] - tc::from16(h));
+                    }
                 }
             }
             tc::tc_fence_before();
@@ -265,8 +312,8 @@ __global__ void __launch_bounds__(tc::kThreads) tc_phase1(const TcBlock* __restr
 
 struct TcSeg {
     int64_t u;      // element offset of the chunk U^T [r][m8]
-    int64_t w;      // w_base of the block
-    int r, pad;
+    int64_t w;      // offset of the block's W16 [F][r16]
+    int r, r16;
 };
 
 struct TcLeaf {
@@ -277,8 +324,8 @@ struct TcLeaf {
 template <class T>
 __global__ void __launch_bounds__(tc::kThreads) tc_phase2(const TcLeaf* __restrict__ leaves,
                                                           const TcSeg* __restrict__ segs, const T* __restrict__ far,
-                                                          const float* __restrict__ W, float* __restrict__ Y, int N,
-                                                          int F, int* __restrict__ err)
+                                                          const T* __restrict__ whi, const T* __restrict__ wlo,
+                                                          float* __restrict__ Y, int N, int F, int* __restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;
@@ -293,6 +340,9 @@ __global__ void __launch_bounds__(tc::kThreads) tc_phase2(const TcLeaf* __restri
         tc::bar_init(tc::smem_addr(&bar));
         tc::fence_async_smem();
     }
+    // rows beyond the leaf stay zero for the whole kernel
+    for (int e = tid; e < tc::kM * tc::kKT * 2 / 16; e += tc::kThreads)
+        reinterpret_cast<uint4*>(sA)[e] = make_uint4(0, 0, 0, 0);
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
@@ -307,29 +357,29 @@ __global__ void __launch_bounds__(tc::kThreads) tc_phase2(const TcLeaf* __restri
     for (int si = L.seg0; si < L.seg0 + L.nseg && ok; ++si) {
         const TcSeg S = segs[si];
         for (int k0 = 0; k0 < S.r && ok; k0 += tc::kKT) {
-            // A: (row i, k) = U^T[k0 + k][i] -- transposed into K-major
-            for (int e = tid; e < tc::kM * tc::kKT; e += tc::kThreads) {
-                const int k = e / tc::kM, i = e % tc::kM;
-                T v = tc::to16<T>(0.f);
-                if (i < L.m && k0 + k < S.r) v = far[S.u + (int64_t)(k0 + k) * L.m8 + i];
-                tc::st16<T>(sA, i, k, v);
+            const int kc = min(tc::kKT, S.r - k0), kc16 = (kc + 15) & ~15;
+            // A: (row i, k) = U^T[k0 + k][i], transposed into K-major; 8 rows i per 16-byte load
+            for (int e = tid; e < kc16 * (L.m8 >> 3); e += tc::kThreads) {
+                const int k = e % kc16, ic = e / kc16;
+                if (k < kc) {
+                    const uint4 v = __ldg(reinterpret_cast<const uint4*>(far + S.u + (int64_t)(k0 + k) * L.m8 + 8 * ic));
+                    const T* pv = reinterpret_cast<const T*>(&v);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) tc::st16<T>(sA, 8 * ic + j, k, pv[j]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) tc::st16<T>(sA, 8 * ic + j, k, tc::to16<T>(0.f));
+                }
             }
-            // B: (f, k) = W_b[f][k0 + k], split into 16-bit hi + lo
-            for (int e = tid; e < F * tc::kKT; e += tc::kThreads) {
-                const int f = e / tc::kKT, k = e % tc::kKT;
-                float x = 0.f;
-                if (k0 + k < S.r) x = W[S.w + (int64_t)f * S.r + k0 + k];
-                const T h = tc::to16<T>(x);
-                tc::st16<T>(sBh, f, k, h);
-                tc::st16<T>(sBl, f, k, tc::to16<T>(x - tc::from16(h)));
-            }
+            // B: (f, k) = W_b[f][k0 + k], hi and lo parts (zero-padded to r16)
+            tc::stage_rows<T>(sBh, F, whi + S.w + k0, S.r16, [&](int, int c) { return 8 * c < kc16; });
+            tc::stage_rows<T>(sBl, F, wlo + S.w + k0, S.r16, [&](int, int c) { return 8 * c < kc16; });
             tc::fence_async_smem();
             __syncthreads();
             if (tid == 0) {
                 tc::tc_fence_after();
                 const uint32_t a0 = tc::smem_addr(sA), bh0 = tc::smem_addr(sBh), bl0 = tc::smem_addr(sBl);
-                const int nks = (min(tc::kKT, S.r - k0) + 15) / 16;
-                for (int ks = 0; ks < nks; ++ks) {
+                for (int ks = 0; ks < kc16 / 16; ++ks) {
                     const uint64_t da = tc::sdesc(a0 + ks * 2 * lbo, lbo, sbo);
                     tc::mma_f16(tmem, da, tc::sdesc(bh0 + ks * 2 * lbo, lbo, sbo), idesc, first ? 0u : 1u);
                     first = 0;
@@ -400,6 +450,7 @@ __global__ void __launch_bounds__(256) near_mrhs(const TcLeaf* __restrict__ leav
                 }
                 __syncthreads();
                 if (act) {
+#pragma unroll 4
                     for (int k = 0; k < kc; ++k) {
                         const float4 a = __ldg(reinterpret_cast<const float4*>(A + S.a + (int64_t)(k0 + k) * L.m8 + 4 * rq));
                         const float4 x = *reinterpret_cast<const float4*>(sx + k * F + 4 * fq);
@@ -438,10 +489,11 @@ int tc_prepare(Operator& op, std::string& err)
     std::vector<int64_t> w_base(op.n_far);
     int64_t wl = 0;
     for (int b = 0; b < op.n_far; ++b) {
+        const int r16 = (op.rank[b] + 15) & ~15;
         w_base[b] = wl;
-        wl += (int64_t)op.F * op.rank[b];
+        wl += (int64_t)op.F * r16;
         const FarBlock& fb = op.far_blocks[b];
-        blocks.push_back({op.far_v_off[b], w_base[b], fb.n, round8(fb.n), fb.col0, op.rank[b]});
+        blocks.push_back({op.far_v_off[b], w_base[b], fb.n, round8(fb.n), fb.col0, op.rank[b], r16, 0});
     }
     std::stable_sort(blocks.begin(), blocks.end(),
                      [](const TcBlock& a, const TcBlock& b) { return (int64_t)a.n * a.r > (int64_t)b.n * b.r; });
@@ -451,7 +503,7 @@ int tc_prepare(Operator& op, std::string& err)
     for (int b = 0; b < op.n_far; ++b)
         for (int c = op.far_chunk_ptr[b]; c < op.far_chunk_ptr[b + 1]; ++c) {
             const Chunk& ch = op.far_chunks[c];
-            fl[ch.leaf].push_back({op.far_u_off[b] + ch.off, w_base[b], op.rank[b], 0});
+            fl[ch.leaf].push_back({op.far_u_off[b] + ch.off, w_base[b], op.rank[b], (op.rank[b] + 15) & ~15});
         }
     for (int b = 0; b < op.n_near; ++b)
         for (int c = op.dense_chunk_ptr[b]; c < op.dense_chunk_ptr[b + 1]; ++c) {
@@ -493,7 +545,10 @@ int tc_prepare(Operator& op, std::string& err)
     void* p = nullptr;
     if ((rc = dev_alloc(op, (char**)&p, (size_t)2 * 2 * op.F * op.N, err))) return rc;
     op.tc_xsplit = p;
-    if ((rc = dev_alloc(op, &op.tc_w, (size_t)std::max<int64_t>(wl, 1), err))) return rc;
+    // W as 16-bit hi and lo parts, [F][r16] per block; the padding stays zero
+    if ((rc = dev_alloc(op, (char**)&p, (size_t)2 * 2 * std::max<int64_t>(wl, 1), err))) return rc;
+    op.tc_w = (float*)p;
+    RT_CUDA_TRY(cudaMemset(p, 0, (size_t)2 * 2 * std::max<int64_t>(wl, 1)));
     if ((rc = dev_alloc(op, &op.tc_err, 1, err))) return rc;
     RT_CUDA_TRY(cudaMemset(op.tc_err, 0, sizeof(int)));
     const int smem = tc::kM * tc::kKT * 2 + 2 * op.F * tc::kKT * 2;
@@ -516,29 +571,31 @@ int tc_apply(Operator& op, const float* X, float* Y, cudaStream_t s, std::string
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(op.tc_nblocks, (int64_t)sms * 4));
     const int nl = (int)op.plan.leaf_start.size();
+    const int xal = ((int64_t)N % 8 == 0) ? 1 : 0;   // 16-byte X loads need every row start aligned
     if (op.far_prec == RT_PREC_BF16) {
-        __nv_bfloat16* hi = (__nv_bfloat16*)op.tc_xsplit;
-        __nv_bfloat16* lo = hi + total;
-        tc_split_kernel<__nv_bfloat16><<<(int)std::min<int64_t>((total + 255) / 256, sms * 16), 256, 0, s>>>(X, hi, lo,
-                                                                                                             total);
+        using T = __nv_bfloat16;
+        T* hi = (T*)op.tc_xsplit;
+        T* lo = hi + total;
+        T* whi = (T*)op.tc_w;
+        T* wlo = whi + std::max<int64_t>(op.tc_wlen, 1);
+        tc_split_kernel<T><<<(int)std::min<int64_t>((total + 255) / 256, sms * 16), 256, 0, s>>>(X, hi, lo, total);
         if (op.tc_nblocks > 0)
-            tc_phase1<__nv_bfloat16><<<g1, tc::kThreads, smem, s>>>((const TcBlock*)op.tc_blocks, op.tc_nblocks,
-                                                                    (const __nv_bfloat16*)op.d_far, hi, lo, op.tc_w,
-                                                                    N, F, op.tc_err);
-        tc_phase2<__nv_bfloat16><<<nl, tc::kThreads, smem, s>>>((const TcLeaf*)op.tc_leaf_far,
-                                                                (const TcSeg*)op.tc_segs_far,
-                                                                (const __nv_bfloat16*)op.d_far, op.tc_w, Y, N, F,
-                                                                op.tc_err);
+            tc_phase1<T><<<g1, tc::kThreads, smem, s>>>((const TcBlock*)op.tc_blocks, op.tc_nblocks, (const T*)op.d_far,
+                                                        hi, lo, whi, wlo, N, F, xal, op.tc_err);
+        tc_phase2<T><<<nl, tc::kThreads, smem, s>>>((const TcLeaf*)op.tc_leaf_far, (const TcSeg*)op.tc_segs_far,
+                                                    (const T*)op.d_far, whi, wlo, Y, N, F, op.tc_err);
     } else {
-        __half* hi = (__half*)op.tc_xsplit;
-        __half* lo = hi + total;
-        tc_split_kernel<__half><<<(int)std::min<int64_t>((total + 255) / 256, sms * 16), 256, 0, s>>>(X, hi, lo, total);
+        using T = __half;
+        T* hi = (T*)op.tc_xsplit;
+        T* lo = hi + total;
+        T* whi = (T*)op.tc_w;
+        T* wlo = whi + std::max<int64_t>(op.tc_wlen, 1);
+        tc_split_kernel<T><<<(int)std::min<int64_t>((total + 255) / 256, sms * 16), 256, 0, s>>>(X, hi, lo, total);
         if (op.tc_nblocks > 0)
-            tc_phase1<__half><<<g1, tc::kThreads, smem, s>>>((const TcBlock*)op.tc_blocks, op.tc_nblocks,
-                                                             (const __half*)op.d_far, hi, lo, op.tc_w, N, F,
-                                                             op.tc_err);
-        tc_phase2<__half><<<nl, tc::kThreads, smem, s>>>((const TcLeaf*)op.tc_leaf_far, (const TcSeg*)op.tc_segs_far,
-                                                         (const __half*)op.d_far, op.tc_w, Y, N, F, op.tc_err);
+            tc_phase1<T><<<g1, tc::kThreads, smem, s>>>((const TcBlock*)op.tc_blocks, op.tc_nblocks, (const T*)op.d_far,
+                                                        hi, lo, whi, wlo, N, F, xal, op.tc_err);
+        tc_phase2<T><<<nl, tc::kThreads, smem, s>>>((const TcLeaf*)op.tc_leaf_far, (const TcSeg*)op.tc_segs_far,
+                                                    (const T*)op.d_far, whi, wlo, Y, N, F, op.tc_err);
     }
     RT_CUDA_TRY(cudaGetLastError());
     near_mrhs<<<nl, 256, (size_t)64 * F * sizeof(float), s>>>((const TcLeaf*)op.tc_leaf_near,
