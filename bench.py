@@ -45,10 +45,16 @@ def peaks():
 
 
 def workload(name):
+    if name.startswith("batch"):
+        return W.batch_instances(count=int(name[5:] or 256), seed=0)
     if name == "cube32_F16":
         return W.multifreq_32()
     if name == "cube12_grey":
         return W.plain_grey_12()
+    if name.startswith("cube") and name.endswith("s") and "_F" in name:
+        # one operator shared by all frequencies (kappa_nu = kappa(x))
+        n, F = name[4:-1].split("_F")
+        return W.shared_kappa_64(n=int(n), F=int(F))
     if name.startswith("cube") and "_F" in name:
         n, F = name[4:].split("_F")
         return W.multifreq_32(n=int(n), F=int(F))
@@ -104,6 +110,79 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def run_batch(args):
+    """Batched workload: one step = build + solve of every instance (rt_build_batch + rt_solve_batch)."""
+    import torch
+
+    import paper_2306_05789_gb300 as rt
+    from paper_2306_05789_gb300 import build as _b
+    _b.build()
+    rt.lib()
+    dev = torch.device("cuda", 0)
+    probs = workload(args.workload)
+    hp = rt.hparams()
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        b = rt.rt_build_batch(probs, hp, threads=8, tune=args.tune, stream=stream)
+        J = torch.zeros(int(b.vec_off[-1]), dtype=torch.float32, device=dev)
+        T = torch.zeros(int(b.vert_off[-1]), dtype=torch.float64, device=dev)
+        iters, st = b.solve(J, T, tol=args.tol, max_iter=300, check_every=4, stream=stream)
+        return b, iters, st
+
+    for _ in range(args.warmup):
+        b, _, _ = step()
+        b.free()
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    info = None
+    solve_ms = []
+    for k in range(args.steps):
+        b, iters, st = step()
+        solve_ms.append(st["ms_total"])
+        info = b.info()
+        if k < args.steps - 1:
+            b.free()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    X = torch.rand(int(b.vec_off[-1]), device=dev)
+    Y = torch.zeros_like(X)
+    for _ in range(3):
+        b.apply(X, Y, stream)
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(20):
+        b.apply(X, Y, stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    t_apply = a0.elapsed_time(a1) / 20 / 1e3
+    b.free()
+    hbm, _, peak_kind = peaks()
+    n = len(probs)
+    gbs = info["apply_bytes"] / t_apply / 1e9
+    print(json.dumps({
+        "metric": METRIC, "value": n * args.steps / (ms / 1e3), "unit": "solves/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "instances": n, "n_range": [8, 24], "F_range": [1, 8],
+                   "amp_range": [0.0, 0.8], "tol": args.tol, "autotune": bool(args.tune),
+                   "l2": "batch operators larger than L2"},
+        "roofline": {"bound": "hbm", "kernel": "batch_apply_kernel (persistent, all instances)", "achieved": gbs,
+                     "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "peak_kind": peak_kind,
+                     "ms": t_apply * 1e3, "algorithmic_bytes": info["apply_bytes"]},
+        "batch": {k: info[k] for k in ("p1_target_bytes", "ctas_per_sm", "n_works", "tune_ms", "build_ms")},
+        "solve": {"ms_mean": statistics.mean(solve_ms), "iters_max": int(max(iters))},
+        "clocks": clk,
+    }))
 
 
 def run_gpu(args):
@@ -337,9 +416,12 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--cpu-rows", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", dest="tune", action="store_false")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.startswith("batch"):
+        run_batch(args)
     else:
         run_gpu(args)
 

@@ -236,6 +236,52 @@ int rt_solve_fixed_point(rt_operator* op, const rt_solve_opts* opts, void* J_dev
 /* Release the operator and its device memory. */
 void rt_free(rt_operator* op);
 
+/* ---- batches of independent instances ------------------------------------
+ * A batch holds one operator per problem (same hparams, H-matrix mode with
+ * an FP32 far field, at most 16 kappa groups per problem) and applies or
+ * solves all of them together: one persistent launch applies every
+ * operator, and the fixed point runs on concatenated vectors, each instance
+ * stopping at its own first iteration with residual <= tol.  Vectors of a
+ * batch are the instances' [F_b][N_b] vectors (caller vertex order)
+ * concatenated in problem order; temperatures the [N_b] arrays likewise. */
+typedef struct rt_batch rt_batch;
+
+typedef struct {
+    int64_t count;          /* instances */
+    int64_t total_vec;      /* sum F_b N_b */
+    int64_t total_vert;     /* sum N_b */
+    int p1_target_bytes;    /* operator bytes per phase-1 work item (chosen by the autotuner) */
+    int ctas_per_sm;        /* persistent grid size per SM (chosen by the autotuner) */
+    int n_works;            /* work items of one apply */
+    int64_t apply_bytes;    /* algorithmic bytes of one apply of every operator */
+    double tune_ms, build_ms;
+} rt_batch_info_t;
+
+/* Build the operators of `count` problems with `threads` host threads (each
+ * on its own stream; 0 = 8), then, if tune != 0, time candidate work-item
+ * sizes and persistent grid sizes on the batch and keep the fastest. */
+int rt_build_batch(const rt_problem* probs, int64_t count, const rt_hparams* hp, int threads, int tune, void* stream,
+                   rt_batch** out);
+
+/* Sizes and tuner choices; vec_off / vert_off (may be NULL) receive count+1
+ * offsets of each instance's vectors and temperatures. */
+int rt_batch_info(const rt_batch* b, rt_batch_info_t* info, int64_t* vec_off, int64_t* vert_off);
+
+/* Y = Gbar X for every instance, X and Y device arrays [total_vec]. */
+int rt_batch_apply(rt_batch* b, const float* X, float* Y, void* stream);
+
+/* Fixed point of every instance from T = T0, J = 0 (use_J0 and refine_tol are
+ * ignored): J_dev [total_vec], T_dev [total_vert] (device), iters (host,
+ * may be NULL) [count] = iterations each instance took.  RT_ENOCONV if some
+ * instance did not reach tol; RT_ETIMEOUT if a bounded device wait gave up. */
+int rt_solve_batch(rt_batch* b, const rt_solve_opts* opts, float* J_dev, double* T_dev, int32_t* iters,
+                   rt_solve_stats* stats, void* stream);
+
+void rt_batch_free(rt_batch* b);
+
+/* Thread-local text of the last batch error. */
+const char* rt_batch_last_error(void);
+
 /* Thread-local text of the last error on the calling thread ("" if none). */
 const char* rt_last_error(void);
 

@@ -80,6 +80,15 @@ class RtSolveOpts(ctypes.Structure):
                 ("use_graph", _c_int), ("refine_tol", _c_dbl)]
 
 
+class RtBatchInfo(ctypes.Structure):
+    _fields_ = [("count", _c_i64), ("total_vec", _c_i64), ("total_vert", _c_i64), ("p1_target_bytes", _c_int),
+                ("ctas_per_sm", _c_int), ("n_works", _c_int), ("apply_bytes", _c_i64), ("tune_ms", _c_dbl),
+                ("build_ms", _c_dbl)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class RtSolveStats(ctypes.Structure):
     _fields_ = [("iters", _c_int), ("converged", _c_int), ("residual", _c_dbl), ("ms_total", _c_dbl)]
 
@@ -89,7 +98,8 @@ class RtSolveStats(ctypes.Structure):
 
 # every symbol declared in include/rt.h
 EXPORTS = ("rt_build_operator", "rt_operator_info", "rt_apply", "rt_apply_noalloc", "rt_source", "rt_eval_entries",
-           "rt_solve_fixed_point", "rt_free", "rt_last_error", "rt_plan")
+           "rt_solve_fixed_point", "rt_free", "rt_last_error", "rt_plan", "rt_build_batch", "rt_batch_info",
+           "rt_batch_apply", "rt_solve_batch", "rt_batch_free", "rt_batch_last_error")
 
 _lib = None
 
@@ -114,6 +124,13 @@ def lib():
     L.rt_free.restype = None
     L.rt_last_error.restype = ctypes.c_char_p
     L.rt_plan.argtypes = [_P, _c_i64, _c_int, _c_dbl, _c_int, _P, _P, _c_i64, _P]
+    L.rt_build_batch.argtypes = [_P, _c_i64, ctypes.POINTER(RtHparams), _c_int, _c_int, _P, ctypes.POINTER(_P)]
+    L.rt_batch_info.argtypes = [_P, ctypes.POINTER(RtBatchInfo), _P, _P]
+    L.rt_batch_apply.argtypes = [_P, _P, _P, _P]
+    L.rt_solve_batch.argtypes = [_P, ctypes.POINTER(RtSolveOpts), _P, _P, _P, ctypes.POINTER(RtSolveStats), _P]
+    L.rt_batch_free.argtypes = [_P]
+    L.rt_batch_free.restype = None
+    L.rt_batch_last_error.restype = ctypes.c_char_p
     _lib = L
     return L
 
@@ -263,3 +280,62 @@ def rt_plan(xyz, leaf=64, eta=2.0, adm=RT_ADM_GAP):
     _check(lib().rt_plan(_ptr(xyz), n, int(leaf), float(eta), int(adm), _ptr(perm), _ptr(blocks), nb,
                          _ptr(counts)))
     return perm, blocks[:nb], tuple(int(c) for c in counts)
+
+
+def _check_batch(rc):
+    if rc != RT_OK:
+        raise RtError(rc, lib().rt_batch_last_error().decode(errors="replace"))
+
+
+class Batch:
+    """Independent instances applied and solved together (rt_build_batch)."""
+
+    def __init__(self, handle, count):
+        self.h = handle
+        self.count = count
+        i = RtBatchInfo()
+        self.vec_off = np.zeros(count + 1, dtype=np.int64)
+        self.vert_off = np.zeros(count + 1, dtype=np.int64)
+        _check_batch(lib().rt_batch_info(self.h, ctypes.byref(i), _ptr(self.vec_off), _ptr(self.vert_off)))
+        self._info = i.as_dict()
+
+    def info(self) -> dict:
+        return dict(self._info)
+
+    def apply(self, X, Y, stream=None):
+        """rt_batch_apply on concatenated [total_vec] float32 device tensors."""
+        _check_batch(lib().rt_batch_apply(self.h, _P(X.data_ptr()), _P(Y.data_ptr()), _stream_ptr(stream)))
+
+    def solve(self, J, T, tol=1e-6, max_iter=300, check_every=4, T0=0.0, use_graph=True, stream=None,
+              raise_on_noconv=True):
+        """rt_solve_batch: J [total_vec] float32, T [total_vert] float64 device tensors; returns (iters, stats)."""
+        o = RtSolveOpts(float(tol), int(max_iter), int(check_every), float(T0), 0, 1 if use_graph else 0, 0.0)
+        st = RtSolveStats()
+        iters = np.zeros(self.count, dtype=np.int32)
+        rc = lib().rt_solve_batch(self.h, ctypes.byref(o), _P(J.data_ptr()), _P(T.data_ptr()), _ptr(iters),
+                                  ctypes.byref(st), _stream_ptr(stream))
+        if rc != RT_OK and (raise_on_noconv or rc != RT_ENOCONV):
+            _check_batch(rc)
+        return iters, st.as_dict()
+
+    def free(self):
+        if self.h:
+            lib().rt_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def rt_build_batch(problems, hp: RtHparams, threads: int = 8, tune: bool = True, stream=None) -> Batch:
+    """Build one operator per problem and the batch structures (rt_build_batch)."""
+    args = [_ProblemArgs(p) for p in problems]
+    arr = (RtProblem * len(args))(*[a.s for a in args])
+    out = _P()
+    _check_batch(lib().rt_build_batch(ctypes.cast(arr, _P), len(args), ctypes.byref(hp), int(threads),
+                                      1 if tune else 0, _stream_ptr(stream), ctypes.byref(out)))
+    return Batch(out, len(args))
+

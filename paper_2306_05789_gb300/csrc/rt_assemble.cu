@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -112,8 +113,10 @@ int assemble_setup_constants(Operator& op, std::string& err)
         op.kp.gu32[g] = (float)u;
         op.kp.gw32[g] = (float)hw;
     }
-    // fixed rule tables: uploaded once per device
+    // fixed rule tables: uploaded once per device (serialised across host threads)
     static bool done[64] = {false};
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
     int dev = 0;
     RT_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 64 && done[dev]) return RT_OK;
@@ -690,6 +693,8 @@ int prepare_row_eval(Operator& op, std::string& err)
     if (rc) return rc;
     RT_CUDA_TRY(cudaMemcpy(op.d_sub_tets, tets.data(), sizeof(int) * tets.size(), cudaMemcpyHostToDevice));
     static bool attr_set[64] = {false};
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 64 && !attr_set[dev]) {
@@ -1052,7 +1057,7 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
     AcaDev D{};
     std::vector<void*> tmp;   // freed at the end
     auto talloc = [&](void** p, size_t bytes) -> int {
-        cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
+        cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 1, s);
         if (e != cudaSuccess) {
             err = std::string("cudaMalloc (ACA scratch): ") + cudaGetErrorString(e);
             return RT_ENOMEM;
@@ -1061,8 +1066,7 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
         return RT_OK;
     };
     auto cleanup = [&]() {
-        cudaStreamSynchronize(s);
-        for (void* p : tmp) cudaFree(p);
+        for (void* p : tmp) cudaFreeAsync(p, s);
         tmp.clear();
     };
     float* pool = nullptr;
@@ -1128,18 +1132,17 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
         DotItem* d_dot;
         int64_t dot_cap = 0;
         d_dot = nullptr;
-        int* h_status = nullptr;
-        RT_CUDA_TRY(cudaMallocHost((void**)&h_status, sizeof(int) * nfar * 2));
+        std::vector<int> h_status_buf((size_t)nfar * 2);
+        int* h_status = h_status_buf.data();
         std::vector<int> h_rank(nfar, 0);
 
         // initial pool: the first 8 steps of every block
         pool_cap = 0;
         for (auto& fb : farb) pool_cap += (int64_t)G * (fb.m + fb.n) * 8;
         {
-            cudaError_t e = cudaMalloc((void**)&pool, sizeof(float) * pool_cap);
+            cudaError_t e = cudaMallocAsync((void**)&pool, sizeof(float) * pool_cap, s);
             if (e != cudaSuccess) {
-                cudaFreeHost(h_status);
-                cleanup();
+                                cleanup();
                 err = "cudaMalloc (ACA pool) failed";
                 return RT_ENOMEM;
             }
@@ -1162,17 +1165,15 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
             if (pool_used + need > pool_cap) {
                 int64_t ncap = std::max<int64_t>(pool_cap * 2, pool_used + need * 8);
                 float* np = nullptr;
-                cudaError_t e = cudaMalloc((void**)&np, sizeof(float) * ncap);
+                cudaError_t e = cudaMallocAsync((void**)&np, sizeof(float) * ncap, s);
                 if (e != cudaSuccess) {
-                    cudaFreeHost(h_status);
-                    cudaFree(pool);
+                                        cudaFreeAsync(pool, s);
                     cleanup();
                     err = "cudaMalloc (ACA pool growth) failed";
                     return RT_ENOMEM;
                 }
                 RT_CUDA_TRY(cudaMemcpyAsync(np, pool, sizeof(float) * pool_used, cudaMemcpyDeviceToDevice, s));
-                RT_CUDA_TRY(cudaStreamSynchronize(s));
-                cudaFree(pool);
+                cudaFreeAsync(pool, s);
                 pool = np;
                 pool_cap = ncap;
                 D.pool = pool;
@@ -1246,9 +1247,9 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
             for (int ai = 0; ai < na; ++ai)
                 for (int l = 0; l <= h_rank[act[ai].b]; ++l) dots.push_back({ai, l});
             if ((int64_t)dots.size() > dot_cap) {
-                if (d_dot) cudaFree(d_dot);
+                if (d_dot) cudaFreeAsync(d_dot, s);
                 dot_cap = (int64_t)dots.size() * 2;
-                RT_CUDA_TRY(cudaMalloc((void**)&d_dot, sizeof(DotItem) * dot_cap));
+                RT_CUDA_TRY(cudaMallocAsync((void**)&d_dot, sizeof(DotItem) * dot_cap, s));
             }
             RT_CUDA_TRY(cudaMemcpyAsync(d_dot, dots.data(), sizeof(DotItem) * dots.size(), cudaMemcpyHostToDevice, s));
             aca_dots<<<(int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)dots.size() + 7) / 8, (int64_t)sms * 32)),
@@ -1268,9 +1269,8 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
             final_status[b] = status[b] == ACA_ACTIVE ? ACA_DENSE : status[b];
             final_rank[b] = h_rank[b];
         }
-        if (d_dot) cudaFree(d_dot);
-        cudaFreeHost(h_status);
-#undef TA
+        if (d_dot) cudaFreeAsync(d_dot, s);
+        #undef TA
     }
     cudaEventRecord(ev1, s);
     cudaEventSynchronize(ev1);
@@ -1319,7 +1319,7 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
     if (op.n_far > 0) {
         char* d = nullptr;
         if ((rc = dev_alloc(op, &d, (size_t)far_elems * esz, err))) {
-            if (pool) cudaFree(pool);
+            if (pool) cudaFreeAsync(pool, s);
             cleanup();
             return rc;
         }
@@ -1333,8 +1333,8 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
                                  op.far_chunk_ptr[k + 1]});
         PackItem* d_items = nullptr;
         Chunk* d_chunks = nullptr;
-        RT_CUDA_TRY(cudaMalloc((void**)&d_items, sizeof(PackItem) * items.size()));
-        RT_CUDA_TRY(cudaMalloc((void**)&d_chunks, sizeof(Chunk) * op.far_chunks.size()));
+        RT_CUDA_TRY(cudaMallocAsync((void**)&d_items, sizeof(PackItem) * items.size(), s));
+        RT_CUDA_TRY(cudaMallocAsync((void**)&d_chunks, sizeof(Chunk) * op.far_chunks.size(), s));
         RT_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), sizeof(PackItem) * items.size(), cudaMemcpyHostToDevice, s));
         RT_CUDA_TRY(cudaMemcpyAsync(d_chunks, op.far_chunks.data(), sizeof(Chunk) * op.far_chunks.size(),
                                     cudaMemcpyHostToDevice, s));
@@ -1348,7 +1348,7 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
         if (op.refine && op.far_prec != RT_PREC_F32) {
             // FP32 copy of the far field in the same layout, for refinement sweeps
             if ((rc = dev_alloc(op, &op.d_far32, (size_t)far_elems, err))) {
-                if (pool) cudaFree(pool);
+                if (pool) cudaFreeAsync(pool, s);
                 cleanup();
                 return rc;
             }
@@ -1356,11 +1356,10 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
             aca_pack<float><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, op.d_far32);
             RT_CUDA_TRY(cudaGetLastError());
         }
-        RT_CUDA_TRY(cudaStreamSynchronize(s));
-        cudaFree(d_items);
-        cudaFree(d_chunks);
+        cudaFreeAsync(d_items, s);
+        cudaFreeAsync(d_chunks, s);
     }
-    if (pool) cudaFree(pool);
+    if (pool) cudaFreeAsync(pool, s);
     cleanup();
     cudaEventRecord(ev1, s);
     cudaEventSynchronize(ev1);

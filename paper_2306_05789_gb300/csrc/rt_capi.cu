@@ -9,9 +9,6 @@
 
 #include "rt_internal.h"
 
-struct rt_operator {
-    rt::Operator op;
-};
 
 namespace {
 

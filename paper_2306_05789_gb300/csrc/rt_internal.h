@@ -181,6 +181,7 @@ struct Operator {
     // matvec work lists (device)
     void* d_p1_items = nullptr; int n_p1 = 0;
     void* d_p1_rows = nullptr;
+    std::vector<char> h_p1_rows;   // host copy of the (length-sorted) phase-1 row list
     void* d_p2_leaf = nullptr;  int n_p2 = 0;
     void* d_p2_segs = nullptr;  int n_p2_segs = 0;
     float* d_w = nullptr;       int64_t w_len = 0;   // phase-1 scratch [sum r][F]
@@ -265,3 +266,8 @@ int dev_alloc(Operator& op, T** p, size_t count, std::string& err)
 }
 
 }  // namespace rt
+
+// the opaque handle of the C ABI
+struct rt_operator {
+    rt::Operator op;
+};
