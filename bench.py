@@ -185,6 +185,113 @@ def run_batch(args):
     }))
 
 
+def run_serve(args):
+    """Serving workload: a Poisson stream of solve requests (random mesh size,
+    frequency count, kappa amplitude and wall reflectivity) admitted by the
+    library's server under an HBM budget, BF16 far field with refinement.
+    Latency runs from each request's scheduled arrival to its result in host
+    memory.  The same requests are then solved one after another by the plain
+    FP32 path (rt_build_operator + rt_solve_fixed_point, results copied to the
+    host) for comparison."""
+    import threading
+
+    import torch
+
+    import paper_2306_05789_gb300 as rt
+    from paper_2306_05789_gb300 import build as _b
+    _b.build()
+    rt.lib()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    reqs = W.serving_requests(count=args.requests, rate_per_s=args.rate, seed=args.seed)
+    far = {"f32": rt.RT_PREC_F32, "bf16": rt.RT_PREC_BF16, "f16": rt.RT_PREC_F16}[args.far_prec]
+    hp = rt.hparams(far_prec=far, refine=1 if far != rt.RT_PREC_F32 else 0)
+    budget = int(args.budget_gb * 1e9)
+    refine_tol = 1e-3 if far != rt.RT_PREC_F32 else 0.0
+    # warm-up: a few small requests through a server of the same shape
+    warm = W.serving_requests(count=max(1, args.warmup), rate_per_s=args.rate, seed=12345, nmin=10, nmax=14, fmax=4)
+    srv = rt.Server(hp, hbm_budget=budget, slots=args.slots, tol=args.tol, refine_tol=refine_tol)
+    ids = [srv.submit(p) for _, p in warm]
+    for i in ids:
+        srv.poll(i, wait_ms=-1)
+    srv.free()
+
+    clocks = Clocks(0)
+    clocks.start()
+    t_base = time.perf_counter()
+    srv = rt.Server(hp, hbm_budget=budget, slots=args.slots, tol=args.tol, refine_tol=refine_tol)
+    t_srv = time.perf_counter()
+    ids = [None] * len(reqs)
+    arrive = [t_srv + t for t, _ in reqs]
+
+    def submitter():
+        for k, (t, p) in enumerate(reqs):
+            d = arrive[k] - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            ids[k] = srv.submit(p)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    results = [srv.poll(i, wait_ms=-1) for i in ids]
+    sinfo = srv.info()
+    srv.free()
+    clk = clocks.stop()
+    # t_done is on the server clock, which starts within t_srv - t_base of t_srv
+    done = [t_srv + r[2]["t_done"] for r in results]
+    lat = sorted(d - a for d, a in zip(done, arrive))
+    span = max(done) - arrive[0]
+    served = len(reqs) / span
+
+    def pct(q):
+        return lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)] * 1e3
+
+    # plain FP32 form, one request after another, same requests
+    hp32 = rt.hparams(far_prec=rt.RT_PREC_F32)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    errs_T, errs_J = [], []
+    for (t, p), r in zip(reqs, results):
+        op = rt.rt_build_operator(p, hp32, stream)
+        J = torch.zeros(p.freqs.F, p.N, dtype=torch.float32, device=dev)
+        T = torch.zeros(p.N, dtype=torch.float64, device=dev)
+        op.solve_fixed_point(J, T, tol=args.tol, max_iter=300, check_every=4, stream=stream)
+        Jh, Th = J.cpu().numpy(), T.cpu().numpy()
+        op.free()
+        errs_T.append(float(np.linalg.norm(r[1] - Th) / np.linalg.norm(Th)))
+        errs_J.append(float(np.linalg.norm(r[0] - Jh) / np.linalg.norm(Jh)))
+    t_plain = time.perf_counter() - t0
+    plain = len(reqs) / t_plain
+    infos = [r[2] for r in results]
+    h2d = sum(p.xyz.nbytes + p.tet.nbytes + p.emit_tri.nbytes for _, p in reqs)
+    d2h = sum(p.freqs.F * p.N * 4 + p.N * 8 for _, p in reqs)
+    print(json.dumps({
+        "metric": METRIC, "value": served, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": f"f32+{args.far_prec}" if args.far_prec != "f32" else "f32", "data": "synthetic",
+        "config": {"workload": "serve", "requests": len(reqs), "rate_per_s": args.rate, "seed": args.seed,
+                   "n_range": [16, 48], "F_range": [1, 32], "amp_range": [0.0, 0.8], "R0_range": [0.0, 0.9],
+                   "far_prec": args.far_prec, "refine": far != rt.RT_PREC_F32, "hbm_budget_gb": args.budget_gb,
+                   "slots": args.slots, "tol": args.tol,
+                   "l2": "operators larger than L2 (no flush needed)"},
+        "latency_ms": {"p50": pct(0.50), "p99": pct(0.99), "mean": 1e3 * statistics.mean(lat), "max": lat[-1] * 1e3},
+        "plain_fp32_sequential": {"value": plain, "unit": "solves/s"},
+        "speedup_vs_plain_fp32": served / plain,
+        "err_vs_plain_fp32": {"T_rel_l2_max": max(errs_T), "J_rel_l2_max": max(errs_J)},
+        "server": sinfo,
+        "per_request": {"ms_build_mean": statistics.mean(i["ms_build"] for i in infos),
+                        "ms_solve_mean": statistics.mean(i["ms_solve"] for i in infos),
+                        "iters_mean": statistics.mean(i["iters"] for i in infos),
+                        "est_over_peak_min": min(i["est_bytes"] / max(1, i["peak_bytes"]) for i in infos),
+                        "peak_gb_max": max(i["peak_bytes"] for i in infos) / 1e9},
+        "e2e": {"value": served, "unit": "solves/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "note": "the served rate is itself end to end: host inputs in, host results out"},
+        "clocks": clk,
+    }))
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -417,9 +524,18 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", dest="tune", action="store_false")
+    ap.add_argument("--requests", type=int, default=24, help="serve: requests in the stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (1/s)")
+    ap.add_argument("--seed", type=int, default=0, help="serve: request stream seed")
+    ap.add_argument("--slots", type=int, default=6, help="serve: requests on the device at once")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM budget")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        if args.far_prec == "f32" and "--far-prec" not in sys.argv:
+            args.far_prec = "bf16"
+        run_serve(args)
     elif args.workload.startswith("batch"):
         run_batch(args)
     else:

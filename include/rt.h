@@ -45,6 +45,7 @@ extern "C" {
 #define RT_ECUDA (-3)    /* a CUDA call failed */
 #define RT_ENOCONV (-4)  /* fixed point did not reach tol within max_iter */
 #define RT_ETIMEOUT (-5) /* a bounded device-side wait gave up */
+#define RT_EAGAIN (-6)   /* rt_poll: the request has not finished yet */
 
 /* kappa(x) descriptors (kappa_nu = c_nu * kappa(x)) */
 #define RT_KAPPA_CONST 0   /* kappa = k0 */
@@ -137,7 +138,9 @@ typedef struct {
     int rank_max;    /* ACA rank limit before a block is stored dense (0 = 512) */
     int adm;         /* RT_ADM_GAP (default) or RT_ADM_CENTER */
     int line_eval;   /* RT_LINE_CLOSED (default) or RT_LINE_NODES (FP32 paths) */
-    int refine;      /* with a BF16/FP16 far field: also keep an FP32 copy for refinement sweeps */
+    int refine;      /* with a BF16/FP16 far field: also store each value's 16-bit remainder
+                        (value - high part, same layout) for refinement sweeps, so that the
+                        far field takes 4 bytes per entry in all, like FP32 storage */
     int tensor_cores; /* 0: use the tcgen05 apply when eligible (one operator group, F a multiple
                          of 16 up to 256, BF16/FP16 far field, leaves <= 128); 1: CUDA cores only */
 } rt_hparams;
@@ -158,6 +161,7 @@ typedef struct {
     int64_t apply_flops;
     int64_t device_bytes;        /* device memory held by the operator */
     double ms_tree, ms_near, ms_aca, ms_pack, ms_source; /* assembly phase times */
+    int64_t peak_bytes;          /* largest device footprint during assembly (operator + ACA scratch) */
 } rt_info;
 
 /* Fixed-point options (Section 1.3).  The iteration starts from T = T0 at
@@ -169,9 +173,9 @@ typedef struct {
     double T0;
     int use_J0;
     int use_graph;   /* capture check_every iterations in a CUDA graph */
-    double refine_tol; /* operator built with refine: iterate on the BF16/FP16 far field until the
-                          residual is <= refine_tol, then on the FP32 copy down to tol (0: FP32 copy
-                          from the start) */
+    double refine_tol; /* operator built with refine: iterate on the 16-bit high parts of the far
+                          field until the residual is <= refine_tol, then on high + low parts down
+                          to tol (0: high + low parts from the start) */
 } rt_solve_opts;
 
 typedef struct {
@@ -296,6 +300,72 @@ const char* rt_last_error(void);
  * [2] = admissible blocks. */
 int rt_plan(const double* xyz, int64_t n, int leaf, double eta, int adm, int32_t* perm, int32_t* blocks,
             int64_t cap, int64_t* counts);
+
+/* ---- serving: continuous admission of independent solve requests --------
+ * (The paper solves one problem at a time; this is the deployment form.)
+ * A server owns `slots` worker threads, each with its own CUDA stream on the
+ * device current at rt_server_create.  A submitted request (a problem as for
+ * rt_build_operator) waits in a queue until a slot is free and its estimated
+ * device footprint fits in what the budget has left; it is then assembled
+ * (Section 2, 2.1) and iterated to the fixed point (Section 1.3) on that
+ * slot's stream, so the work of several requests overlaps on the device.
+ * Each request's operator and iterates stay on the device until its result
+ * has been copied to host memory; then they are freed and the next request
+ * is admitted.  Admission is first come, first served, except that a request
+ * that fits may start ahead of one that does not, at most `max_bypass` times
+ * per waiting request.  The estimate (cluster and block tree plus an assumed
+ * far-block rank) is replaced by the operator's measured size once it is
+ * built.  Results do not depend on what else is in flight. */
+typedef struct rt_server rt_server;
+
+typedef struct {
+    int64_t hbm_budget;      /* bytes of device memory the admitted requests may hold (> 0) */
+    int slots;               /* requests on the device at once (1..64) */
+    int max_bypass;          /* times a waiting request may be overtaken (>= 0) */
+    rt_hparams hp;           /* assembly parameters of every request (H-matrix mode) */
+    rt_solve_opts opts;      /* fixed-point options of every request (T0, tol, ...) */
+} rt_server_opts;
+
+typedef struct {
+    int status;              /* RT_OK or the request's error code */
+    int iters, converged;
+    double residual;
+    int64_t N, F;
+    int64_t est_bytes;       /* footprint estimate used for admission */
+    int64_t peak_bytes;      /* measured peak during assembly (operator + ACA scratch) */
+    int64_t resident_bytes;  /* operator + iterates while the fixed point ran */
+    double t_submit, t_admit, t_built, t_done;   /* seconds since rt_server_create */
+    double ms_build, ms_solve;
+} rt_request_info;
+
+typedef struct {
+    int64_t submitted, finished, failed, queued, running;
+    int64_t reserved_bytes;      /* budget held by admitted requests now */
+    int64_t peak_reserved_bytes; /* largest value it reached */
+    int64_t max_running;         /* most requests on the device at once */
+} rt_server_info_t;
+
+/* Start a server.  RT_EINVAL for bad options. */
+int rt_server_create(const rt_server_opts* opts, rt_server** out);
+
+/* Queue one request; its inputs are copied.  *id receives its handle.
+ * RT_EINVAL for a malformed problem, RT_ENOMEM if its estimated footprint
+ * alone exceeds the budget. */
+int rt_submit(rt_server* s, const rt_problem* prob, int64_t* id);
+
+/* Wait up to wait_ms milliseconds (< 0: no limit) for request `id`.  Returns
+ * RT_EAGAIN if it is still queued or running (nothing is copied).  Otherwise
+ * the request is retired: J_host [F][N] floats and T_host [N] doubles (each
+ * may be NULL) receive the final iterate in the caller's vertex order, info
+ * (may be NULL) its record, and the return value is the request's status.
+ * RT_EINVAL for an unknown (or already retired) id. */
+int rt_poll(rt_server* s, int64_t id, int wait_ms, float* J_host, double* T_host, rt_request_info* info);
+
+/* Counters of the server. */
+int rt_server_info(rt_server* s, rt_server_info_t* info);
+
+/* Finish the requests on the device, drop the queued ones, free everything. */
+void rt_server_free(rt_server* s);
 
 #ifdef __cplusplus
 }

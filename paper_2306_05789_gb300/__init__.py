@@ -22,7 +22,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librt.so")
 
-RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOCONV, RT_ETIMEOUT = 0, -1, -2, -3, -4, -5
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOCONV, RT_ETIMEOUT, RT_EAGAIN = 0, -1, -2, -3, -4, -5, -6
 RT_KAPPA_CONST, RT_KAPPA_SINPROD = 0, 1
 RT_MODE_DENSE, RT_MODE_HMATRIX = 0, 1
 RT_PREC_F64, RT_PREC_F32, RT_PREC_BF16, RT_PREC_F16 = 0, 1, 2, 3
@@ -69,7 +69,7 @@ class RtInfo(ctypes.Structure):
                 ("rank_sum", _c_i64), ("aca_steps", _c_i64), ("entries_evaluated", _c_i64),
                 ("apply_bytes", _c_i64), ("apply_flops", _c_i64), ("device_bytes", _c_i64),
                 ("ms_tree", _c_dbl), ("ms_near", _c_dbl), ("ms_aca", _c_dbl), ("ms_pack", _c_dbl),
-                ("ms_source", _c_dbl)]
+                ("ms_source", _c_dbl), ("peak_bytes", _c_i64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,6 +89,30 @@ class RtBatchInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class RtServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget", _c_i64), ("slots", _c_int), ("max_bypass", _c_int), ("hp", RtHparams),
+                ("opts", RtSolveOpts)]
+
+
+class RtRequestInfo(ctypes.Structure):
+    _fields_ = [("status", _c_int), ("iters", _c_int), ("converged", _c_int), ("residual", _c_dbl), ("N", _c_i64),
+                ("F", _c_i64), ("est_bytes", _c_i64), ("peak_bytes", _c_i64), ("resident_bytes", _c_i64),
+                ("t_submit", _c_dbl), ("t_admit", _c_dbl), ("t_built", _c_dbl), ("t_done", _c_dbl),
+                ("ms_build", _c_dbl), ("ms_solve", _c_dbl)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class RtServerInfo(ctypes.Structure):
+    _fields_ = [("submitted", _c_i64), ("finished", _c_i64), ("failed", _c_i64), ("queued", _c_i64),
+                ("running", _c_i64), ("reserved_bytes", _c_i64), ("peak_reserved_bytes", _c_i64),
+                ("max_running", _c_i64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class RtSolveStats(ctypes.Structure):
     _fields_ = [("iters", _c_int), ("converged", _c_int), ("residual", _c_dbl), ("ms_total", _c_dbl)]
 
@@ -99,7 +123,8 @@ class RtSolveStats(ctypes.Structure):
 # every symbol declared in include/rt.h
 EXPORTS = ("rt_build_operator", "rt_operator_info", "rt_apply", "rt_apply_noalloc", "rt_source", "rt_eval_entries",
            "rt_solve_fixed_point", "rt_free", "rt_last_error", "rt_plan", "rt_build_batch", "rt_batch_info",
-           "rt_batch_apply", "rt_solve_batch", "rt_batch_free", "rt_batch_last_error")
+           "rt_batch_apply", "rt_solve_batch", "rt_batch_free", "rt_batch_last_error", "rt_server_create",
+           "rt_submit", "rt_poll", "rt_server_info", "rt_server_free")
 
 _lib = None
 
@@ -131,6 +156,12 @@ def lib():
     L.rt_batch_free.argtypes = [_P]
     L.rt_batch_free.restype = None
     L.rt_batch_last_error.restype = ctypes.c_char_p
+    L.rt_server_create.argtypes = [ctypes.POINTER(RtServerOpts), ctypes.POINTER(_P)]
+    L.rt_submit.argtypes = [_P, ctypes.POINTER(RtProblem), ctypes.POINTER(_c_i64)]
+    L.rt_poll.argtypes = [_P, _c_i64, _c_int, _P, _P, ctypes.POINTER(RtRequestInfo)]
+    L.rt_server_info.argtypes = [_P, ctypes.POINTER(RtServerInfo)]
+    L.rt_server_free.argtypes = [_P]
+    L.rt_server_free.restype = None
     _lib = L
     return L
 
@@ -339,3 +370,57 @@ def rt_build_batch(problems, hp: RtHparams, threads: int = 8, tune: bool = True,
                                       1 if tune else 0, _stream_ptr(stream), ctypes.byref(out)))
     return Batch(out, len(args))
 
+
+
+class Server:
+    """Continuous admission of solve requests under an HBM budget (rt_server_create).
+
+    ``submit`` copies a problem and returns at once with an id; ``poll`` returns
+    None while the request is queued or running, else (J [F, N] float32 numpy,
+    T [N] float64 numpy, info dict)."""
+
+    def __init__(self, hp: RtHparams, hbm_budget=120 * 10**9, slots=8, max_bypass=4, tol=1e-6, max_iter=300,
+                 check_every=4, T0=0.0, use_graph=True, refine_tol=0.0):
+        o = RtServerOpts(int(hbm_budget), int(slots), int(max_bypass), hp,
+                         RtSolveOpts(float(tol), int(max_iter), int(check_every), float(T0), 0,
+                                     1 if use_graph else 0, float(refine_tol)))
+        self.h = _P()
+        _check(lib().rt_server_create(ctypes.byref(o), ctypes.byref(self.h)))
+        self._dims = {}
+
+    def submit(self, prob) -> int:
+        a = _ProblemArgs(prob)
+        rid = _c_i64(0)
+        _check(lib().rt_submit(self.h, ctypes.byref(a.s), ctypes.byref(rid)))
+        self._dims[rid.value] = (prob.freqs.F, prob.N)
+        return rid.value
+
+    def poll(self, rid: int, wait_ms: int = 0, raise_on_error=True):
+        F, N = self._dims[rid]
+        J = np.empty((F, N), dtype=np.float32)
+        T = np.empty(N, dtype=np.float64)
+        info = RtRequestInfo()
+        rc = lib().rt_poll(self.h, int(rid), int(wait_ms), _ptr(J), _ptr(T), ctypes.byref(info))
+        if rc == RT_EAGAIN:
+            return None
+        del self._dims[rid]
+        d = info.as_dict()
+        if rc != RT_OK and raise_on_error:
+            _check(rc)
+        return J, T, d
+
+    def info(self) -> dict:
+        i = RtServerInfo()
+        _check(lib().rt_server_info(self.h, ctypes.byref(i)))
+        return i.as_dict()
+
+    def free(self):
+        if self.h:
+            lib().rt_server_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -691,7 +691,7 @@ int prepare_row_eval(Operator& op, std::string& err)
     }
     int rc = dev_alloc(op, &op.d_sub_tets, tets.size(), err);
     if (rc) return rc;
-    RT_CUDA_TRY(cudaMemcpy(op.d_sub_tets, tets.data(), sizeof(int) * tets.size(), cudaMemcpyHostToDevice));
+    if ((rc = upload_async(op, op.d_sub_tets, tets.data(), tets.size(), err))) return rc;
     static bool attr_set[64] = {false};
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
@@ -993,8 +993,17 @@ struct PackItem {
 // Each rank-1 term u v^T is stored as (s u)(v / s) with s chosen so that both
 // factors have the same largest magnitude (s = 1 for FP32): the product is
 // unchanged and 16-bit storage keeps both factors away from the subnormals.
+// With `lo` set, each scaled value x is stored as the 16-bit high part
+// h = round(x) in dst and the 16-bit remainder round(x - h) in lo.
 template <class T>
-__global__ void aca_pack(AcaDev D, const PackItem* items, int nitems, const Chunk* chunks, T* dst)
+__device__ __forceinline__ void store_split(T* dst, T* lo, int64_t i, float x)
+{
+    const T h = to_store<T>(x);
+    dst[i] = h;
+    if (lo) lo[i] = to_store<T>(x - (float)h);
+}
+template <class T>
+__global__ void aca_pack(AcaDev D, const PackItem* items, int nitems, const Chunk* chunks, T* dst, T* lo)
 {
     __shared__ float red[2][32];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -1026,13 +1035,13 @@ __global__ void aca_pack(AcaDev D, const PackItem* items, int nitems, const Chun
             }
             const float sv = 1.f / su;
             for (int j = threadIdx.x; j < p.n; j += blockDim.x)
-                dst[p.voff_dst + ((int64_t)g * p.r + p.l) * p.n8 + j] =
-                    to_store<T>(sv * D.pool[vs + (int64_t)g * p.n + j]);
+                store_split<T>(dst, lo, p.voff_dst + ((int64_t)g * p.r + p.l) * p.n8 + j,
+                               sv * D.pool[vs + (int64_t)g * p.n + j]);
             for (int c = p.c0; c < p.c1; ++c) {
                 const Chunk ch = chunks[c];
                 for (int i = threadIdx.x; i < ch.m; i += blockDim.x)
-                    dst[p.uoff_dst + ch.off + ((int64_t)g * p.r + p.l) * ch.m8 + i] =
-                        to_store<T>(su * D.pool[us + (int64_t)g * p.m + ch.rbeg + i]);
+                    store_split<T>(dst, lo, p.uoff_dst + ch.off + ((int64_t)g * p.r + p.l) * ch.m8 + i,
+                                   su * D.pool[us + (int64_t)g * p.m + ch.rbeg + i]);
             }
         }
     }
@@ -1056,6 +1065,10 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
     int64_t aca_steps = 0;
     AcaDev D{};
     std::vector<void*> tmp;   // freed at the end
+    int64_t scratch = 0;      // bytes of ACA scratch held now (tmp, pool, dot list)
+    auto note_peak = [&](int64_t extra) {
+        op.info.peak_bytes = std::max<int64_t>(op.info.peak_bytes, op.info.device_bytes + scratch + extra);
+    };
     auto talloc = [&](void** p, size_t bytes) -> int {
         cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 1, s);
         if (e != cudaSuccess) {
@@ -1063,6 +1076,8 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
             return RT_ENOMEM;
         }
         tmp.push_back(*p);
+        scratch += (int64_t)(bytes ? bytes : 1);
+        note_peak(0);
         return RT_OK;
     };
     auto cleanup = [&]() {
@@ -1148,6 +1163,8 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
             }
         }
         D.pool = pool;
+        scratch += (int64_t)sizeof(float) * pool_cap;
+        note_peak(0);
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1173,6 +1190,8 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
                     return RT_ENOMEM;
                 }
                 RT_CUDA_TRY(cudaMemcpyAsync(np, pool, sizeof(float) * pool_used, cudaMemcpyDeviceToDevice, s));
+                note_peak((int64_t)sizeof(float) * ncap);   // old and new pool both live here
+                scratch += (int64_t)sizeof(float) * (ncap - pool_cap);
                 cudaFreeAsync(pool, s);
                 pool = np;
                 pool_cap = ncap;
@@ -1248,8 +1267,11 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
                 for (int l = 0; l <= h_rank[act[ai].b]; ++l) dots.push_back({ai, l});
             if ((int64_t)dots.size() > dot_cap) {
                 if (d_dot) cudaFreeAsync(d_dot, s);
+                scratch -= (int64_t)sizeof(DotItem) * dot_cap;
                 dot_cap = (int64_t)dots.size() * 2;
                 RT_CUDA_TRY(cudaMallocAsync((void**)&d_dot, sizeof(DotItem) * dot_cap, s));
+                scratch += (int64_t)sizeof(DotItem) * dot_cap;
+                note_peak(0);
             }
             RT_CUDA_TRY(cudaMemcpyAsync(d_dot, dots.data(), sizeof(DotItem) * dots.size(), cudaMemcpyHostToDevice, s));
             aca_dots<<<(int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)dots.size() + 7) / 8, (int64_t)sms * 32)),
@@ -1270,6 +1292,7 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
             final_rank[b] = h_rank[b];
         }
         if (d_dot) cudaFreeAsync(d_dot, s);
+        scratch -= (int64_t)sizeof(DotItem) * dot_cap;
         #undef TA
     }
     cudaEventRecord(ev1, s);
@@ -1338,24 +1361,27 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
         RT_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), sizeof(PackItem) * items.size(), cudaMemcpyHostToDevice, s));
         RT_CUDA_TRY(cudaMemcpyAsync(d_chunks, op.far_chunks.data(), sizeof(Chunk) * op.far_chunks.size(),
                                     cudaMemcpyHostToDevice, s));
-        const int grid = (int)std::min<size_t>(items.size(), 152 * 64);
-        const int ni = (int)items.size();
-        if (op.far_prec == RT_PREC_F32) aca_pack<float><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, (float*)d);
-        else if (op.far_prec == RT_PREC_BF16)
-            aca_pack<__nv_bfloat16><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, (__nv_bfloat16*)d);
-        else aca_pack<__half><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, (__half*)d);
-        RT_CUDA_TRY(cudaGetLastError());
+        char* dl = nullptr;
         if (op.refine && op.far_prec != RT_PREC_F32) {
-            // FP32 copy of the far field in the same layout, for refinement sweeps
-            if ((rc = dev_alloc(op, &op.d_far32, (size_t)far_elems, err))) {
+            // 16-bit remainders in the same layout, for refinement sweeps
+            if ((rc = dev_alloc(op, &dl, (size_t)far_elems * esz, err))) {
                 if (pool) cudaFreeAsync(pool, s);
                 cleanup();
                 return rc;
             }
-            RT_CUDA_TRY(cudaMemsetAsync(op.d_far32, 0, sizeof(float) * (size_t)far_elems, s));
-            aca_pack<float><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, op.d_far32);
-            RT_CUDA_TRY(cudaGetLastError());
+            RT_CUDA_TRY(cudaMemsetAsync(dl, 0, (size_t)far_elems * esz, s));
+            op.d_far_lo = dl;
         }
+        note_peak(0);   // packed far field (and remainders) next to the pool
+        const int grid = (int)std::min<size_t>(items.size(), 152 * 64);
+        const int ni = (int)items.size();
+        if (op.far_prec == RT_PREC_F32)
+            aca_pack<float><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, (float*)d, nullptr);
+        else if (op.far_prec == RT_PREC_BF16)
+            aca_pack<__nv_bfloat16><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, (__nv_bfloat16*)d,
+                                                         (__nv_bfloat16*)dl);
+        else aca_pack<__half><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, (__half*)d, (__half*)dl);
+        RT_CUDA_TRY(cudaGetLastError());
         cudaFreeAsync(d_items, s);
         cudaFreeAsync(d_chunks, s);
     }

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) batch_apply_kernel(const BatchInst* __res
         const BatchInst I = insts[wk.inst];
         const int g = I.fgroup[wk.f];
         if (wk.kind == 1) {
-            hmv_p1_body<float>(items[wk.idx], wk.f, g, I.rows, I.far, X + I.voff, I.W, I.N);
+            hmv_p1_body<float>(items[wk.idx], wk.f, g, I.rows, I.far, nullptr, X + I.voff, I.W, I.N);
             __threadfence();   // every writer publishes its w values before the count
             __syncthreads();
             if (threadIdx.x == 0) atomicAdd(&done1[wk.inst], 1);
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) batch_apply_kernel(const BatchInst* __res
                 __threadfence();
             }
             __syncthreads();
-            hmv_p2_body<float, true>(I.leaves[wk.idx], wk.f, g, I.segs, I.far, I.nearp, X + I.voff, I.W,
+            hmv_p2_body<float, true>(I.leaves[wk.idx], wk.f, g, I.segs, I.far, nullptr, I.nearp, X + I.voff, I.W,
                                      Y + I.voff, I.N, red);
         }
     }
@@ -402,7 +402,7 @@ static int build_works(Batch& B, int p1_bytes, std::vector<P1Item>& items, std::
     return RT_OK;
 }
 
-static int upload_works(Batch& B, int p1_bytes, std::string& err)
+static int upload_works(Batch& B, int p1_bytes, cudaStream_t s, std::string& err)
 {
     std::vector<P1Item> items;
     std::vector<BatchWork> works;
@@ -428,6 +428,7 @@ static int upload_works(Batch& B, int p1_bytes, std::string& err)
         I.voff = B.voff[b];
         I.toff = B.toff[b];
     }
+    if (B.d_items || B.d_works) RT_CUDA_TRY(cudaStreamSynchronize(s));   // the previous lists may be in use
     if (B.d_items) cudaFree(B.d_items);
     if (B.d_works) cudaFree(B.d_works);
     B.allocs.erase(std::remove(B.allocs.begin(), B.allocs.end(), (void*)B.d_items), B.allocs.end());
@@ -435,9 +436,9 @@ static int upload_works(Batch& B, int p1_bytes, std::string& err)
     int rc;
     if ((rc = balloc(B, &B.d_items, items.size(), err))) return rc;
     if ((rc = balloc(B, &B.d_works, works.size(), err))) return rc;
-    RT_CUDA_TRY(cudaMemcpy(B.d_items, items.data(), sizeof(P1Item) * items.size(), cudaMemcpyHostToDevice));
-    RT_CUDA_TRY(cudaMemcpy(B.d_works, works.data(), sizeof(BatchWork) * works.size(), cudaMemcpyHostToDevice));
-    RT_CUDA_TRY(cudaMemcpy(B.d_inst, hi.data(), sizeof(BatchInst) * hi.size(), cudaMemcpyHostToDevice));
+    RT_CUDA_TRY(cudaMemcpyAsync(B.d_items, items.data(), sizeof(P1Item) * items.size(), cudaMemcpyHostToDevice, s));
+    RT_CUDA_TRY(cudaMemcpyAsync(B.d_works, works.data(), sizeof(BatchWork) * works.size(), cudaMemcpyHostToDevice, s));
+    RT_CUDA_TRY(cudaMemcpyAsync(B.d_inst, hi.data(), sizeof(BatchInst) * hi.size(), cudaMemcpyHostToDevice, s));
     B.nworks = (int)works.size();
     B.p1_bytes = p1_bytes;
     return RT_OK;
@@ -469,7 +470,7 @@ static int autotune(Batch& B, cudaStream_t s, std::string& err)
     const auto t0 = std::chrono::steady_clock::now();
     int rc;
     for (int sz : sizes) {
-        if ((rc = upload_works(B, sz, err))) return rc;
+        if ((rc = upload_works(B, sz, s, err))) return rc;
         for (int ps : per_sm) {
             B.ctas = sms * ps;
             if ((rc = launch_apply(B, B.d_xt, B.d_yt, nullptr, s, err))) return rc;   // warm
@@ -491,7 +492,7 @@ static int autotune(Batch& B, cudaStream_t s, std::string& err)
     cudaEventDestroy(e1);
     B.ctas_per_sm = bp;
     B.ctas = sms * bp;
-    if ((rc = upload_works(B, bs, err))) return rc;
+    if ((rc = upload_works(B, bs, s, err))) return rc;
     B.tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return RT_OK;
 }
@@ -606,18 +607,18 @@ int rt_build_batch(const rt_problem* probs, int64_t count, const rt_hparams* hp,
         !chk(balloc(B, &B.d_T, B.total_vert, err)) && !chk(balloc(B, &B.d_active, count, err)) &&
         !chk(balloc(B, &B.d_done_now, count, err)) && !chk(balloc(B, &B.d_iters, count, err)) &&
         !chk(balloc(B, &B.d_nactive, 1, err))) {
-        cudaMemcpy(B.d_voff, B.voff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice);
-        cudaMemcpy(B.d_toff, B.toff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice);
-        cudaMemset(B.d_err, 0, sizeof(int));
-        cudaMemset(B.d_xt, 0, sizeof(float) * B.total_vec);
+        cudaMemcpyAsync(B.d_voff, B.voff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(B.d_toff, B.toff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(B.d_err, 0, sizeof(int), s);
+        cudaMemsetAsync(B.d_xt, 0, sizeof(float) * B.total_vec, s);
         for (int64_t k = 0; k < count; ++k) {
             const Operator& op = B.ops[k]->op;
-            cudaMemcpy(B.d_SE + B.voff[k], op.d_SE, sizeof(float) * op.F * op.N, cudaMemcpyDeviceToDevice);
+            cudaMemcpyAsync(B.d_SE + B.voff[k], op.d_SE, sizeof(float) * op.F * op.N, cudaMemcpyDeviceToDevice, s);
         }
         int sms = 148;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         B.ctas = sms * B.ctas_per_sm;
-        chk(upload_works(B, B.p1_bytes, err));
+        chk(upload_works(B, B.p1_bytes, s, err));
         if (rc == RT_OK && tune) chk(autotune(B, s, err));
     }
     if (rc == RT_OK) {
@@ -764,7 +765,8 @@ int rt_solve_batch(rt_batch* h, const rt_solve_opts* o, float* J, double* T, int
         stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     if (herr) {
-        cudaMemset(B.d_err, 0, sizeof(int));
+        cudaMemsetAsync(B.d_err, 0, sizeof(int), s);
+        cudaStreamSynchronize(s);
         return bfail(RT_ETIMEOUT, "a bounded device wait gave up or a Newton solve failed");
     }
     if (nactive > 0) return bfail(RT_ENOCONV, "some instances did not reach tol within max_iter");

@@ -20,14 +20,6 @@ int fail(int code, const std::string& msg)
     return code;
 }
 
-void release(rt::Operator& op)
-{
-    for (void* p : op.allocations)
-        if (p) cudaFree(p);
-    op.allocations.clear();
-    if (op.cap_stream) cudaStreamDestroy(op.cap_stream);
-    op.cap_stream = nullptr;
-}
 
 double planck_host(double nu, double T)
 {
@@ -96,20 +88,17 @@ int upload(rt::Operator& op, T** dst, const std::vector<T>& src, std::string& er
 {
     int rc = rt::dev_alloc(op, dst, src.size(), err);
     if (rc) return rc;
-    cudaError_t e = cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        err = std::string("cudaMemcpy: ") + cudaGetErrorString(e);
-        return RT_ECUDA;
-    }
-    return RT_OK;
+    return rt::upload_async(op, *dst, src.data(), src.size(), err);
 }
 
-int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream_t s, std::string& err)
+int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream_t s, std::string& err,
+          rt::Plan* pre)
 {
     using namespace rt;
     int rc;
     cudaEvent_t e0, e1;
     RT_CUDA_TRY(cudaGetDevice(&op.device));
+    op.stream = s;
     const int64_t N = P->mesh.n_vert, T = P->mesh.n_tet;
     op.N = (int)N;
     op.T = (int)T;
@@ -157,7 +146,8 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
     if (op.mode == RT_MODE_HMATRIX) {
-        if ((rc = plan_build(P->mesh.xyz, N, op.leaf, op.eta, op.adm, op.plan, err))) return rc;
+        if (pre) op.plan = std::move(*pre);   // computed earlier for the same mesh and parameters
+        else if ((rc = plan_build(P->mesh.xyz, N, op.leaf, op.eta, op.adm, op.plan, err))) return rc;
     } else {
         op.plan = Plan();
         op.plan.N = (int)N;
@@ -333,10 +323,45 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
     I.n_far = op.n_far;
     I.n_dense_fallback = op.n_fallback;
     I.compression = 1.0 - (double)I.stored_entries / ((double)N * (double)N);
+    I.peak_bytes = std::max(I.peak_bytes, I.device_bytes);
     return RT_OK;
 }
 
 }  // namespace
+
+namespace rt {
+int validate_problem(const rt_problem* P, const rt_hparams* H, std::string& err)
+{
+    const int rc = validate(P, H);
+    if (rc) err = g_err;
+    return rc;
+}
+
+int build_operator(Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream_t s, std::string& err,
+                   Plan* pre)
+{
+    try {
+        return build(op, P, H, s, err, pre);
+    } catch (const std::bad_alloc&) {
+        err = "host allocation failed";
+        return RT_ENOMEM;
+    } catch (...) {
+        err = "unexpected exception during build";
+        return RT_EINVAL;
+    }
+}
+
+void set_last_error(const std::string& msg) { g_err = msg; }
+
+void operator_release(Operator& op, cudaStream_t s)
+{
+    for (void* p : op.allocations)
+        if (p) cudaFreeAsync(p, s);
+    op.allocations.clear();
+    if (op.cap_stream) cudaStreamDestroy(op.cap_stream);
+    op.cap_stream = nullptr;
+}
+}  // namespace rt
 
 extern "C" {
 
@@ -349,18 +374,10 @@ int rt_build_operator(const rt_problem* prob, const rt_hparams* hp, void* stream
     rt_operator* h = new (std::nothrow) rt_operator();
     if (!h) return fail(RT_ENOMEM, "host allocation failed");
     std::string err;
-    try {
-        rc = build(h->op, prob, hp, (cudaStream_t)stream, err);
-    } catch (const std::bad_alloc&) {
-        rc = RT_ENOMEM;
-        err = "host allocation failed";
-    } catch (...) {
-        rc = RT_EINVAL;
-        err = "unexpected exception during build";
-    }
+    rc = rt::build_operator(h->op, prob, hp, (cudaStream_t)stream, err, nullptr);
     if (rc) {
+        rt::operator_release(h->op, (cudaStream_t)stream);
         cudaStreamSynchronize((cudaStream_t)stream);
-        release(h->op);
         delete h;
         return fail(rc, err);
     }
@@ -441,8 +458,10 @@ int rt_solve_fixed_point(rt_operator* h, const rt_solve_opts* opts, void* J_dev,
 void rt_free(rt_operator* h)
 {
     if (!h) return;
+    // the operator may still be read by work the caller queued on any stream
     cudaDeviceSynchronize();
-    release(h->op);
+    rt::operator_release(h->op, nullptr);
+    cudaStreamSynchronize(nullptr);
     delete h;
 }
 

@@ -84,7 +84,7 @@ int hmatvec_prepare(Operator& op, std::string& err)
     int rc;
     int* d_fg = nullptr;
     if ((rc = dev_alloc(op, &d_fg, op.F, err))) return rc;
-    RT_CUDA_TRY(cudaMemcpy(d_fg, op.fgroup.data(), sizeof(int) * op.F, cudaMemcpyHostToDevice));
+    if ((rc = upload_async(op, d_fg, op.fgroup.data(), op.F, err))) return rc;
     op.d_fq_group = d_fg;
     // frequency table for the solver: nu, w c (1-a), a, group
     {
@@ -96,7 +96,7 @@ int hmatvec_prepare(Operator& op, std::string& err)
             fq[4 * f + 3] = (double)op.fgroup[f];
         }
         if ((rc = dev_alloc(op, &op.d_fq, fq.size(), err))) return rc;
-        RT_CUDA_TRY(cudaMemcpy(op.d_fq, fq.data(), sizeof(double) * fq.size(), cudaMemcpyHostToDevice));
+        if ((rc = upload_async(op, op.d_fq, fq.data(), fq.size(), err))) return rc;
     }
     const size_t esz = op.vec64 ? 8 : 4;
     const int64_t N = op.N, F = op.F;
@@ -189,10 +189,10 @@ int hmatvec_prepare(Operator& op, std::string& err)
     if ((rc = dev_alloc(op, &d_rows, rows.size(), err))) return rc;
     if ((rc = dev_alloc(op, &d_l, leaves.size(), err))) return rc;
     if ((rc = dev_alloc(op, &d_s, segs.size(), err))) return rc;
-    if (!items.empty()) RT_CUDA_TRY(cudaMemcpy(d_it, items.data(), sizeof(P1Item) * items.size(), cudaMemcpyHostToDevice));
-    if (!rows.empty()) RT_CUDA_TRY(cudaMemcpy(d_rows, rows.data(), sizeof(P1Row) * rows.size(), cudaMemcpyHostToDevice));
-    RT_CUDA_TRY(cudaMemcpy(d_l, leaves.data(), sizeof(P2Leaf) * leaves.size(), cudaMemcpyHostToDevice));
-    if (!segs.empty()) RT_CUDA_TRY(cudaMemcpy(d_s, segs.data(), sizeof(P2Seg) * segs.size(), cudaMemcpyHostToDevice));
+    if ((rc = upload_async(op, d_it, items.data(), items.size(), err))) return rc;
+    if ((rc = upload_async(op, d_rows, rows.data(), rows.size(), err))) return rc;
+    if ((rc = upload_async(op, d_l, leaves.data(), leaves.size(), err))) return rc;
+    if ((rc = upload_async(op, d_s, segs.data(), segs.size(), err))) return rc;
     op.d_p1_items = d_it;
     op.d_p1_rows = d_rows;
     op.h_p1_rows.assign(reinterpret_cast<const char*>(rows.data()),
@@ -220,32 +220,28 @@ int hmatvec_prepare(Operator& op, std::string& err)
 static int launch_hmv(Operator& op, const float* x, float* w, float* y, cudaStream_t s, std::string& err)
 {
     const int N = op.N, F = op.F;
-    const int far_prec = (op.use_far32 && op.d_far32) ? RT_PREC_F32 : op.far_prec;
-    const void* farp = (op.use_far32 && op.d_far32) ? (const void*)op.d_far32 : op.d_far;
+    const bool lo = op.use_lo && op.d_far_lo;   // refinement sweep: high + low parts
     const P1Item* it = (const P1Item*)op.d_p1_items;
     const P1Row* rw = (const P1Row*)op.d_p1_rows;
-    if (op.n_p1 > 0) {
-        dim3 g1(op.n_p1, F);
-        if (far_prec == RT_PREC_F32)
-            hmv_phase1<float><<<g1, 256, 0, s>>>(it, rw, (const float*)farp, x, w, N, op.d_fq_group);
-        else if (far_prec == RT_PREC_BF16)
-            hmv_phase1<__nv_bfloat16><<<g1, 256, 0, s>>>(it, rw, (const __nv_bfloat16*)farp, x, w, N,
-                                                         op.d_fq_group);
-        else
-            hmv_phase1<__half><<<g1, 256, 0, s>>>(it, rw, (const __half*)farp, x, w, N, op.d_fq_group);
-        RT_CUDA_TRY(cudaGetLastError());
-    }
-    dim3 g2(op.n_p2, F);
     const P2Leaf* lv = (const P2Leaf*)op.d_p2_leaf;
     const P2Seg* sg = (const P2Seg*)op.d_p2_segs;
-    if (far_prec == RT_PREC_F32)
-        hmv_phase2<float><<<g2, 256, 0, s>>>(lv, sg, (const float*)farp, op.d_near, x, w, y, N, op.d_fq_group);
-    else if (far_prec == RT_PREC_BF16)
-        hmv_phase2<__nv_bfloat16><<<g2, 256, 0, s>>>(lv, sg, (const __nv_bfloat16*)farp, op.d_near, x, w, y, N,
-                                                     op.d_fq_group);
-    else
-        hmv_phase2<__half><<<g2, 256, 0, s>>>(lv, sg, (const __half*)farp, op.d_near, x, w, y, N,
-                                              op.d_fq_group);
+    dim3 g1(op.n_p1, F), g2(op.n_p2, F);
+#define RT_HMV(T, LO)                                                                                             \
+    do {                                                                                                          \
+        const T* fp = (const T*)op.d_far;                                                                         \
+        const T* fl = (const T*)op.d_far_lo;                                                                      \
+        if (op.n_p1 > 0) hmv_phase1<T, LO><<<g1, 256, 0, s>>>(it, rw, fp, fl, x, w, N, op.d_fq_group);            \
+        hmv_phase2<T, LO><<<g2, 256, 0, s>>>(lv, sg, fp, fl, op.d_near, x, w, y, N, op.d_fq_group);               \
+    } while (0)
+    if (op.far_prec == RT_PREC_F32) RT_HMV(float, false);
+    else if (op.far_prec == RT_PREC_BF16) {
+        if (lo) RT_HMV(__nv_bfloat16, true);
+        else RT_HMV(__nv_bfloat16, false);
+    } else {
+        if (lo) RT_HMV(__half, true);
+        else RT_HMV(__half, false);
+    }
+#undef RT_HMV
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
 }
@@ -268,7 +264,7 @@ static int launch_dense(Operator& op, const void* X, void* Y, cudaStream_t s, st
 int apply_tree(Operator& op, const void* X, void* Y, cudaStream_t s, std::string& err)
 {
     if (op.mode == RT_MODE_DENSE) return launch_dense(op, X, Y, s, err);
-    if (op.tc_enabled && !op.use_far32) return tc_apply(op, (const float*)X, (float*)Y, s, err);
+    if (op.tc_enabled && !op.use_lo) return tc_apply(op, (const float*)X, (float*)Y, s, err);
     return launch_hmv(op, (const float*)X, op.d_w, (float*)Y, s, err);
 }
 

@@ -104,11 +104,34 @@ __device__ __forceinline__ float4 load4(const __half* p)
     return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
-// phase 1 body: one item (a run of rank rows) for frequency f of group g, 256 threads
-template <class T>
+// add the low 16-bit parts of a split far field (kLo) to values just loaded
+template <bool kLo, class T, int n>
+__device__ __forceinline__ void add_lo16(const T* __restrict__ lo, float* v)
+{
+    if constexpr (kLo) {
+        float l[n];
+        load16(lo, l);
+#pragma unroll
+        for (int e = 0; e < n; ++e) v[e] += l[e];
+    }
+}
+template <bool kLo, class T>
+__device__ __forceinline__ float4 add_lo4(const T* __restrict__ lo, float4 v)
+{
+    if constexpr (kLo) {
+        const float4 l = load4(lo);
+        v.x += l.x; v.y += l.y; v.z += l.z; v.w += l.w;
+    }
+    return v;
+}
+
+// phase 1 body: one item (a run of rank rows) for frequency f of group g, 256 threads.
+// kLo: the far field is stored as 16-bit high parts `far` plus 16-bit
+// remainders `far_lo` at the same offsets (refinement sweeps read both).
+template <class T, bool kLo = false>
 __device__ __forceinline__ void hmv_p1_body(const P1Item it, int f, int g, const P1Row* __restrict__ rows,
-                                            const T* __restrict__ far, const float* __restrict__ X,
-                                            float* __restrict__ W, int N)
+                                            const T* __restrict__ far, const T* __restrict__ far_lo,
+                                            const float* __restrict__ X, float* __restrict__ W, int N)
 {
     constexpr int VW = VecW<T>::n;
     const int sw = it.sw;
@@ -125,7 +148,9 @@ __device__ __forceinline__ void hmv_p1_body(const P1Item it, int f, int g, const
         P1Row rw{};
         if (ok) {
             rw = rows[ri];
-            const T* __restrict__ v = far + rw.v + (int64_t)g * rw.gstride;
+            const int64_t vo = rw.v + (int64_t)g * rw.gstride;
+            const T* __restrict__ v = far + vo;
+            const T* __restrict__ vl = kLo ? far_lo + vo : nullptr;
             const float* __restrict__ x = xf + rw.col0;
             const int nv = rw.n - rw.n % VW;
             float s0 = 0.f, s1 = 0.f;
@@ -134,6 +159,8 @@ __device__ __forceinline__ void hmv_p1_body(const P1Item it, int f, int g, const
                 float a[VW], b[VW];
                 load16(v + j, a);
                 load16(v + j + sw * VW, b);
+                add_lo16<kLo, T, VW>(vl + j, a);
+                add_lo16<kLo, T, VW>(vl + j + sw * VW, b);
 #pragma unroll
                 for (int e = 0; e < VW; ++e) {
                     s0 += a[e] * __ldg(x + j + e);
@@ -143,10 +170,11 @@ __device__ __forceinline__ void hmv_p1_body(const P1Item it, int f, int g, const
             for (; j < nv; j += sw * VW) {
                 float a[VW];
                 load16(v + j, a);
+                add_lo16<kLo, T, VW>(vl + j, a);
 #pragma unroll
                 for (int e = 0; e < VW; ++e) s0 += a[e] * __ldg(x + j + e);
             }
-            for (int t = nv + sl; t < rw.n; t += sw) s0 += to_f(v[t]) * __ldg(x + t);
+            for (int t = nv + sl; t < rw.n; t += sw) s0 += (to_f(v[t]) + (kLo ? to_f(vl[t]) : 0.f)) * __ldg(x + t);
             s = s0 + s1;
         }
         for (int o = sw >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, sw);
@@ -155,13 +183,14 @@ __device__ __forceinline__ void hmv_p1_body(const P1Item it, int f, int g, const
 }
 
 // phase 1: grid (items, F), 256 threads
-template <class T>
+template <class T, bool kLo>
 __global__ void __launch_bounds__(256) hmv_phase1(const P1Item* __restrict__ items, const P1Row* __restrict__ rows,
-                                                  const T* __restrict__ far, const float* __restrict__ X,
-                                                  float* __restrict__ W, int N, const int* __restrict__ fgroup)
+                                                  const T* __restrict__ far, const T* __restrict__ far_lo,
+                                                  const float* __restrict__ X, float* __restrict__ W, int N,
+                                                  const int* __restrict__ fgroup)
 {
     const int f = blockIdx.y;
-    hmv_p1_body<T>(items[blockIdx.x], f, fgroup[f], rows, far, X, W, N);
+    hmv_p1_body<T, kLo>(items[blockIdx.x], f, fgroup[f], rows, far, far_lo, X, W, N);
 }
 
 // phase-2 reads of w: through the read-only path, or L2-coherent when w is
@@ -175,9 +204,10 @@ __device__ __forceinline__ float ld_w(const float* p)
 
 // phase 2 body: one leaf for frequency f of group g, 256 threads;
 // thread owns rows 4c..4c+3 and a slice of each segment's count
-template <class T, bool kCoherentW>
+template <class T, bool kCoherentW, bool kLo = false>
 __device__ __forceinline__ void hmv_p2_body(const P2Leaf L, int f, int g, const P2Seg* __restrict__ segs,
-                                            const T* __restrict__ far, const float* __restrict__ nearp,
+                                            const T* __restrict__ far, const T* __restrict__ far_lo,
+                                            const float* __restrict__ nearp,
                                             const float* __restrict__ X, const float* __restrict__ W,
                                             float* __restrict__ Y, int N, float4* red)
 {
@@ -190,18 +220,20 @@ __device__ __forceinline__ void hmv_p2_body(const P2Leaf L, int f, int g, const 
         for (int si = L.seg0; si < L.seg0 + L.nseg; ++si) {
             const P2Seg sg = segs[si];
             if (sg.kind == 0) {
-                const T* __restrict__ a = far + sg.a + (int64_t)g * sg.gstride + 4 * c;
+                const int64_t ao = sg.a + (int64_t)g * sg.gstride + 4 * c;
+                const T* __restrict__ a = far + ao;
+                const T* __restrict__ al = kLo ? far_lo + ao : nullptr;
                 const float* __restrict__ w = W + sg.vbase + (int64_t)f * sg.count;
                 int k = slice;
                 for (; k + nslice < sg.count; k += 2 * nslice) {
-                    const float4 p = load4(a + (int64_t)k * L.m8);
-                    const float4 q = load4(a + (int64_t)(k + nslice) * L.m8);
+                    const float4 p = add_lo4<kLo>(al + (int64_t)k * L.m8, load4(a + (int64_t)k * L.m8));
+                    const float4 q = add_lo4<kLo>(al + (int64_t)(k + nslice) * L.m8, load4(a + (int64_t)(k + nslice) * L.m8));
                     const float wp = ld_w<kCoherentW>(w + k), wq = ld_w<kCoherentW>(w + k + nslice);
                     acc0.x += p.x * wp; acc0.y += p.y * wp; acc0.z += p.z * wp; acc0.w += p.w * wp;
                     acc1.x += q.x * wq; acc1.y += q.y * wq; acc1.z += q.z * wq; acc1.w += q.w * wq;
                 }
                 for (; k < sg.count; k += nslice) {
-                    const float4 p = load4(a + (int64_t)k * L.m8);
+                    const float4 p = add_lo4<kLo>(al + (int64_t)k * L.m8, load4(a + (int64_t)k * L.m8));
                     const float wp = ld_w<kCoherentW>(w + k);
                     acc0.x += p.x * wp; acc0.y += p.y * wp; acc0.z += p.z * wp; acc0.w += p.w * wp;
                 }
@@ -242,15 +274,16 @@ __device__ __forceinline__ void hmv_p2_body(const P2Leaf L, int f, int g, const 
 }
 
 // phase 2: grid (leaves, F), 256 threads
-template <class T>
+template <class T, bool kLo>
 __global__ void __launch_bounds__(256) hmv_phase2(const P2Leaf* __restrict__ leaves, const P2Seg* __restrict__ segs,
-                                                  const T* __restrict__ far, const float* __restrict__ nearp,
-                                                  const float* __restrict__ X, const float* __restrict__ W,
-                                                  float* __restrict__ Y, int N, const int* __restrict__ fgroup)
+                                                  const T* __restrict__ far, const T* __restrict__ far_lo,
+                                                  const float* __restrict__ nearp, const float* __restrict__ X,
+                                                  const float* __restrict__ W, float* __restrict__ Y, int N,
+                                                  const int* __restrict__ fgroup)
 {
     __shared__ float4 red[256];
     const int f = blockIdx.y;
-    hmv_p2_body<T, false>(leaves[blockIdx.x], f, fgroup[f], segs, far, nearp, X, W, Y, N, red);
+    hmv_p2_body<T, false, kLo>(leaves[blockIdx.x], f, fgroup[f], segs, far, far_lo, nearp, X, W, Y, N, red);
 }
 
 

@@ -174,9 +174,10 @@ struct Operator {
     std::vector<int> dense_chunk_ptr, far_chunk_ptr;   // CSR over the chunk arrays
     std::vector<Chunk> dense_chunks, far_chunks;
     void* d_far = nullptr;      // far U/V (float, bf16 or f16)
-    float* d_far32 = nullptr;   // FP32 copy of a BF16/FP16 far field (refinement), same layout
+    void* d_far_lo = nullptr;   // refinement: 16-bit remainders (value - high part) of a BF16/FP16
+                                // far field, same layout as d_far
     int refine = 0;
-    int use_far32 = 0;          // apply with the FP32 copy (set by the solver)
+    int use_lo = 0;             // apply with high + low parts (set by the solver)
     std::vector<int64_t> far_v_off, far_u_off;
     // matvec work lists (device)
     void* d_p1_items = nullptr; int n_p1 = 0;
@@ -215,6 +216,9 @@ struct Operator {
     // stats
     rt_info info{};
     std::vector<void*> allocations;
+    // stream that orders the operator's allocations and host uploads (the
+    // build stream; the solve stream while a solve allocates its vectors)
+    cudaStream_t stream = nullptr;
 };
 
 // ---- kernels / drivers implemented in the .cu files -----------------------
@@ -254,9 +258,11 @@ int dev_alloc(Operator& op, T** p, size_t count, std::string& err)
 {
     *p = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    // stream-ordered: no device-wide synchronisation, so builds on other
+    // streams keep running
+    cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), op.stream);
     if (e != cudaSuccess) {
-        err = std::string("cudaMalloc(") + std::to_string(count * sizeof(T)) + " bytes): " + cudaGetErrorString(e);
+        err = std::string("cudaMallocAsync(") + std::to_string(count * sizeof(T)) + " bytes): " + cudaGetErrorString(e);
         *p = nullptr;
         return RT_ENOMEM;
     }
@@ -264,6 +270,29 @@ int dev_alloc(Operator& op, T** p, size_t count, std::string& err)
     op.info.device_bytes += (int64_t)(count * sizeof(T));
     return RT_OK;
 }
+
+// host -> device copy ordered on the operator's stream (the source is staged
+// before the call returns, so it may be a temporary)
+template <class T>
+int upload_async(Operator& op, T* dst, const T* src, size_t count, std::string& err)
+{
+    if (count == 0) return RT_OK;
+    cudaError_t e = cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, op.stream);
+    if (e != cudaSuccess) {
+        err = std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e);
+        return RT_ECUDA;
+    }
+    return RT_OK;
+}
+
+// free every device allocation of the operator, ordered on stream s
+void operator_release(Operator& op, cudaStream_t s);
+// checks and the build behind rt_build_operator (pre: a plan computed for the
+// same mesh and hparams, moved into the operator; may be null)
+int validate_problem(const rt_problem* P, const rt_hparams* H, std::string& err);
+int build_operator(Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream_t s, std::string& err,
+                   Plan* pre);
+void set_last_error(const std::string& msg);
 
 }  // namespace rt
 

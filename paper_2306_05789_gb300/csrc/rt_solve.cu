@@ -233,6 +233,7 @@ static int solve_impl(Operator& op, const rt_solve_opts& o, void* J_out, double*
     const int cap = std::max(1, o.max_iter);
     const int every = std::max(1, o.check_every);
     if (!op.d_J) {
+        op.stream = s;
         V *J, *S, *Y;
         if ((rc = dev_alloc(op, &J, tot, err))) return rc;
         if ((rc = dev_alloc(op, &S, tot, err))) return rc;
@@ -270,14 +271,14 @@ static int solve_impl(Operator& op, const rt_solve_opts& o, void* J_out, double*
     double last = INFINITY;
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
-    int graph_len = 0, graph_far32 = -1;
-    // operators with an FP32 refinement copy start on the low-precision far
-    // field and switch once the residual reaches refine_tol
-    op.use_far32 = (op.d_far32 && !(o.refine_tol > 0.0)) ? 1 : 0;
+    int graph_len = 0, graph_lo = -1;
+    // operators with split (high + low) far fields start on the high parts
+    // alone and switch to both once the residual reaches refine_tol
+    op.use_lo = (op.d_far_lo && !(o.refine_tol > 0.0)) ? 1 : 0;
     while (iters < cap && !converged) {
         const int todo = std::min(every, cap - iters);
         if (o.use_graph) {
-            if (!gexec || graph_len != todo || graph_far32 != op.use_far32) {
+            if (!gexec || graph_len != todo || graph_lo != op.use_lo) {
                 if (gexec) cudaGraphExecDestroy(gexec);
                 if (graph) cudaGraphDestroy(graph);
                 gexec = nullptr;
@@ -297,7 +298,7 @@ static int solve_impl(Operator& op, const rt_solve_opts& o, void* J_out, double*
                 }
                 RT_CUDA_TRY(cudaGraphInstantiate(&gexec, graph, 0));
                 graph_len = todo;
-                graph_far32 = op.use_far32;
+                graph_lo = op.use_lo;
             }
             RT_CUDA_TRY(cudaGraphLaunch(gexec, s));
         } else {
@@ -308,14 +309,14 @@ static int solve_impl(Operator& op, const rt_solve_opts& o, void* J_out, double*
         RT_CUDA_TRY(cudaStreamSynchronize(s));
         for (int k = 0; k < todo; ++k) {
             last = hres[iters + k];
-            if (last <= o.tol && (!op.d_far32 || op.use_far32)) converged = true;
+            if (last <= o.tol && (!op.d_far_lo || op.use_lo)) converged = true;
         }
         iters += todo;
-        if (op.d_far32 && !op.use_far32 && last <= std::max(o.refine_tol, o.tol)) op.use_far32 = 1;
+        if (op.d_far_lo && !op.use_lo && last <= std::max(o.refine_tol, o.tol)) op.use_lo = 1;
     }
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
-    op.use_far32 = 0;
+    op.use_lo = 0;
     int fail = 0;
     RT_CUDA_TRY(cudaMemcpyAsync(&fail, d_ctr + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
     // results back to caller order

@@ -529,12 +529,11 @@ int tc_prepare(Operator& op, std::string& err)
     if ((rc = dev_alloc(op, &d_ln, ln.size(), err))) return rc;
     if ((rc = dev_alloc(op, &d_fs, fs.size(), err))) return rc;
     if ((rc = dev_alloc(op, &d_ns, ns.size(), err))) return rc;
-    if (!blocks.empty())
-        RT_CUDA_TRY(cudaMemcpy(d_b, blocks.data(), sizeof(TcBlock) * blocks.size(), cudaMemcpyHostToDevice));
-    RT_CUDA_TRY(cudaMemcpy(d_lf, lf.data(), sizeof(TcLeaf) * lf.size(), cudaMemcpyHostToDevice));
-    RT_CUDA_TRY(cudaMemcpy(d_ln, ln.data(), sizeof(TcLeaf) * ln.size(), cudaMemcpyHostToDevice));
-    if (!fs.empty()) RT_CUDA_TRY(cudaMemcpy(d_fs, fs.data(), sizeof(TcSeg) * fs.size(), cudaMemcpyHostToDevice));
-    if (!ns.empty()) RT_CUDA_TRY(cudaMemcpy(d_ns, ns.data(), sizeof(NearSeg) * ns.size(), cudaMemcpyHostToDevice));
+    if ((rc = upload_async(op, d_b, blocks.data(), blocks.size(), err))) return rc;
+    if ((rc = upload_async(op, d_lf, lf.data(), lf.size(), err))) return rc;
+    if ((rc = upload_async(op, d_ln, ln.data(), ln.size(), err))) return rc;
+    if ((rc = upload_async(op, d_fs, fs.data(), fs.size(), err))) return rc;
+    if ((rc = upload_async(op, d_ns, ns.data(), ns.size(), err))) return rc;
     op.tc_blocks = d_b;
     op.tc_nblocks = (int)blocks.size();
     op.tc_leaf_far = d_lf;
@@ -548,9 +547,9 @@ int tc_prepare(Operator& op, std::string& err)
     // W as 16-bit hi and lo parts, [F][r16] per block; the padding stays zero
     if ((rc = dev_alloc(op, (char**)&p, (size_t)2 * 2 * std::max<int64_t>(wl, 1), err))) return rc;
     op.tc_w = (float*)p;
-    RT_CUDA_TRY(cudaMemset(p, 0, (size_t)2 * 2 * std::max<int64_t>(wl, 1)));
+    RT_CUDA_TRY(cudaMemsetAsync(p, 0, (size_t)2 * 2 * std::max<int64_t>(wl, 1), op.stream));
     if ((rc = dev_alloc(op, &op.tc_err, 1, err))) return rc;
-    RT_CUDA_TRY(cudaMemset(op.tc_err, 0, sizeof(int)));
+    RT_CUDA_TRY(cudaMemsetAsync(op.tc_err, 0, sizeof(int), op.stream));
     const int smem = tc::kM * tc::kKT * 2 + 2 * op.F * tc::kKT * 2;
     RT_CUDA_TRY(cudaFuncSetAttribute(tc_phase1<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     RT_CUDA_TRY(cudaFuncSetAttribute(tc_phase1<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -608,7 +607,8 @@ int tc_check_error(Operator& op, std::string& err)
 {
     if (!op.tc_enabled) return RT_OK;
     int h = 0;
-    RT_CUDA_TRY(cudaMemcpy(&h, op.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    RT_CUDA_TRY(cudaMemcpyAsync(&h, op.tc_err, sizeof(int), cudaMemcpyDeviceToHost, op.stream));
+    RT_CUDA_TRY(cudaStreamSynchronize(op.stream));
     if (h) {
         err = "tensor-core apply: an mbarrier wait timed out";
         return RT_ETIMEOUT;
