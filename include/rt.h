@@ -143,6 +143,9 @@ typedef struct {
                         far field takes 4 bytes per entry in all, like FP32 storage */
     int tensor_cores; /* 0: use the tcgen05 apply when eligible (one operator group, F a multiple
                          of 16 up to 256, BF16/FP16 far field, leaves <= 128); 1: CUDA cores only */
+    int64_t wave_bytes; /* ACA runs over consecutive waves of admissible blocks whose FP32 term
+                           scratch (estimated at 24 terms per block) stays below this many bytes;
+                           each wave is packed and its scratch freed before the next (0 = 8 GiB) */
 } rt_hparams;
 
 typedef struct rt_operator rt_operator;
@@ -162,6 +165,7 @@ typedef struct {
     int64_t device_bytes;        /* device memory held by the operator */
     double ms_tree, ms_near, ms_aca, ms_pack, ms_source; /* assembly phase times */
     int64_t peak_bytes;          /* largest device footprint during assembly (operator + ACA scratch) */
+    int64_t aca_waves;           /* waves of admissible blocks the ACA ran in */
 } rt_info;
 
 /* Fixed-point options (Section 1.3).  The iteration starts from T = T0 at

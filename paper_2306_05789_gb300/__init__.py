@@ -59,7 +59,7 @@ class RtProblem(ctypes.Structure):
 class RtHparams(ctypes.Structure):
     _fields_ = [("mode", _c_int), ("prec", _c_int), ("far_prec", _c_int), ("aca_eps", _c_dbl), ("leaf", _c_int),
                 ("eta", _c_dbl), ("gauss_pts", _c_int), ("rank_max", _c_int), ("adm", _c_int),
-                ("line_eval", _c_int), ("refine", _c_int), ("tensor_cores", _c_int)]
+                ("line_eval", _c_int), ("refine", _c_int), ("tensor_cores", _c_int), ("wave_bytes", _c_i64)]
 
 
 class RtInfo(ctypes.Structure):
@@ -69,7 +69,7 @@ class RtInfo(ctypes.Structure):
                 ("rank_sum", _c_i64), ("aca_steps", _c_i64), ("entries_evaluated", _c_i64),
                 ("apply_bytes", _c_i64), ("apply_flops", _c_i64), ("device_bytes", _c_i64),
                 ("ms_tree", _c_dbl), ("ms_near", _c_dbl), ("ms_aca", _c_dbl), ("ms_pack", _c_dbl),
-                ("ms_source", _c_dbl), ("peak_bytes", _c_i64)]
+                ("ms_source", _c_dbl), ("peak_bytes", _c_i64), ("aca_waves", _c_i64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -191,11 +191,12 @@ def _stream_ptr(stream):
 
 
 def hparams(mode=RT_MODE_HMATRIX, prec=None, far_prec=RT_PREC_F32, aca_eps=1e-4, leaf=64, eta=2.0, gauss_pts=16,
-            rank_max=0, adm=RT_ADM_GAP, line_eval=RT_LINE_CLOSED, refine=0, tensor_cores=0) -> RtHparams:
+            rank_max=0, adm=RT_ADM_GAP, line_eval=RT_LINE_CLOSED, refine=0, tensor_cores=0,
+            wave_bytes=0) -> RtHparams:
     if prec is None:
         prec = RT_PREC_F32
     return RtHparams(mode, prec, far_prec, aca_eps, leaf, eta, gauss_pts, rank_max, adm, line_eval, refine,
-                     tensor_cores)
+                     tensor_cores, int(wave_bytes))
 
 
 class _ProblemArgs:

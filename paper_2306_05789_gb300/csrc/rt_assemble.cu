@@ -181,6 +181,7 @@ struct AcaActive {
     int64_t cbuf;   // offset of this block's [G][m] column buffer
     int64_t first_row, first_col;   // prefix of n (rows) and m (cols) over the active list
     int64_t uoff, voff;             // pool offsets of this step's u [G][m] and v [G][n]
+    int64_t dot0;                   // first entry of this block's rank+1 dot products this step
     int skip;       // set by the pivot kernel: zero row, no rank this step
 };
 
@@ -777,7 +778,7 @@ struct AcaDev {
     int64_t* used_off;  // [nfar]
     unsigned long long* key;   // [nfar]  row pivot key, then next-row key
     unsigned* rowmax;   // [nfar][G]  max |R_g| of the current row (float bits)
-    double* dots;       // [nfar][rmax+1][G][2]  (u_l.u, v_l.v), l = rank -> (|u|^2, |v|^2)
+    double* dots;       // per step: [dot0 + l][G][2]  (u_l.u, v_l.v), l = rank -> (|u|^2, |v|^2)
     float* pool;
 };
 
@@ -917,7 +918,7 @@ __global__ void __launch_bounds__(256) aca_dots(AcaDev D, const AcaActive* act, 
                 sv += __shfl_xor_sync(0xffffffffu, sv, o);
             }
             if (lane == 0) {
-                double* dst = D.dots + (((int64_t)b * (D.rmax + 1) + di.l) * D.G + g) * 2;
+                double* dst = D.dots + ((a.dot0 + di.l) * D.G + g) * 2;
                 dst[0] = su;
                 dst[1] = sv;
             }
@@ -933,12 +934,12 @@ __global__ void aca_finish(AcaDev D, const AcaActive* act, int na)
         const int b = a.b, r = D.rank[b];
         bool all_done = true;
         for (int g = 0; g < D.G; ++g) {
-            const double* dk = D.dots + (((int64_t)b * (D.rmax + 1) + r) * D.G + g) * 2;
+            const double* dk = D.dots + ((a.dot0 + r) * D.G + g) * 2;
             const double uu = dk[0], vv = dk[1];
             double s = D.norm2[(int64_t)b * D.G + g];
             double cross = 0.0;
             for (int l = 0; l < r; ++l) {
-                const double* dl = D.dots + (((int64_t)b * (D.rmax + 1) + l) * D.G + g) * 2;
+                const double* dl = D.dots + ((a.dot0 + l) * D.G + g) * 2;
                 cross += dl[0] * dl[1];
             }
             s += 2.0 * cross + uu * vv;
@@ -1065,7 +1066,7 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
     int64_t aca_steps = 0;
     AcaDev D{};
     std::vector<void*> tmp;   // freed at the end
-    int64_t scratch = 0;      // bytes of ACA scratch held now (tmp, pool, dot list)
+    int64_t scratch = 0;      // bytes of ACA scratch held now (tmp, pool, dot lists)
     auto note_peak = [&](int64_t extra) {
         op.info.peak_bytes = std::max<int64_t>(op.info.peak_bytes, op.info.device_bytes + scratch + extra);
     };
@@ -1086,17 +1087,72 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
     };
     float* pool = nullptr;
     int64_t pool_cap = 0, pool_used = 0;
+    float ms = 0.f, ms_pack = 0.f;
+    const int esz = op.far_prec == RT_PREC_F32 ? 4 : 2;
+    const bool split = op.refine && op.far_prec != RT_PREC_F32;
 
+    // ---- waves: consecutive runs of far blocks whose ACA terms (estimated at
+    // kWaveRank terms per block) take at most kWaveBytes of FP32 scratch.  Each
+    // wave is approximated, packed into the far storage and its scratch freed
+    // before the next starts, which bounds the assembly's memory peak.
+    constexpr double kWaveRank = 24.0;
+    const int64_t kWaveBytes = op.wave_bytes;
+    std::vector<int> wave_start(1, 0);
+    {
+        double acc = 0.0;
+        for (int b = 0; b < nfar; ++b) {
+            const double est = 4.0 * G * (double)(farb[b].m + farb[b].n) * kWaveRank;
+            if (acc > 0.0 && acc + est > (double)kWaveBytes) {
+                wave_start.push_back(b);
+                acc = 0.0;
+            }
+            acc += est;
+        }
+        wave_start.push_back(nfar);
+    }
+    const int nwaves = (int)wave_start.size() - 1;
+    op.info.aca_waves = nfar > 0 ? nwaves : 0;
+    int nw_max = 0;
+    int64_t summ_max = 0, sumn_max = 0;
+    for (int w = 0; w < nwaves; ++w) {
+        int64_t sm = 0, sn = 0;
+        for (int b = wave_start[w]; b < wave_start[w + 1]; ++b) {
+            sm += farb[b].m;
+            sn += farb[b].n;
+        }
+        nw_max = std::max(nw_max, wave_start[w + 1] - wave_start[w]);
+        summ_max = std::max(summ_max, sm);
+        sumn_max = std::max(sumn_max, sn);
+    }
+
+    // final far storage layout, filled wave by wave
+    op.far_blocks.clear();
+    op.dense_blocks = op.plan.near_blocks;
+    op.rank.clear();
+    op.far_v_off.clear();
+    op.far_u_off.clear();
+    op.far_chunks.clear();
+    op.far_chunk_ptr.assign(1, 0);
+    std::vector<int> far_src;   // ACA block id of each stored far block
+    int64_t far_elems = 0;
+    if (nwaves > 1) {
+        // address range for the largest possible far field: every block at the
+        // rank where dense storage becomes cheaper
+        int64_t bound = 0;
+        std::vector<Chunk> tmpc;
+        for (int b = 0; b < nfar; ++b) {
+            const FarBlock& fb = farb[b];
+            const int64_t rcap = std::min<int64_t>(rmax, (int64_t)fb.m * fb.n / (fb.m + fb.n) + 1);
+            tmpc.clear();
+            bound += (int64_t)G * rcap * ((int64_t)round8(fb.n) + block_chunks(op.plan, fb.row0, fb.m, 1, tmpc));
+        }
+        if ((rc = growbuf_reserve(op.far_buf, (size_t)bound * esz, op.device, err))) return rc;
+        if (split && (rc = growbuf_reserve(op.far_lo_buf, (size_t)bound * esz, op.device, err))) return rc;
+    }
     if (nfar > 0) {
         D.G = G;
         D.rmax = rmax;
         D.eps = op.aca_eps;
-        int64_t sum_m = 0;
-        std::vector<int64_t> used_off(nfar);
-        for (int b = 0; b < nfar; ++b) {
-            used_off[b] = sum_m;
-            sum_m += farb[b].m;
-        }
 #define TA(ptr, bytes)                                       \
     do {                                                     \
         if ((rc = talloc((void**)&(ptr), (bytes)))) {        \
@@ -1104,293 +1160,305 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
             return rc;                                       \
         }                                                    \
     } while (0)
+        // per-block state, sized for the largest wave and indexed by the
+        // block's position in its wave
         FarBlock* d_blk;
-        TA(d_blk, sizeof(FarBlock) * nfar);
-        TA(D.istar, sizeof(int) * nfar);
-        TA(D.jstar, sizeof(int) * nfar);
-        TA(D.rank, sizeof(int) * nfar);
-        TA(D.status, sizeof(int) * nfar);
-        TA(D.norm2, sizeof(double) * nfar * G);
-        TA(D.wscale, sizeof(float) * nfar * G);
-        TA(D.inv, sizeof(float) * nfar * G);
-        TA(D.uoff, sizeof(int64_t) * nfar * rmax);
-        TA(D.voff, sizeof(int64_t) * nfar * rmax);
-        TA(D.used, sum_m);
-        TA(D.used_off, sizeof(int64_t) * nfar);
-        TA(D.key, sizeof(unsigned long long) * nfar);
-        TA(D.rowmax, sizeof(unsigned) * nfar * G);
-        TA(D.dots, sizeof(double) * 2 * (size_t)nfar * (rmax + 1) * G);
+        TA(d_blk, sizeof(FarBlock) * nw_max);
+        TA(D.istar, sizeof(int) * nw_max);
+        TA(D.jstar, sizeof(int) * nw_max);
+        TA(D.rank, sizeof(int) * nw_max);
+        TA(D.status, sizeof(int) * nw_max);
+        TA(D.norm2, sizeof(double) * nw_max * G);
+        TA(D.wscale, sizeof(float) * nw_max * G);
+        TA(D.inv, sizeof(float) * nw_max * G);
+        TA(D.uoff, sizeof(int64_t) * nw_max * rmax);
+        TA(D.voff, sizeof(int64_t) * nw_max * rmax);
+        TA(D.used, summ_max);
+        TA(D.used_off, sizeof(int64_t) * nw_max);
+        TA(D.key, sizeof(unsigned long long) * nw_max);
+        TA(D.rowmax, sizeof(unsigned) * nw_max * G);
         D.blk = d_blk;
-        RT_CUDA_TRY(cudaMemcpyAsync(d_blk, farb.data(), sizeof(FarBlock) * nfar, cudaMemcpyHostToDevice, s));
-        RT_CUDA_TRY(cudaMemsetAsync(D.istar, 0, sizeof(int) * nfar, s));
-        RT_CUDA_TRY(cudaMemsetAsync(D.rank, 0, sizeof(int) * nfar, s));
-        RT_CUDA_TRY(cudaMemsetAsync(D.status, 0, sizeof(int) * nfar, s));
-        RT_CUDA_TRY(cudaMemsetAsync(D.norm2, 0, sizeof(double) * nfar * G, s));
-        {
-            std::vector<float> ones((size_t)nfar * G, 1.0f);
-            RT_CUDA_TRY(cudaMemcpyAsync(D.wscale, ones.data(), sizeof(float) * ones.size(), cudaMemcpyHostToDevice, s));
-            RT_CUDA_TRY(cudaStreamSynchronize(s));
-        }
-        RT_CUDA_TRY(cudaMemsetAsync(D.used, 0, sum_m, s));
-        RT_CUDA_TRY(cudaMemcpyAsync(D.used_off, used_off.data(), sizeof(int64_t) * nfar, cudaMemcpyHostToDevice, s));
-        RT_CUDA_TRY(cudaMemsetAsync(D.key, 0, sizeof(unsigned long long) * nfar, s));
-        RT_CUDA_TRY(cudaMemsetAsync(D.rowmax, 0, sizeof(unsigned) * nfar * G, s));
-
-        // row/col buffers sized for all blocks at once
-        int64_t sum_n = 0;
-        for (auto& fb : farb) sum_n += fb.n;
         float *rowbuf, *colbuf;
-        TA(rowbuf, sizeof(float) * (size_t)G * sum_n);
-        TA(colbuf, sizeof(float) * (size_t)G * sum_m);
+        TA(rowbuf, sizeof(float) * (size_t)G * sumn_max);
+        TA(colbuf, sizeof(float) * (size_t)G * summ_max);
         AcaActive* d_act;
-        TA(d_act, sizeof(AcaActive) * nfar);
-        DotItem* d_dot;
+        TA(d_act, sizeof(AcaActive) * nw_max);
+        DotItem* d_dot = nullptr;
+        double* d_dotv = nullptr;
         int64_t dot_cap = 0;
-        d_dot = nullptr;
-        std::vector<int> h_status_buf((size_t)nfar * 2);
+        std::vector<int> h_status_buf((size_t)nw_max * 2);
         int* h_status = h_status_buf.data();
-        std::vector<int> h_rank(nfar, 0);
-
-        // initial pool: the first 8 steps of every block
-        pool_cap = 0;
-        for (auto& fb : farb) pool_cap += (int64_t)G * (fb.m + fb.n) * 8;
-        {
-            cudaError_t e = cudaMallocAsync((void**)&pool, sizeof(float) * pool_cap, s);
-            if (e != cudaSuccess) {
-                                cleanup();
-                err = "cudaMalloc (ACA pool) failed";
-                return RT_ENOMEM;
-            }
-        }
-        D.pool = pool;
-        scratch += (int64_t)sizeof(float) * pool_cap;
-        note_peak(0);
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const std::vector<float> ones((size_t)nw_max * G, 1.0f);
+        cudaEvent_t pk0, pk1;
+        cudaEventCreate(&pk0);
+        cudaEventCreate(&pk1);
 
-        std::vector<int> status(nfar, ACA_ACTIVE);
-        std::vector<AcaActive> act;
-        std::vector<DotItem> dots;
-        for (int step = 0; step < rmax + 64; ++step) {
-            act.clear();
-            int64_t fr = 0, fc = 0, bufr = 0, bufc = 0;
-            int64_t need = 0;
-            for (int b = 0; b < nfar; ++b)
-                if (status[b] == ACA_ACTIVE) need += (int64_t)G * (farb[b].m + farb[b].n);
-            if (need == 0) break;
-            if (pool_used + need > pool_cap) {
-                int64_t ncap = std::max<int64_t>(pool_cap * 2, pool_used + need * 8);
-                float* np = nullptr;
-                cudaError_t e = cudaMallocAsync((void**)&np, sizeof(float) * ncap, s);
-                if (e != cudaSuccess) {
-                                        cudaFreeAsync(pool, s);
-                    cleanup();
-                    err = "cudaMalloc (ACA pool growth) failed";
-                    return RT_ENOMEM;
+        for (int w = 0; w < nwaves; ++w) {
+            const int w0 = wave_start[w], nb = wave_start[w + 1] - w0;
+            const FarBlock* fw = farb.data() + w0;
+            std::vector<int64_t> used_off(nb);
+            int64_t sum_m = 0;
+            for (int b = 0; b < nb; ++b) {
+                used_off[b] = sum_m;
+                sum_m += fw[b].m;
+            }
+            RT_CUDA_TRY(cudaMemcpyAsync(d_blk, fw, sizeof(FarBlock) * nb, cudaMemcpyHostToDevice, s));
+            RT_CUDA_TRY(cudaMemsetAsync(D.istar, 0, sizeof(int) * nb, s));
+            RT_CUDA_TRY(cudaMemsetAsync(D.rank, 0, sizeof(int) * nb, s));
+            RT_CUDA_TRY(cudaMemsetAsync(D.status, 0, sizeof(int) * nb, s));
+            RT_CUDA_TRY(cudaMemsetAsync(D.norm2, 0, sizeof(double) * nb * G, s));
+            RT_CUDA_TRY(cudaMemcpyAsync(D.wscale, ones.data(), sizeof(float) * nb * G, cudaMemcpyHostToDevice, s));
+            RT_CUDA_TRY(cudaMemsetAsync(D.used, 0, sum_m, s));
+            RT_CUDA_TRY(cudaMemcpyAsync(D.used_off, used_off.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, s));
+            RT_CUDA_TRY(cudaMemsetAsync(D.key, 0, sizeof(unsigned long long) * nb, s));
+            RT_CUDA_TRY(cudaMemsetAsync(D.rowmax, 0, sizeof(unsigned) * nb * G, s));
+            std::vector<int> h_rank(nb, 0), status(nb, ACA_ACTIVE);
+
+            // term pool of this wave: kWaveRank terms per block, grown if needed
+            pool_used = 0;
+            pool_cap = 0;
+            for (int b = 0; b < nb; ++b) pool_cap += (int64_t)G * (fw[b].m + fw[b].n) * (int64_t)kWaveRank;
+            if (cudaMallocAsync((void**)&pool, sizeof(float) * pool_cap, s) != cudaSuccess) {
+                cleanup();
+                err = "cudaMalloc (ACA pool) failed";
+                return RT_ENOMEM;
+            }
+            D.pool = pool;
+            scratch += (int64_t)sizeof(float) * pool_cap;
+            note_peak(0);
+
+            std::vector<AcaActive> act;
+            std::vector<DotItem> dots;
+            for (int step = 0; step < rmax + 64; ++step) {
+                act.clear();
+                int64_t fr = 0, fc = 0, bufr = 0, bufc = 0, need = 0;
+                for (int b = 0; b < nb; ++b)
+                    if (status[b] == ACA_ACTIVE) need += (int64_t)G * (fw[b].m + fw[b].n);
+                if (need == 0) break;
+                if (pool_used + need > pool_cap) {
+                    const int64_t ncap = std::max<int64_t>(pool_cap + pool_cap / 2, pool_used + need * 8);
+                    float* np = nullptr;
+                    if (cudaMallocAsync((void**)&np, sizeof(float) * ncap, s) != cudaSuccess) {
+                        cudaFreeAsync(pool, s);
+                        cleanup();
+                        err = "cudaMalloc (ACA pool growth) failed";
+                        return RT_ENOMEM;
+                    }
+                    RT_CUDA_TRY(cudaMemcpyAsync(np, pool, sizeof(float) * pool_used, cudaMemcpyDeviceToDevice, s));
+                    note_peak((int64_t)sizeof(float) * ncap);   // old and new pool both live here
+                    scratch += (int64_t)sizeof(float) * (ncap - pool_cap);
+                    cudaFreeAsync(pool, s);
+                    pool = np;
+                    pool_cap = ncap;
+                    D.pool = pool;
                 }
-                RT_CUDA_TRY(cudaMemcpyAsync(np, pool, sizeof(float) * pool_used, cudaMemcpyDeviceToDevice, s));
-                note_peak((int64_t)sizeof(float) * ncap);   // old and new pool both live here
-                scratch += (int64_t)sizeof(float) * (ncap - pool_cap);
-                cudaFreeAsync(pool, s);
-                pool = np;
-                pool_cap = ncap;
-                D.pool = pool;
-            }
-            for (int b = 0; b < nfar; ++b) {
-                if (status[b] != ACA_ACTIVE) continue;
-                AcaActive a{};
-                a.b = b;
-                a.row0 = farb[b].row0;
-                a.m = farb[b].m;
-                a.col0 = farb[b].col0;
-                a.n = farb[b].n;
-                a.first_row = fr;
-                a.first_col = fc;
-                a.rbuf = bufr;
-                a.cbuf = bufc;
-                a.uoff = pool_used;
-                pool_used += (int64_t)G * a.m;
-                a.voff = pool_used;
-                pool_used += (int64_t)G * a.n;
-                fr += a.n;
-                fc += a.m;
-                bufr += (int64_t)G * a.n;
-                bufc += (int64_t)G * a.m;
-                act.push_back(a);
-            }
-            const int na = (int)act.size();
-            RT_CUDA_TRY(cudaMemcpyAsync(d_act, act.data(), sizeof(AcaActive) * na, cudaMemcpyHostToDevice, s));
-            // 1. pivot rows: one CTA per (block, sub-cluster of its columns)
-            {
-                std::vector<RowItem> ritems;
-                for (const AcaActive& a : act) {
-                    const FarBlock& fb = farb[a.b];
-                    for (int e = op.sub_of_cluster_ptr[fb.sc]; e < op.sub_of_cluster_ptr[fb.sc + 1]; ++e) {
-                        const int sb = op.sub_of_cluster[e];
-                        RowItem it{};
-                        it.b = a.b;
-                        it.i = fb.row0;
-                        it.col0 = op.sub_start[sb];
-                        it.n = op.sub_size[sb];
-                        it.tet0 = op.sub_tet_ptr[sb];
-                        it.ntet = op.sub_tet_ptr[sb + 1] - op.sub_tet_ptr[sb];
-                        it.out = a.rbuf + (op.sub_start[sb] - fb.col0);
-                        it.gs = fb.n;
-                        it.js = 1;
-                        ritems.push_back(it);
+                int64_t ndot = 0;
+                for (int b = 0; b < nb; ++b) {
+                    if (status[b] != ACA_ACTIVE) continue;
+                    AcaActive a{};
+                    a.b = b;
+                    a.row0 = fw[b].row0;
+                    a.m = fw[b].m;
+                    a.col0 = fw[b].col0;
+                    a.n = fw[b].n;
+                    a.first_row = fr;
+                    a.first_col = fc;
+                    a.rbuf = bufr;
+                    a.cbuf = bufc;
+                    a.uoff = pool_used;
+                    pool_used += (int64_t)G * a.m;
+                    a.voff = pool_used;
+                    pool_used += (int64_t)G * a.n;
+                    a.dot0 = ndot;
+                    ndot += h_rank[b] + 1;
+                    fr += a.n;
+                    fc += a.m;
+                    bufr += (int64_t)G * a.n;
+                    bufc += (int64_t)G * a.m;
+                    act.push_back(a);
+                }
+                const int na = (int)act.size();
+                RT_CUDA_TRY(cudaMemcpyAsync(d_act, act.data(), sizeof(AcaActive) * na, cudaMemcpyHostToDevice, s));
+                // 1. pivot rows: one CTA per (block, sub-cluster of its columns)
+                {
+                    std::vector<RowItem> ritems;
+                    for (const AcaActive& a : act) {
+                        const FarBlock& fb = fw[a.b];
+                        for (int e = op.sub_of_cluster_ptr[fb.sc]; e < op.sub_of_cluster_ptr[fb.sc + 1]; ++e) {
+                            const int sb = op.sub_of_cluster[e];
+                            RowItem it{};
+                            it.b = a.b;
+                            it.i = fb.row0;
+                            it.col0 = op.sub_start[sb];
+                            it.n = op.sub_size[sb];
+                            it.tet0 = op.sub_tet_ptr[sb];
+                            it.ntet = op.sub_tet_ptr[sb + 1] - op.sub_tet_ptr[sb];
+                            it.out = a.rbuf + (op.sub_start[sb] - fb.col0);
+                            it.gs = fb.n;
+                            it.js = 1;
+                            ritems.push_back(it);
+                        }
+                    }
+                    if ((rc = launch_rows(op, ritems, D.istar, rowbuf, s, err))) {
+                        cleanup();
+                        return rc;
                     }
                 }
-                if ((rc = launch_rows(op, ritems, D.istar, rowbuf, s, err))) {
+                const int eg_r = (int)std::min<int64_t>((fr + 255) / 256, (int64_t)sms * 32);
+                aca_row_residual<<<std::max(1, eg_r), 256, 0, s>>>(D, d_act, na, fr, rowbuf);
+                aca_row_pivot<<<(na + 127) / 128, 128, 0, s>>>(D, d_act, na, rowbuf);
+                aca_store_v<<<std::max(1, eg_r), 256, 0, s>>>(D, d_act, na, fr, rowbuf);
+                // 2. pivot columns
+                {
+                    int grid = grid_for(fc);
+#define RT_LAUNCH_ACAC(MG) \
+    aca_entries_kernel<MG><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, d_act, na, fc, 1, D.istar, D.jstar, colbuf)
+                    RT_DISPATCH_MG(G, RT_LAUNCH_ACAC);
+#undef RT_LAUNCH_ACAC
+                    RT_CUDA_TRY(cudaGetLastError());
+                }
+                const int eg_c = (int)std::min<int64_t>((fc + 255) / 256, (int64_t)sms * 32);
+                aca_col_residual<<<std::max(1, eg_c), 256, 0, s>>>(D, d_act, na, fc, colbuf);
+                // 3. dots with all previous terms and the new one (per-step scratch)
+                dots.clear();
+                for (int ai = 0; ai < na; ++ai)
+                    for (int l = 0; l <= h_rank[act[ai].b]; ++l) dots.push_back({ai, l});
+                if ((int64_t)dots.size() > dot_cap) {
+                    if (d_dot) cudaFreeAsync(d_dot, s);
+                    if (d_dotv) cudaFreeAsync(d_dotv, s);
+                    scratch -= (int64_t)(sizeof(DotItem) + 2 * G * sizeof(double)) * dot_cap;
+                    dot_cap = (int64_t)dots.size() * 2;
+                    RT_CUDA_TRY(cudaMallocAsync((void**)&d_dot, sizeof(DotItem) * dot_cap, s));
+                    RT_CUDA_TRY(cudaMallocAsync((void**)&d_dotv, sizeof(double) * 2 * G * dot_cap, s));
+                    scratch += (int64_t)(sizeof(DotItem) + 2 * G * sizeof(double)) * dot_cap;
+                    note_peak(0);
+                }
+                D.dots = d_dotv;
+                RT_CUDA_TRY(cudaMemcpyAsync(d_dot, dots.data(), sizeof(DotItem) * dots.size(), cudaMemcpyHostToDevice, s));
+                aca_dots<<<(int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)dots.size() + 7) / 8, (int64_t)sms * 32)),
+                           256, 0, s>>>(D, d_act, d_dot, (int)dots.size());
+                aca_finish<<<(na + 127) / 128, 128, 0, s>>>(D, d_act, na);
+                RT_CUDA_TRY(cudaGetLastError());
+                RT_CUDA_TRY(cudaMemcpyAsync(h_status, D.status, sizeof(int) * nb, cudaMemcpyDeviceToHost, s));
+                RT_CUDA_TRY(cudaMemcpyAsync(h_status + nb, D.rank, sizeof(int) * nb, cudaMemcpyDeviceToHost, s));
+                RT_CUDA_TRY(cudaStreamSynchronize(s));
+                for (int b = 0; b < nb; ++b) {
+                    status[b] = h_status[b];
+                    h_rank[b] = h_status[nb + b];
+                }
+                ++aca_steps;
+            }
+            // ---- this wave's blocks: stored low rank, all-zero, or dense ------
+            const int64_t elems0 = far_elems;
+            const int k0 = (int)op.far_blocks.size();
+            for (int b = 0; b < nb; ++b) {
+                final_status[w0 + b] = status[b] == ACA_ACTIVE ? ACA_DENSE : status[b];
+                final_rank[w0 + b] = h_rank[b];
+                if (final_status[w0 + b] == ACA_DONE && h_rank[b] > 0) {
+                    const FarBlock& fb = fw[b];
+                    const int r = h_rank[b];
+                    op.far_blocks.push_back(fb);
+                    op.rank.push_back(r);
+                    far_src.push_back(b);
+                    op.far_v_off.push_back(far_elems);
+                    far_elems += (int64_t)G * r * round8(fb.n);
+                    op.far_u_off.push_back(far_elems);
+                    far_elems += block_chunks(op.plan, fb.row0, fb.m, (int64_t)G * r, op.far_chunks);
+                    op.far_chunk_ptr.push_back((int)op.far_chunks.size());
+                } else if (final_status[w0 + b] == ACA_DONE) {
+                    // an all-zero block: nothing to store
+                } else {
+                    op.dense_blocks.push_back(fw[b]);
+                    op.n_fallback++;
+                }
+            }
+            const int k1 = (int)op.far_blocks.size();
+            // ---- storage for the new far blocks, then pack them -----------------
+            if (nwaves == 1 && k1 > 0) {
+                char *d = nullptr, *dl = nullptr;
+                if ((rc = dev_alloc(op, &d, (size_t)far_elems * esz, err)) ||
+                    (split && (rc = dev_alloc(op, &dl, (size_t)far_elems * esz, err)))) {
+                    cudaFreeAsync(pool, s);
                     cleanup();
                     return rc;
                 }
+                op.d_far = d;
+                op.d_far_lo = dl;
+            } else if (nwaves > 1 && far_elems > elems0) {
+                const size_t before = op.far_buf.mapped;
+                if ((rc = growbuf_grow(op.far_buf, (size_t)far_elems * esz, err)) ||
+                    (split && (rc = growbuf_grow(op.far_lo_buf, (size_t)far_elems * esz, err)))) {
+                    cudaFreeAsync(pool, s);
+                    cleanup();
+                    return rc;
+                }
+                op.info.device_bytes += (int64_t)(op.far_buf.mapped - before) * (split ? 2 : 1);
+                op.d_far = (void*)op.far_buf.base;
+                op.d_far_lo = split ? (void*)op.far_lo_buf.base : nullptr;
             }
-            const int eg_r = (int)std::min<int64_t>((fr + 255) / 256, (int64_t)sms * 32);
-            aca_row_residual<<<std::max(1, eg_r), 256, 0, s>>>(D, d_act, na, fr, rowbuf);
-            aca_row_pivot<<<(na + 127) / 128, 128, 0, s>>>(D, d_act, na, rowbuf);
-            aca_store_v<<<std::max(1, eg_r), 256, 0, s>>>(D, d_act, na, fr, rowbuf);
-            // 2. pivot columns
-            {
-                int grid = grid_for(fc);
-#define RT_LAUNCH_ACAC(MG) \
-    aca_entries_kernel<MG><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, d_act, na, fc, 1, D.istar, D.jstar, colbuf)
-                RT_DISPATCH_MG(G, RT_LAUNCH_ACAC);
-#undef RT_LAUNCH_ACAC
+            if (k1 > k0) {
+                char* base = (char*)op.d_far;
+                char* base_lo = (char*)op.d_far_lo;
+                RT_CUDA_TRY(cudaMemsetAsync(base + elems0 * esz, 0, (size_t)(far_elems - elems0) * esz, s));
+                if (base_lo) RT_CUDA_TRY(cudaMemsetAsync(base_lo + elems0 * esz, 0, (size_t)(far_elems - elems0) * esz, s));
+                note_peak(0);   // packed far field next to this wave's pool
+                std::vector<PackItem> items;
+                for (int k = k0; k < k1; ++k)
+                    for (int l = 0; l < op.rank[k]; ++l)
+                        items.push_back({far_src[k], l, op.rank[k], op.far_blocks[k].m, op.far_blocks[k].n,
+                                         round8(op.far_blocks[k].n), op.far_v_off[k], op.far_u_off[k],
+                                         op.far_chunk_ptr[k], op.far_chunk_ptr[k + 1]});
+                PackItem* d_items = nullptr;
+                Chunk* d_chunks = nullptr;
+                const int c0 = op.far_chunk_ptr[k0], nc = op.far_chunk_ptr[k1] - c0;
+                RT_CUDA_TRY(cudaMallocAsync((void**)&d_items, sizeof(PackItem) * items.size(), s));
+                RT_CUDA_TRY(cudaMallocAsync((void**)&d_chunks, sizeof(Chunk) * op.far_chunks.size(), s));
+                RT_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), sizeof(PackItem) * items.size(),
+                                            cudaMemcpyHostToDevice, s));
+                RT_CUDA_TRY(cudaMemcpyAsync(d_chunks + c0, op.far_chunks.data() + c0, sizeof(Chunk) * nc,
+                                            cudaMemcpyHostToDevice, s));
+                const int grid = (int)std::min<size_t>(items.size(), 152 * 64);
+                const int ni = (int)items.size();
+                cudaEventRecord(pk0, s);
+                if (op.far_prec == RT_PREC_F32)
+                    aca_pack<float><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, (float*)base, nullptr);
+                else if (op.far_prec == RT_PREC_BF16)
+                    aca_pack<__nv_bfloat16><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, (__nv_bfloat16*)base,
+                                                                 (__nv_bfloat16*)base_lo);
+                else aca_pack<__half><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, (__half*)base, (__half*)base_lo);
+                cudaEventRecord(pk1, s);
                 RT_CUDA_TRY(cudaGetLastError());
+                cudaFreeAsync(d_items, s);
+                cudaFreeAsync(d_chunks, s);
+                RT_CUDA_TRY(cudaEventSynchronize(pk1));
+                float t = 0.f;
+                cudaEventElapsedTime(&t, pk0, pk1);
+                ms_pack += t;
             }
-            const int eg_c = (int)std::min<int64_t>((fc + 255) / 256, (int64_t)sms * 32);
-            aca_col_residual<<<std::max(1, eg_c), 256, 0, s>>>(D, d_act, na, fc, colbuf);
-            // 3. dots with all previous terms and the new one
-            dots.clear();
-            for (int ai = 0; ai < na; ++ai)
-                for (int l = 0; l <= h_rank[act[ai].b]; ++l) dots.push_back({ai, l});
-            if ((int64_t)dots.size() > dot_cap) {
-                if (d_dot) cudaFreeAsync(d_dot, s);
-                scratch -= (int64_t)sizeof(DotItem) * dot_cap;
-                dot_cap = (int64_t)dots.size() * 2;
-                RT_CUDA_TRY(cudaMallocAsync((void**)&d_dot, sizeof(DotItem) * dot_cap, s));
-                scratch += (int64_t)sizeof(DotItem) * dot_cap;
-                note_peak(0);
-            }
-            RT_CUDA_TRY(cudaMemcpyAsync(d_dot, dots.data(), sizeof(DotItem) * dots.size(), cudaMemcpyHostToDevice, s));
-            aca_dots<<<(int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)dots.size() + 7) / 8, (int64_t)sms * 32)),
-                       256, 0, s>>>(D, d_act, d_dot, (int)dots.size());
-            aca_finish<<<(na + 127) / 128, 128, 0, s>>>(D, d_act, na);
-            RT_CUDA_TRY(cudaGetLastError());
-            RT_CUDA_TRY(cudaMemcpyAsync(h_status, D.status, sizeof(int) * nfar, cudaMemcpyDeviceToHost, s));
-            RT_CUDA_TRY(cudaMemcpyAsync(h_status + nfar, D.rank, sizeof(int) * nfar, cudaMemcpyDeviceToHost, s));
-            RT_CUDA_TRY(cudaStreamSynchronize(s));
-            for (int b = 0; b < nfar; ++b) {
-                status[b] = h_status[b];
-                h_rank[b] = h_status[nfar + b];
-            }
-            ++aca_steps;
-        }
-        for (int b = 0; b < nfar; ++b) {
-            final_status[b] = status[b] == ACA_ACTIVE ? ACA_DENSE : status[b];
-            final_rank[b] = h_rank[b];
+            cudaFreeAsync(pool, s);
+            scratch -= (int64_t)sizeof(float) * pool_cap;
+            pool = nullptr;
         }
         if (d_dot) cudaFreeAsync(d_dot, s);
-        scratch -= (int64_t)sizeof(DotItem) * dot_cap;
-        #undef TA
+        if (d_dotv) cudaFreeAsync(d_dotv, s);
+        scratch -= (int64_t)(sizeof(DotItem) + 2 * G * sizeof(double)) * dot_cap;
+        cudaEventDestroy(pk0);
+        cudaEventDestroy(pk1);
+#undef TA
     }
-    cudaEventRecord(ev1, s);
-    cudaEventSynchronize(ev1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ev0, ev1);
-    op.info.ms_aca = ms;
-    op.info.aca_steps = aca_steps;
-
-    // ---- final split: ACA blocks and dense blocks --------------------------
-    op.far_blocks.clear();
-    op.dense_blocks = op.plan.near_blocks;
-    op.rank.clear();
-    std::vector<int> far_src;
-    for (int b = 0; b < nfar; ++b) {
-        if (final_status[b] == ACA_DONE && final_rank[b] > 0) {
-            op.far_blocks.push_back(farb[b]);
-            op.rank.push_back(final_rank[b]);
-            far_src.push_back(b);
-        } else if (final_status[b] == ACA_DONE && final_rank[b] == 0) {
-            // an all-zero block: nothing to store
-        } else {
-            op.dense_blocks.push_back(farb[b]);
-            op.n_fallback++;
-        }
-    }
+    cleanup();
+    scratch = 0;
     op.n_far = (int)op.far_blocks.size();
     op.n_near = (int)op.dense_blocks.size();
-
-    // ---- far storage (pack): V^T [G][r][n8], U^T per leaf chunk [G][r][m8] ----
-    cudaEventRecord(ev0, s);
-    const int esz = op.far_prec == RT_PREC_F32 ? 4 : 2;
-    int64_t far_elems = 0;
-    op.far_v_off.assign(op.n_far, 0);
-    op.far_u_off.assign(op.n_far, 0);
-    op.far_chunks.clear();
-    op.far_chunk_ptr.assign(1, 0);
-    for (int k = 0; k < op.n_far; ++k) {
-        const FarBlock& fb = op.far_blocks[k];
-        const int r = op.rank[k];
-        op.far_v_off[k] = far_elems;
-        far_elems += (int64_t)G * r * round8(fb.n);
-        op.far_u_off[k] = far_elems;
-        far_elems += block_chunks(op.plan, fb.row0, fb.m, (int64_t)G * r, op.far_chunks);
-        op.far_chunk_ptr.push_back((int)op.far_chunks.size());
-    }
-    if (op.n_far > 0) {
-        char* d = nullptr;
-        if ((rc = dev_alloc(op, &d, (size_t)far_elems * esz, err))) {
-            if (pool) cudaFreeAsync(pool, s);
-            cleanup();
-            return rc;
-        }
-        op.d_far = d;
-        RT_CUDA_TRY(cudaMemsetAsync(d, 0, (size_t)far_elems * esz, s));   // padding stays zero
-        std::vector<PackItem> items;
-        for (int k = 0; k < op.n_far; ++k)
-            for (int l = 0; l < op.rank[k]; ++l)
-                items.push_back({far_src[k], l, op.rank[k], op.far_blocks[k].m, op.far_blocks[k].n,
-                                 round8(op.far_blocks[k].n), op.far_v_off[k], op.far_u_off[k], op.far_chunk_ptr[k],
-                                 op.far_chunk_ptr[k + 1]});
-        PackItem* d_items = nullptr;
-        Chunk* d_chunks = nullptr;
-        RT_CUDA_TRY(cudaMallocAsync((void**)&d_items, sizeof(PackItem) * items.size(), s));
-        RT_CUDA_TRY(cudaMallocAsync((void**)&d_chunks, sizeof(Chunk) * op.far_chunks.size(), s));
-        RT_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), sizeof(PackItem) * items.size(), cudaMemcpyHostToDevice, s));
-        RT_CUDA_TRY(cudaMemcpyAsync(d_chunks, op.far_chunks.data(), sizeof(Chunk) * op.far_chunks.size(),
-                                    cudaMemcpyHostToDevice, s));
-        char* dl = nullptr;
-        if (op.refine && op.far_prec != RT_PREC_F32) {
-            // 16-bit remainders in the same layout, for refinement sweeps
-            if ((rc = dev_alloc(op, &dl, (size_t)far_elems * esz, err))) {
-                if (pool) cudaFreeAsync(pool, s);
-                cleanup();
-                return rc;
-            }
-            RT_CUDA_TRY(cudaMemsetAsync(dl, 0, (size_t)far_elems * esz, s));
-            op.d_far_lo = dl;
-        }
-        note_peak(0);   // packed far field (and remainders) next to the pool
-        const int grid = (int)std::min<size_t>(items.size(), 152 * 64);
-        const int ni = (int)items.size();
-        if (op.far_prec == RT_PREC_F32)
-            aca_pack<float><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, (float*)d, nullptr);
-        else if (op.far_prec == RT_PREC_BF16)
-            aca_pack<__nv_bfloat16><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, (__nv_bfloat16*)d,
-                                                         (__nv_bfloat16*)dl);
-        else aca_pack<__half><<<grid, 256, 0, s>>>(D, d_items, ni, d_chunks, (__half*)d, (__half*)dl);
-        RT_CUDA_TRY(cudaGetLastError());
-        cudaFreeAsync(d_items, s);
-        cudaFreeAsync(d_chunks, s);
-    }
-    if (pool) cudaFreeAsync(pool, s);
-    cleanup();
     cudaEventRecord(ev1, s);
     cudaEventSynchronize(ev1);
     cudaEventElapsedTime(&ms, ev0, ev1);
-    op.info.ms_pack = ms;
+    op.info.ms_aca = ms - ms_pack;
+    op.info.ms_pack = ms_pack;
+    op.info.aca_steps = aca_steps;
 
     // ---- dense blocks (near leaves and fallbacks): per leaf chunk A^T [G][n][m8]
     cudaEventRecord(ev0, s);

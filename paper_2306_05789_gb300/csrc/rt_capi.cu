@@ -75,6 +75,7 @@ int validate(const rt_problem* P, const rt_hparams* H)
         if (!(H->eta > 0.0)) return fail(RT_EINVAL, "eta must be > 0");
         if (H->rank_max < 0 || H->rank_max > 8192) return fail(RT_EINVAL, "rank_max must be in [0, 8192]");
         if (H->adm != RT_ADM_GAP && H->adm != RT_ADM_CENTER) return fail(RT_EINVAL, "adm must be RT_ADM_GAP or RT_ADM_CENTER");
+        if (H->wave_bytes < 0) return fail(RT_EINVAL, "wave_bytes must be >= 0");
     }
     if (H->gauss_pts < 1 || H->gauss_pts > rt::kMaxGauss) return fail(RT_EINVAL, "gauss_pts must be in [1, 32]");
     if (H->line_eval != RT_LINE_CLOSED && H->line_eval != RT_LINE_NODES) return fail(RT_EINVAL, "line_eval");
@@ -114,6 +115,7 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
     op.refine = H->mode == RT_MODE_HMATRIX && H->refine && H->far_prec != RT_PREC_F32;
     op.ngauss = H->gauss_pts;
     op.rank_max = H->rank_max > 0 ? H->rank_max : 512;
+    op.wave_bytes = H->wave_bytes > 0 ? H->wave_bytes : ((int64_t)8 << 30);
     op.grey = P->grey ? 1 : 0;
     const rt_freqs& Fq = P->freqs;
     op.F = Fq.F;
@@ -358,6 +360,12 @@ void operator_release(Operator& op, cudaStream_t s)
     for (void* p : op.allocations)
         if (p) cudaFreeAsync(p, s);
     op.allocations.clear();
+    if (op.far_buf.base || op.far_lo_buf.base) {
+        // unmapping is not stream ordered: wait for the work queued on s
+        cudaStreamSynchronize(s);
+        growbuf_release(op.far_buf);
+        growbuf_release(op.far_lo_buf);
+    }
     if (op.cap_stream) cudaStreamDestroy(op.cap_stream);
     op.cap_stream = nullptr;
 }

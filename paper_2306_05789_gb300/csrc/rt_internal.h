@@ -129,6 +129,20 @@ inline int64_t block_chunks(const Plan& P, int row0, int m, int64_t per_row, std
     return off;
 }
 
+// Device buffer that grows in place: a reserved virtual address range whose
+// physical memory is mapped chunk by chunk as it grows, so that data already
+// written never moves (rt_vmm.cu).
+struct GrowBuf {
+    unsigned long long base = 0;   // device address of byte 0
+    size_t reserved = 0, mapped = 0, gran = 0;
+    int device = 0;
+    std::vector<unsigned long long> handles;   // physical allocations, in address order
+    std::vector<size_t> sizes;
+};
+int growbuf_reserve(GrowBuf& b, size_t bytes, int device, std::string& err);
+int growbuf_grow(GrowBuf& b, size_t bytes, std::string& err);   // mapped >= bytes afterwards
+void growbuf_release(GrowBuf& b);   // no work may still use the buffer
+
 // Operator (one instance).
 struct Operator {
     int device = 0;
@@ -138,6 +152,7 @@ struct Operator {
     double aca_eps = 1e-4, eta = 2.0;
     int adm = RT_ADM_GAP;
     int leaf = 64, ngauss = 16, rank_max = 512;
+    int64_t wave_bytes = (int64_t)8 << 30;   // ACA scratch bound per wave
     KernelParams kp{};
     // frequencies (host copies) and the group of each frequency
     std::vector<double> nu, w, c, albedo, Q;
@@ -179,6 +194,7 @@ struct Operator {
     int refine = 0;
     int use_lo = 0;             // apply with high + low parts (set by the solver)
     std::vector<int64_t> far_v_off, far_u_off;
+    GrowBuf far_buf, far_lo_buf;   // backing of d_far / d_far_lo when ACA ran in several waves
     // matvec work lists (device)
     void* d_p1_items = nullptr; int n_p1 = 0;
     void* d_p1_rows = nullptr;

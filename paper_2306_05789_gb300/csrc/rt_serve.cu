@@ -59,7 +59,9 @@ struct Request {
 // size while the fixed point runs.  Exact for the near field and the vectors;
 // the far field assumes every admissible block reaches rank r_hat, a little
 // above the mean rank that ACA reaches at the given tolerance (about 19 at
-// 1e-4 on the cube workloads), and the ACA term pool grows by half again.
+// 1e-4 on the cube workloads).  The ACA term scratch lives one wave at a time
+// (at most hp.wave_bytes of 24-term pools, grown by half once at worst) and
+// is gone before the near field is allocated.
 struct Footprint {
     int64_t peak = 0, resident = 0;
 };
@@ -78,14 +80,17 @@ static Footprint estimate_footprint(const Plan& P, int64_t N, int64_t T, int F, 
         tmp.clear();
         const int64_t mpad = block_chunks(P, b.row0, b.m, 1, tmp);
         far_elems += (int64_t)std::ceil(G * r_hat) * ((int64_t)round8(b.n) + mpad);
-        pool += (int64_t)std::ceil(G * r_hat * 1.5) * (b.m + b.n);
+        pool += (int64_t)G * 24 * (b.m + b.n);
         bufs += (int64_t)G * (b.m + b.n);
     }
+    const int64_t wave = hp.wave_bytes > 0 ? hp.wave_bytes : ((int64_t)8 << 30);
+    const int64_t aca = (int64_t)(1.5 * (double)std::min<int64_t>(4 * pool, wave)) +
+                        std::min<int64_t>(4 * bufs, wave / 24 + ((int64_t)64 << 20));
     const int64_t geo = N * 64 + T * 120 + (int64_t)F * N * 4;
     const int64_t vec = (int64_t)F * N * 4 * 6 + N * 16 + (int64_t)F * (int64_t)P.far_blocks.size() * (int64_t)r_hat * 4;
     Footprint f;
     f.resident = geo + 4 * near + (int64_t)esz * far_elems + vec;
-    f.peak = geo + std::max<int64_t>(4 * pool + 4 * bufs + (int64_t)esz * far_elems, 4 * near + esz * far_elems + vec);
+    f.peak = geo + (int64_t)esz * far_elems + std::max<int64_t>(aca, 4 * near + vec);
     return f;
 }
 
