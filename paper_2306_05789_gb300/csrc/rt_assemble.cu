@@ -530,7 +530,7 @@ struct RowItem {
 };
 
 // MG > 0: the four vertex sums of a tetrahedron accumulate in registers for
-// all groups and are flushed once per tetrahedron; MG == 0 (more than 16
+// all groups and are flushed once per tetrahedron; MG == 0 (more than 32
 // groups): every point is added to shared memory directly.  Tetrahedra are
 // handed out through a shared counter so that the few tetrahedra near x_i
 // (14-point rules) do not hold up a fixed partition.
@@ -594,16 +594,27 @@ __global__ void __launch_bounds__(256) row_cluster_kernel(KernelParams P, const 
             float w = vol * tet_w<float>(row) * kappa_at<float>(P, y.x, y.y, y.z) * inv4pi / r2;
             if (refl) w *= (float)P.R0;
             if constexpr (MG > 0) {
+                auto add = [&](int g, float eg) {
+                    const float val = w * P.cf[g] * eg;
+                    a0[g] += val * b0;
+                    a1[g] += val * b1;
+                    a2[g] += val * b2;
+                    a3[g] += val * b3;
+                };
+                if (P.c_arith) {
+                    // exp(-c_g tau) as exp(-c_0 tau) exp(-dc tau)^g: two SFU exponentials per point
+                    float E = expf(-P.c0f * tau);
+                    const float D = expf(-P.dcf * tau);
 #pragma unroll
-                for (int g = 0; g < MG; ++g)
-                    if (g < G) {
-                        const float cg = P.cf[g];
-                        const float val = w * cg * expf(-cg * tau);
-                        a0[g] += val * b0;
-                        a1[g] += val * b1;
-                        a2[g] += val * b2;
-                        a3[g] += val * b3;
+                    for (int g = 0; g < MG; ++g) {
+                        if (g < G) add(g, E);
+                        E *= D;
                     }
+                } else {
+#pragma unroll
+                    for (int g = 0; g < MG; ++g)
+                        if (g < G) add(g, expf(-P.cf[g] * tau));
+                }
             } else {
                 for (int g = 0; g < G; ++g) {
                     const float cg = P.cf[g];
@@ -705,6 +716,7 @@ int prepare_row_eval(Operator& op, std::string& err)
         RT_CUDA_TRY(cudaFuncSetAttribute(row_cluster_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
         RT_CUDA_TRY(cudaFuncSetAttribute(row_cluster_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
         RT_CUDA_TRY(cudaFuncSetAttribute(row_cluster_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        RT_CUDA_TRY(cudaFuncSetAttribute(row_cluster_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
         attr_set[dev] = true;
     }
     return RT_OK;
@@ -727,6 +739,7 @@ static int launch_rows(Operator& op, const std::vector<RowItem>& items, const in
         else if (G <= 4) row_cluster_kernel<4><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
         else if (G <= 8) row_cluster_kernel<8><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
         else if (G <= 16) row_cluster_kernel<16><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
+        else if (G <= 32) row_cluster_kernel<32><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
         else row_cluster_kernel<0><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
     }
     RT_CUDA_TRY(cudaGetLastError());

@@ -268,6 +268,18 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
         kp.c[g] = op.gc[g];
         kp.cf[g] = (float)op.gc[g];
     }
+    kp.c_arith = 0;
+    if (op.G >= 3) {
+        const double dc = op.gc[1] - op.gc[0];
+        bool arith = dc != 0.0;
+        for (int g = 2; g < op.G && arith; ++g)
+            arith = std::fabs(op.gc[g] - (op.gc[0] + g * dc)) <= 1e-12 * std::max(1.0, std::fabs(op.gc[g]));
+        if (arith) {
+            kp.c_arith = 1;
+            kp.c0f = (float)op.gc[0];
+            kp.dcf = (float)dc;
+        }
+    }
     kp.ngauss = op.ngauss;
     kp.line_closed = (H->line_eval == RT_LINE_CLOSED && op.ngauss >= 16) ? 1 : 0;
     kp.xyz32 = op.d_xyz32;

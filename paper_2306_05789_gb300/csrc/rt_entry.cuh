@@ -303,12 +303,28 @@ __device__ void entry_warp(const KernelParams& P, int i, int j, R (&acc)[MG], in
             }
             R w = vol * tet_w<R>(row) * lam * kappa_at<R>(P, y.x, y.y, y.z) * inv4pi / r2;
             if (refl) w *= R(P.R0);
+            bool done = false;
+            if constexpr (sizeof(R) == 4) {
+                if (P.c_arith) {
+                    // exp(-c_g tau) = exp(-c_0 tau) exp(-dc tau)^g
+                    float E = expf(-P.c0f * tau);
+                    const float D = expf(-P.dcf * tau);
 #pragma unroll
-            for (int g = 0; g < MG; ++g)
-                if (g < P.G) {
-                    R cg = kp_c<R>(P, g);
-                    acc[g] += w * cg * exp_r(-cg * tau);
+                    for (int g = 0; g < MG; ++g) {
+                        if (g < P.G) acc[g] += w * P.cf[g] * E;
+                        E *= D;
+                    }
+                    done = true;
                 }
+            }
+            if (!done) {
+#pragma unroll
+                for (int g = 0; g < MG; ++g)
+                    if (g < P.G) {
+                        R cg = kp_c<R>(P, g);
+                        acc[g] += w * cg * exp_r(-cg * tau);
+                    }
+            }
         }
         __syncwarp();
     }

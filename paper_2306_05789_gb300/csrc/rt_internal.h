@@ -46,6 +46,10 @@ struct KernelParams {
     int G;              // groups
     double c[kMaxGroups];
     float cf[kMaxGroups];
+    // group scales in arithmetic progression c_g = c_0 + g dc: the FP32 paths
+    // get exp(-c_g tau) = exp(-c_0 tau) exp(-dc tau)^g by repeated products
+    int c_arith;
+    float c0f, dcf;
     int ngauss;
     int line_closed;    // closed-form Gauss sums for the sin-product kappa (FP32 paths)
     // Gauss-Legendre nodes mapped to [0,1] (u = (1+t)/2) and half weights
