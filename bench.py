@@ -44,9 +44,9 @@ def peaks():
         return 6800.0, 1900.0, "fallback"
 
 
-def workload(name):
+def workload(name, seed=0):
     if name.startswith("batch"):
-        return W.batch_instances(count=int(name[5:] or 256), seed=0)
+        return W.batch_instances(count=int(name[5:] or 256), seed=seed)
     if name == "cube32_F16":
         return W.multifreq_32()
     if name == "cube12_grey":
@@ -112,16 +112,34 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def init_ranks():
+    """torchrun ranks (one per GPU): device, process group for N > 1."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2306_05789_gb300 import ranks
+    rank, world, local = ranks.rank_env()
+    torch.cuda.set_device(local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl")
+    from paper_2306_05789_gb300 import build as _b
+    if rank == 0 or world == 1:
+        _b.build()
+    ranks.barrier()
+    return rank, world, local
+
+
 def run_batch(args):
-    """Batched workload: one step = build + solve of every instance (rt_build_batch + rt_solve_batch)."""
+    """Batched workload: one step = build + solve of every instance (rt_build_batch + rt_solve_batch).
+    With N ranks each rank solves its own seeded set of instances (weak scaling)."""
     import torch
 
     import paper_2306_05789_gb300 as rt
-    from paper_2306_05789_gb300 import build as _b
-    _b.build()
+    from paper_2306_05789_gb300 import ranks
+    rank, world, local = init_ranks()
     rt.lib()
-    dev = torch.device("cuda", 0)
-    probs = workload(args.workload)
+    dev = torch.device("cuda", local)
+    probs = workload(args.workload, seed=ranks.instance_seed(0, rank))
     hp = rt.hparams()
     stream = torch.cuda.current_stream(dev)
 
@@ -136,8 +154,11 @@ def run_batch(args):
         b, _, _ = step()
         b.free()
     torch.cuda.synchronize()
-    clocks = Clocks(0)
-    clocks.start()
+    clocks = Clocks(local)
+    if rank == 0:
+        clocks.start()
+    ranks.barrier()
+    torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -151,8 +172,9 @@ def run_batch(args):
             b.free()
     ev1.record(stream)
     torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    clk = clocks.stop()
+    ranks.barrier()
+    ms = ranks.max_over_ranks(ev0.elapsed_time(ev1), dev)
+    clk = clocks.stop() if rank == 0 else None
     X = torch.rand(int(b.vec_off[-1]), device=dev)
     Y = torch.zeros_like(X)
     for _ in range(3):
@@ -166,14 +188,17 @@ def run_batch(args):
     torch.cuda.synchronize()
     t_apply = a0.elapsed_time(a1) / 20 / 1e3
     b.free()
+    if rank != 0:
+        return
     hbm, _, peak_kind = peaks()
     n = len(probs)
     gbs = info["apply_bytes"] / t_apply / 1e9
     print(json.dumps({
-        "metric": METRIC, "value": n * args.steps / (ms / 1e3), "unit": "solves/s", "n_gpus": 1,
+        "metric": METRIC, "value": world * n * args.steps / (ms / 1e3), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "instances": n, "n_range": [8, 24], "F_range": [1, 8],
+        "config": {"workload": args.workload, "instances": n, "instances_per_rank": n, "parallelism": f"shards{world}",
+                   "n_range": [8, 24], "F_range": [1, 8],
                    "amp_range": [0.0, 0.8], "tol": args.tol, "autotune": bool(args.tune),
                    "l2": "batch operators larger than L2"},
         "roofline": {"bound": "hbm", "kernel": "batch_apply_kernel (persistent, all instances)", "achieved": gbs,
@@ -297,19 +322,10 @@ def run_gpu(args):
     import torch.distributed as dist
 
     import paper_2306_05789_gb300 as rt
+    from paper_2306_05789_gb300 import ranks
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
+    rank, world, local = init_ranks()
     dev = torch.device("cuda", local)
-    from paper_2306_05789_gb300 import build as _b
-    if rank == 0 or world == 1:
-        _b.build()
-    if world > 1:
-        dist.barrier()
     rt.lib()
     prob = workload(args.workload)
     far = {"f32": rt.RT_PREC_F32, "bf16": rt.RT_PREC_BF16, "f16": rt.RT_PREC_F16}[args.far_prec]
@@ -386,10 +402,7 @@ def run_gpu(args):
         op.free()
     t_e2e = (time.perf_counter() - t0) / e2e_steps
 
-    t_tensor = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
-    ms_max = float(t_tensor.item())
+    ms_max = ranks.max_over_ranks(ms, dev)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
