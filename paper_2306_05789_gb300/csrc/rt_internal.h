@@ -227,11 +227,12 @@ struct Operator {
     // tensor-core multi-right-hand-side apply (one operator group, F % 16 == 0)
     int tc_enabled = 0;
     int tc_off = 0;     // tensor cores disabled by the caller
-    void *tc_blocks = nullptr, *tc_leaf_far = nullptr, *tc_leaf_near = nullptr;
-    void *tc_segs_far = nullptr, *tc_segs_near = nullptr, *tc_xsplit = nullptr;
-    int tc_nblocks = 0;
+    void *tc_tiles = nullptr, *tc_rows = nullptr, *tc_leaves = nullptr, *tc_segs = nullptr;
+    int tc_ntiles = 0, tc_nleaves = 0;
     int64_t tc_wlen = 0;
-    float* tc_w = nullptr;
+    void* tc_w = nullptr;       // W high parts [tc_wlen], then low parts [tc_wlen]
+    int tc_xal = 0;             // X columns of every cluster 16-byte aligned: X split once per apply
+    void* tc_xsplit = nullptr;  // X high / low parts (BF16; then FP16 for an FP16 far field)
     int* tc_err = nullptr;
     // stats
     rt_info info{};
@@ -259,7 +260,7 @@ int apply_noalloc(Operator& op, const void* X, void* Y, cudaStream_t s, std::str
 size_t apply_noalloc_limit();
 int tc_prepare(Operator& op, std::string& err);
 int tc_apply(Operator& op, const float* X, float* Y, cudaStream_t s, std::string& err);
-int tc_check_error(Operator& op, std::string& err);
+int tc_check_error(Operator& op, cudaStream_t s, std::string& err);
 int solve_fixed_point(Operator& op, const rt_solve_opts& o, void* J, double* T, rt_solve_stats& st,
                       cudaStream_t s, std::string& err);
 
