@@ -166,6 +166,7 @@ typedef struct {
     double ms_tree, ms_near, ms_aca, ms_pack, ms_source; /* assembly phase times */
     int64_t peak_bytes;          /* largest device footprint during assembly (operator + ACA scratch) */
     int64_t aca_waves;           /* waves of admissible blocks the ACA ran in */
+    int64_t apply_tensor_cores;  /* 1 if rt_apply runs on the tcgen05 multi-right-hand-side path */
 } rt_info;
 
 /* Fixed-point options (Section 1.3).  The iteration starts from T = T0 at

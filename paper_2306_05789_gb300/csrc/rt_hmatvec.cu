@@ -211,6 +211,7 @@ int hmatvec_prepare(Operator& op, std::string& err)
     op.info.apply_bytes = F * (far_e * esz_far + near_e * 4) + 2 * F * N * (int64_t)esz;
     op.info.apply_flops = 2 * F * (far_e + near_e);
     if ((rc = tc_prepare(op, err))) return rc;
+    op.info.apply_tensor_cores = op.tc_enabled;
     if (op.tc_enabled)   // one operator serves all F right-hand sides: its data is read once per apply
         op.info.apply_bytes = far_e * esz_far + near_e * 4 + 2 * F * N * (int64_t)esz;
     return RT_OK;
