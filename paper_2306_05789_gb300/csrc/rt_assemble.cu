@@ -182,6 +182,7 @@ struct AcaActive {
     int64_t first_row, first_col;   // prefix of n (rows) and m (cols) over the active list
     int64_t uoff, voff;             // pool offsets of this step's u [G][m] and v [G][n]
     int64_t dot0;                   // first entry of this block's rank+1 dot products this step
+    int64_t first_chunk;            // prefix of ceil(m / kColRows) over the active list
     int skip;       // set by the pivot kernel: zero row, no rank this step
 };
 
@@ -190,7 +191,7 @@ __device__ __forceinline__ int find_active(const AcaActive* a, int na, int64_t e
     int lo = 0, hi = na - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        int64_t f = mode == 0 ? a[mid].first_row : a[mid].first_col;
+        int64_t f = mode == 0 ? a[mid].first_row : (mode == 1 ? a[mid].first_col : a[mid].first_chunk);
         if (f <= e) lo = mid; else hi = mid - 1;
     }
     return lo;
@@ -227,6 +228,114 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) aca_entries_kernel(KernelPa
 #pragma unroll
         for (int g = 0; g < MG; ++g)
             if (g < P.G && lane == (g & 31)) buf[(mode == 0 ? a.rbuf : a.cbuf) + (int64_t)g * len + pos] = acc[g];
+    }
+}
+
+// ACA pivot columns: G_g[i, j*] for the rows i of an active block.  One CTA of
+// kColRows threads per chunk of kColRows rows.  The quadrature points of the
+// tetrahedra around the pivot vertex j* do not depend on the row, so each CTA
+// tabulates them once per batch of 32 tetrahedra in shared memory (position,
+// and vol * w_q * lambda_j(y) * kappa(y) / 4 pi for both rules) and every row
+// walks the table -- the sums of entry_warp, with each point's position,
+// kappa and hat-function weight computed once per chunk instead of per entry.
+constexpr int kColRows = 64;
+constexpr int kColTets = 32;
+
+template <int MG>
+__global__ void __launch_bounds__(kColRows) aca_col_kernel(KernelParams P, const AcaActive* __restrict__ act, int na,
+                                                           int64_t nchunks, const int* __restrict__ jstar,
+                                                           float* __restrict__ buf)
+{
+    __shared__ float4 s_pt[kColTets][18];   // rule rows 0-3: 4-point rule, 4-17: 14-point rule
+    __shared__ float4 s_cen[kColTets];      // centroid, 4 diam^2
+    const float inv4pi = (float)(1.0 / (4.0 * kPi));
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int ai = find_active(act, na, c, 2);
+        const AcaActive a = act[ai];
+        if (a.skip) continue;   // CTA-uniform
+        const int r0 = (int)(c - a.first_chunk) * kColRows;
+        const int j = a.col0 + jstar[a.b];
+        const int pos = r0 + threadIdx.x;
+        const bool row_ok = pos < a.m;
+        const int i = a.row0 + (row_ok ? pos : 0);
+        const Vec3<float> xi = load_xyz<float>(P, i);
+        Vec3<float> xb = xi;
+        if (P.has_wall) xb = mirror_point<float>(P, xi);
+        float acc[MG];
+#pragma unroll
+        for (int g = 0; g < MG; ++g) acc[g] = 0.f;
+        const int t0 = P.vt_ptr[j], t1 = P.vt_ptr[j + 1];
+        for (int b0 = t0; b0 < t1; b0 += kColTets) {
+            const int nt = min(kColTets, t1 - b0);
+            __syncthreads();   // the previous batch's table is no longer read
+            for (int e = threadIdx.x; e < nt * 18; e += blockDim.x) {
+                const int t = e / 18, q = e - t * 18;
+                const int packed = P.vt_idx[b0 + t];
+                const int tet = packed >> 2, loc = packed & 3;
+                const int4 tv = P.tet[tet];
+                const Vec3<float> v0 = load_xyz<float>(P, tv.x), v1 = load_xyz<float>(P, tv.y),
+                                  v2 = load_xyz<float>(P, tv.z), v3 = load_xyz<float>(P, tv.w);
+                const float b0w = tet_b<float>(q, 0), b1 = tet_b<float>(q, 1), b2 = tet_b<float>(q, 2),
+                            b3 = tet_b<float>(q, 3);
+                Vec3<float> y;
+                y.x = b0w * v0.x + b1 * v1.x + b2 * v2.x + b3 * v3.x;
+                y.y = b0w * v0.y + b1 * v1.y + b2 * v2.y + b3 * v3.y;
+                y.z = b0w * v0.z + b1 * v1.z + b2 * v2.z + b3 * v3.z;
+                const float lam = loc == 0 ? b0w : (loc == 1 ? b1 : (loc == 2 ? b2 : b3));
+                const float w = P.tvol32[tet] * tet_w<float>(q) * lam * kappa_at<float>(P, y.x, y.y, y.z) * inv4pi;
+                s_pt[t][q] = make_float4(y.x, y.y, y.z, w);
+                if (q == 0) {
+                    Vec3<float> cen;
+                    float diam, vol;
+                    load_tgeo<float>(P, tet, cen, diam, vol);
+                    s_cen[t] = make_float4(cen.x, cen.y, cen.z, 4.f * diam * diam);
+                }
+            }
+            __syncthreads();
+            if (row_ok) {
+                for (int t = 0; t < nt; ++t) {
+                    const float4 ce = s_cen[t];
+                    const Vec3<float> cen = {ce.x, ce.y, ce.z};
+                    const int nd = dist2<float>(xi, cen) < ce.w ? 14 : 4;
+                    const int nr = P.has_wall ? (dist2<float>(xb, cen) < ce.w ? 14 : 4) : 0;
+                    for (int q = 0; q < nd + nr; ++q) {
+                        const bool refl = q >= nd;
+                        const int qq = refl ? q - nd : q;
+                        const float4 pt = s_pt[t][((refl ? nr : nd) == 14 ? 4 : 0) + qq];
+                        const Vec3<float> y = {pt.x, pt.y, pt.z};
+                        float r2, tau;
+                        if (!refl) {
+                            r2 = dist2<float>(xi, y);
+                            tau = optical_depth<float>(P, xi, y);
+                        } else {
+                            const Vec3<float> xp = wall_point<float>(P, xb, y);
+                            r2 = dist2<float>(xb, y);
+                            tau = optical_depth<float>(P, xi, xp) + optical_depth<float>(P, xp, y);
+                        }
+                        float w = pt.w / r2;
+                        if (refl) w *= (float)P.R0;
+                        if (P.c_arith) {
+                            float E = expf(-P.c0f * tau);
+                            const float D = expf(-P.dcf * tau);
+#pragma unroll
+                            for (int g = 0; g < MG; ++g) {
+                                if (g < P.G) acc[g] += w * P.cf[g] * E;
+                                E *= D;
+                            }
+                        } else {
+#pragma unroll
+                            for (int g = 0; g < MG; ++g)
+                                if (g < P.G) acc[g] += w * P.cf[g] * expf(-P.cf[g] * tau);
+                        }
+                    }
+                }
+            }
+        }
+        if (row_ok) {
+#pragma unroll
+            for (int g = 0; g < MG; ++g)
+                if (g < P.G) buf[a.cbuf + (int64_t)g * a.m + pos] = acc[g];
+        }
     }
 }
 
@@ -1268,7 +1377,7 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
                     pool_cap = ncap;
                     D.pool = pool;
                 }
-                int64_t ndot = 0;
+                int64_t ndot = 0, nchunk = 0;
                 for (int b = 0; b < nb; ++b) {
                     if (status[b] != ACA_ACTIVE) continue;
                     AcaActive a{};
@@ -1287,6 +1396,8 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
                     pool_used += (int64_t)G * a.n;
                     a.dot0 = ndot;
                     ndot += h_rank[b] + 1;
+                    a.first_chunk = nchunk;
+                    nchunk += (a.m + kColRows - 1) / kColRows;
                     fr += a.n;
                     fc += a.m;
                     bufr += (int64_t)G * a.n;
@@ -1324,11 +1435,11 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
                 aca_row_residual<<<std::max(1, eg_r), 256, 0, s>>>(D, d_act, na, fr, rowbuf);
                 aca_row_pivot<<<(na + 127) / 128, 128, 0, s>>>(D, d_act, na, rowbuf);
                 aca_store_v<<<std::max(1, eg_r), 256, 0, s>>>(D, d_act, na, fr, rowbuf);
-                // 2. pivot columns
+                // 2. pivot columns: one CTA per 64-row chunk, the column's quadrature
+                // points tabulated once per chunk
                 {
-                    int grid = grid_for(fc);
-#define RT_LAUNCH_ACAC(MG) \
-    aca_entries_kernel<MG><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, d_act, na, fc, 1, D.istar, D.jstar, colbuf)
+                    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nchunk, (int64_t)sms * 32));
+#define RT_LAUNCH_ACAC(MG) aca_col_kernel<MG><<<grid, kColRows, 0, s>>>(op.kp, d_act, na, nchunk, D.jstar, colbuf)
                     RT_DISPATCH_MG(G, RT_LAUNCH_ACAC);
 #undef RT_LAUNCH_ACAC
                     RT_CUDA_TRY(cudaGetLastError());
