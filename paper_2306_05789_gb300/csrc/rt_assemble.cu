@@ -241,6 +241,26 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) aca_entries_kernel(KernelPa
 constexpr int kColRows = 64;
 constexpr int kColTets = 32;
 
+// acc[g] += w c_g exp(-c_g tau) over the groups (Eq. 5 with the group scale
+// c_g of the multi-frequency operator); exp recurrence when c_g is arithmetic.
+template <int MG>
+__device__ __forceinline__ void row_accumulate(const KernelParams& P, float (&acc)[MG], float w, float tau)
+{
+    if (P.c_arith) {
+        float E = expf(-P.c0f * tau);
+        const float D = expf(-P.dcf * tau);
+#pragma unroll
+        for (int g = 0; g < MG; ++g) {
+            if (g < P.G) acc[g] += w * P.cf[g] * E;
+            E *= D;
+        }
+    } else {
+#pragma unroll
+        for (int g = 0; g < MG; ++g)
+            if (g < P.G) acc[g] += w * P.cf[g] * expf(-P.cf[g] * tau);
+    }
+}
+
 template <int MG>
 __global__ void __launch_bounds__(kColRows) aca_col_kernel(KernelParams P, const AcaActive* __restrict__ act, int na,
                                                            int64_t nchunks, const int* __restrict__ jstar,
@@ -298,35 +318,22 @@ __global__ void __launch_bounds__(kColRows) aca_col_kernel(KernelParams P, const
                     const Vec3<float> cen = {ce.x, ce.y, ce.z};
                     const int nd = dist2<float>(xi, cen) < ce.w ? 14 : 4;
                     const int nr = P.has_wall ? (dist2<float>(xb, cen) < ce.w ? 14 : 4) : 0;
-                    for (int q = 0; q < nd + nr; ++q) {
-                        const bool refl = q >= nd;
-                        const int qq = refl ? q - nd : q;
-                        const float4 pt = s_pt[t][((refl ? nr : nd) == 14 ? 4 : 0) + qq];
+                    // direct points first, then the mirror-reflected ones: two
+                    // loops, so that lanes whose rules differ never run the
+                    // direct and the reflected branch at the same step
+                    const float4* pd = s_pt[t] + (nd == 14 ? 4 : 0);
+                    for (int q = 0; q < nd; ++q) {
+                        const float4 pt = pd[q];
                         const Vec3<float> y = {pt.x, pt.y, pt.z};
-                        float r2, tau;
-                        if (!refl) {
-                            r2 = dist2<float>(xi, y);
-                            tau = optical_depth<float>(P, xi, y);
-                        } else {
-                            const Vec3<float> xp = wall_point<float>(P, xb, y);
-                            r2 = dist2<float>(xb, y);
-                            tau = optical_depth<float>(P, xi, xp) + optical_depth<float>(P, xp, y);
-                        }
-                        float w = pt.w / r2;
-                        if (refl) w *= (float)P.R0;
-                        if (P.c_arith) {
-                            float E = expf(-P.c0f * tau);
-                            const float D = expf(-P.dcf * tau);
-#pragma unroll
-                            for (int g = 0; g < MG; ++g) {
-                                if (g < P.G) acc[g] += w * P.cf[g] * E;
-                                E *= D;
-                            }
-                        } else {
-#pragma unroll
-                            for (int g = 0; g < MG; ++g)
-                                if (g < P.G) acc[g] += w * P.cf[g] * expf(-P.cf[g] * tau);
-                        }
+                        row_accumulate<MG>(P, acc, pt.w / dist2<float>(xi, y), optical_depth<float>(P, xi, y));
+                    }
+                    const float4* pr = s_pt[t] + (nr == 14 ? 4 : 0);
+                    for (int q = 0; q < nr; ++q) {
+                        const float4 pt = pr[q];
+                        const Vec3<float> y = {pt.x, pt.y, pt.z};
+                        const Vec3<float> xp = wall_point<float>(P, xb, y);
+                        const float tau = optical_depth<float>(P, xi, xp) + optical_depth<float>(P, xp, y);
+                        row_accumulate<MG>(P, acc, (float)P.R0 * pt.w / dist2<float>(xb, y), tau);
                     }
                 }
             }
@@ -681,58 +688,63 @@ __global__ void __launch_bounds__(256) row_cluster_kernel(KernelParams P, const 
 #pragma unroll
             for (int g = 0; g < MG; ++g) a0[g] = a1[g] = a2[g] = a3[g] = 0.f;
         }
-        for (int q = 0; q < nd + nr; ++q) {
-            const bool refl = q >= nd;
-            const int qq = refl ? q - nd : q;
-            const int row = ((refl ? nr : nd) == 14 ? 4 : 0) + qq;
-            const float b0 = tet_b<float>(row, 0), b1 = tet_b<float>(row, 1), b2 = tet_b<float>(row, 2),
-                        b3 = tet_b<float>(row, 3);
-            Vec3<float> y;
-            y.x = b0 * v0.x + b1 * v1.x + b2 * v2.x + b3 * v3.x;
-            y.y = b0 * v0.y + b1 * v1.y + b2 * v2.y + b3 * v3.y;
-            y.z = b0 * v0.z + b1 * v1.z + b2 * v2.z + b3 * v3.z;
-            float r2, tau;
-            if (!refl) {
-                r2 = dist2<float>(xi, y);
-                tau = optical_depth<float>(P, xi, y);
-            } else {
-                const Vec3<float> xp = wall_point<float>(P, xb, y);
-                r2 = dist2<float>(xb, y);
-                tau = optical_depth<float>(P, xi, xp) + optical_depth<float>(P, xp, y);
-            }
-            float w = vol * tet_w<float>(row) * kappa_at<float>(P, y.x, y.y, y.z) * inv4pi / r2;
-            if (refl) w *= (float)P.R0;
-            if constexpr (MG > 0) {
-                auto add = [&](int g, float eg) {
-                    const float val = w * P.cf[g] * eg;
-                    a0[g] += val * b0;
-                    a1[g] += val * b1;
-                    a2[g] += val * b2;
-                    a3[g] += val * b3;
-                };
-                if (P.c_arith) {
-                    // exp(-c_g tau) as exp(-c_0 tau) exp(-dc tau)^g: two SFU exponentials per point
-                    float E = expf(-P.c0f * tau);
-                    const float D = expf(-P.dcf * tau);
+        // Pass 0 visits the direct rule's points; when the reflected rule is
+        // the same one (nd == nr, the usual case away from the wall), the
+        // point, its weight and kappa(y) serve both terms.  Pass 1 visits the
+        // reflected rule's points only when the two rules differ.
+        const bool share = nd == nr;
+        for (int pass = 0; pass < 2; ++pass) {
+            const int nq = pass == 0 ? nd : (share ? 0 : nr);
+            const int base = (pass == 0 ? nd : nr) == 14 ? 4 : 0;
+            for (int q = 0; q < nq; ++q) {
+                const int row = base + q;
+                const float b0 = tet_b<float>(row, 0), b1 = tet_b<float>(row, 1), b2 = tet_b<float>(row, 2),
+                            b3 = tet_b<float>(row, 3);
+                Vec3<float> y;
+                y.x = b0 * v0.x + b1 * v1.x + b2 * v2.x + b3 * v3.x;
+                y.y = b0 * v0.y + b1 * v1.y + b2 * v2.y + b3 * v3.y;
+                y.z = b0 * v0.z + b1 * v1.z + b2 * v2.z + b3 * v3.z;
+                const float wq = vol * tet_w<float>(row) * kappa_at<float>(P, y.x, y.y, y.z) * inv4pi;
+                auto accumulate = [&](float w, float tau) {
+                    if constexpr (MG > 0) {
+                        auto add = [&](int g, float eg) {
+                            const float val = w * P.cf[g] * eg;
+                            a0[g] += val * b0;
+                            a1[g] += val * b1;
+                            a2[g] += val * b2;
+                            a3[g] += val * b3;
+                        };
+                        if (P.c_arith) {
+                            // exp(-c_g tau) as exp(-c_0 tau) exp(-dc tau)^g: two SFU exponentials per point
+                            float E = expf(-P.c0f * tau);
+                            const float D = expf(-P.dcf * tau);
 #pragma unroll
-                    for (int g = 0; g < MG; ++g) {
-                        if (g < G) add(g, E);
-                        E *= D;
+                            for (int g = 0; g < MG; ++g) {
+                                if (g < G) add(g, E);
+                                E *= D;
+                            }
+                        } else {
+#pragma unroll
+                            for (int g = 0; g < MG; ++g)
+                                if (g < G) add(g, expf(-P.cf[g] * tau));
+                        }
+                    } else {
+                        for (int g = 0; g < G; ++g) {
+                            const float cg = P.cf[g];
+                            const float val = w * cg * expf(-cg * tau);
+                            float* a = acc + g * n;
+                            if (in0) atomicAdd(a + jj[0], val * b0);
+                            if (in1) atomicAdd(a + jj[1], val * b1);
+                            if (in2) atomicAdd(a + jj[2], val * b2);
+                            if (in3) atomicAdd(a + jj[3], val * b3);
+                        }
                     }
-                } else {
-#pragma unroll
-                    for (int g = 0; g < MG; ++g)
-                        if (g < G) add(g, expf(-P.cf[g] * tau));
-                }
-            } else {
-                for (int g = 0; g < G; ++g) {
-                    const float cg = P.cf[g];
-                    const float val = w * cg * expf(-cg * tau);
-                    float* a = acc + g * n;
-                    if (in0) atomicAdd(a + jj[0], val * b0);
-                    if (in1) atomicAdd(a + jj[1], val * b1);
-                    if (in2) atomicAdd(a + jj[2], val * b2);
-                    if (in3) atomicAdd(a + jj[3], val * b3);
+                };
+                if (pass == 0) accumulate(wq / dist2<float>(xi, y), optical_depth<float>(P, xi, y));
+                if (pass == 1 || share) {
+                    const Vec3<float> xp = wall_point<float>(P, xb, y);
+                    const float tau = optical_depth<float>(P, xi, xp) + optical_depth<float>(P, xp, y);
+                    accumulate((float)P.R0 * wq / dist2<float>(xb, y), tau);
                 }
             }
         }
@@ -1012,10 +1024,17 @@ struct DotItem {
     int l;
 };
 
-// one warp per (block, l); lanes stride over rows / columns
+// one warp per (block, l).  The warp's lanes are split among the groups (gp
+// groups at a time, gp a power of two <= 4, so L = 32 / gp >= 8 lanes per
+// group and every load of a group still fills a whole 32-byte sector); each
+// group's two dot products then need a reduction over only L lanes: FP32
+// partial sums per lane (length / L terms), FP64 across lanes.
 __global__ void __launch_bounds__(256) aca_dots(AcaDev D, const AcaActive* act, const DotItem* items, int nitems)
 {
     const int lane = threadIdx.x & 31;
+    int gp = 1;
+    while (gp < D.G && gp < 4) gp <<= 1;
+    const int L = 32 / gp;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < nitems; it += nw) {
         const DotItem di = items[it];
@@ -1024,22 +1043,23 @@ __global__ void __launch_bounds__(256) aca_dots(AcaDev D, const AcaActive* act, 
         const int b = a.b;
         const int64_t ul = di.l == D.rank[b] ? a.uoff : D.uoff[(int64_t)b * D.rmax + di.l];
         const int64_t vl = di.l == D.rank[b] ? a.voff : D.voff[(int64_t)b * D.rmax + di.l];
-        for (int g = 0; g < D.G; ++g) {
-            const float* U0 = D.pool + ul + (int64_t)g * a.m;
-            const float* U1 = D.pool + a.uoff + (int64_t)g * a.m;
-            const float* V0 = D.pool + vl + (int64_t)g * a.n;
-            const float* V1 = D.pool + a.voff + (int64_t)g * a.n;
-            // FP32 partial sums per lane (short: length/32 terms), FP64 across lanes
+        for (int g0 = 0; g0 < D.G; g0 += gp) {
+            const int g = g0 + lane / L, sl = lane % L;
             float pu = 0.f, pv = 0.f;
-            for (int i = lane; i < a.m; i += 32) pu += U0[i] * U1[i];
-            for (int j = lane; j < a.n; j += 32) pv += V0[j] * V1[j];
+            if (g < D.G) {
+                const float* U0 = D.pool + ul + (int64_t)g * a.m;
+                const float* U1 = D.pool + a.uoff + (int64_t)g * a.m;
+                const float* V0 = D.pool + vl + (int64_t)g * a.n;
+                const float* V1 = D.pool + a.voff + (int64_t)g * a.n;
+                for (int i = sl; i < a.m; i += L) pu += U0[i] * U1[i];
+                for (int j = sl; j < a.n; j += L) pv += V0[j] * V1[j];
+            }
             double su = pu, sv = pv;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
+            for (int o = L >> 1; o > 0; o >>= 1) {   // xor within aligned groups of L lanes
                 su += __shfl_xor_sync(0xffffffffu, su, o);
                 sv += __shfl_xor_sync(0xffffffffu, sv, o);
             }
-            if (lane == 0) {
+            if (sl == 0 && g < D.G) {
                 double* dst = D.dots + ((a.dot0 + di.l) * D.G + g) * 2;
                 dst[0] = su;
                 dst[1] = sv;
