@@ -12,10 +12,17 @@
 //                                   + sum_dense A_g[rows(l), :] x_f[cols(b)].
 //            Each (leaf, block) pair is one contiguous chunk [count][m8] in
 //            HBM; a thread owns 4 consecutive rows and a slice of the count.
+// Both phases run as streamed persistent kernels (rt_hmv_stream.cuh): the
+// host cuts the operator into 16 KB stage records here, and a producer warp
+// per CTA bulk-copies them into a shared-memory ring.  Phase-1 rows longer
+// than one stage, and the refinement sweeps that also read the low parts of a
+// split far field, use the register-streaming kernels of rt_hmv_dev.cuh.
 // Far factors are stored transposed (V^T [r][n8]; U^T per leaf chunk
 // [r][m8]) and dense blocks column-major per leaf chunk (A^T [n][m8]), padded
 // to multiples of 8 elements with zeros so every chunk row is 16-byte aligned.
 #include <algorithm>
+#include <climits>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -26,6 +33,7 @@
 
 
 #include "rt_hmv_dev.cuh"
+#include "rt_hmv_stream.cuh"
 
 namespace rt {
 
@@ -77,6 +85,163 @@ int permute_vectors(Operator& op, const void* in, void* out, int to_tree, int is
     else
         permute_kernel<float><<<grid, 256, 0, s>>>((const float*)in, (float*)out, op.d_perm, op.N, rows, to_tree);
     return cudaGetLastError() == cudaSuccess ? RT_OK : RT_ECUDA;
+}
+
+// Stage records of the streamed phases.
+//  phase 1: far blocks ordered by (padded row length, first column), so the
+//    pieces of a stage mostly share one x segment; whole V^T rows fill a stage
+//    up to kStageBytes, kMaxPieces pieces and kVecFloats gathered x values.
+//  phase 2: per leaf, its far chunks, then its dense chunks, as whole k-rows;
+//    a stage holds one kind only, so it is one [K][m8] array.
+static bool hs_long_row(int n, int esz_far)
+{
+    return round8(n) * esz_far > hs::kStageBytes || round8(n) > hs::kVecFloats;
+}
+
+static int hs_prepare(Operator& op, const std::vector<int64_t>& w_base, const std::vector<std::vector<P2Seg>>& per_leaf,
+                      const std::vector<P2Leaf>& leaves, int esz_far, std::string& err)
+{
+    op.hs_enabled = 0;
+    if (op.w_len > INT_MAX || (int64_t)op.N > INT_MAX / 2) return RT_OK;   // piece fields are 32-bit
+    int rc;
+    std::vector<HsLoad> l1, l2;
+    HsLoad cur{};
+    int used = 0, vtot = 0;
+    auto flush = [&](std::vector<HsLoad>& out, bool keep_empty) {
+        if (cur.np > 0 || keep_empty) {
+            cur.bytes = used;
+            out.push_back(cur);
+        }
+        cur = HsLoad{};
+        used = 0;
+        vtot = 0;
+    };
+    // ---- phase 1 ----
+    std::vector<int> border;
+    for (int b = 0; b < op.n_far; ++b)
+        if (!hs_long_row(op.far_blocks[b].n, esz_far)) border.push_back(b);
+    std::stable_sort(border.begin(), border.end(), [&](int a, int b) {
+        const int na = round8(op.far_blocks[a].n), nb = round8(op.far_blocks[b].n);
+        return na != nb ? na < nb : op.far_blocks[a].col0 < op.far_blocks[b].col0;
+    });
+    for (int b : border) {
+        const FarBlock& fb = op.far_blocks[b];
+        const int r = op.rank[b], n8 = round8(fb.n);
+        const int rowb = n8 * esz_far;
+        for (int k = 0; k < r;) {
+            // the stage's x segment for this block's columns, if already gathered
+            int vo = -1;
+            for (int q = 0; q < cur.np; ++q)
+                if (cur.p[q].vlen > 0 && cur.p[q].vsrc == fb.col0 && cur.p[q].valid == fb.n) vo = cur.p[q].vo;
+            const int fit = (hs::kStageBytes - used) / rowb;
+            if (fit == 0 || cur.np == hs::kMaxPieces || (vo < 0 && vtot + n8 > hs::kVecFloats)) {
+                flush(l1, false);
+                continue;
+            }
+            const int take = std::min(fit, r - k);
+            HsPiece& pc = cur.p[cur.np++];
+            pc = HsPiece{};
+            pc.a = op.far_v_off[b] + (int64_t)k * n8;
+            pc.gstride = (int64_t)r * n8;
+            pc.vsrc = fb.col0;
+            pc.soff = used;
+            pc.bytes = take * rowb;
+            pc.rows = take;
+            pc.n8 = n8;
+            if (vo >= 0) {
+                pc.vo = vo;
+                pc.vlen = 0;
+            } else {
+                pc.vo = vtot;
+                pc.vlen = n8;
+                vtot += n8;
+            }
+            pc.valid = fb.n;
+            pc.r = r;
+            pc.wv = (int)(w_base[b] + k);
+            pc.kind = 0;
+            used += pc.bytes;
+            k += take;
+        }
+    }
+    flush(l1, false);
+    // ---- phase 2 ----
+    const int nl = (int)leaves.size();
+    std::vector<int> leaf0(nl + 1);
+    std::vector<int64_t> leaf_bytes(nl, 0);
+    for (int l = 0; l < nl; ++l) {
+        leaf0[l] = (int)l2.size();
+        const int m8 = leaves[l].m8;
+        for (int kind = 0; kind < 2; ++kind) {
+            for (const P2Seg& sg : per_leaf[l]) {
+                if (sg.kind != kind) continue;
+                const int rowb = m8 * (kind ? 4 : esz_far);
+                for (int k = 0; k < sg.count;) {
+                    const int fit = std::min((hs::kStageBytes - used) / rowb, hs::kVecFloats - cur.K);
+                    if (fit <= 0 || cur.np == hs::kMaxPieces) {
+                        flush(l2, false);
+                        continue;
+                    }
+                    const int take = std::min(fit, sg.count - k);
+                    HsPiece& pc = cur.p[cur.np++];
+                    pc = HsPiece{};
+                    pc.a = sg.a + (int64_t)k * m8;
+                    pc.gstride = sg.gstride;
+                    pc.vsrc = sg.vbase + k;
+                    pc.soff = used;
+                    pc.bytes = take * rowb;
+                    pc.rows = take;
+                    pc.n8 = m8;
+                    pc.vo = cur.K;
+                    pc.vlen = take;
+                    pc.valid = take;
+                    pc.r = kind ? 0 : sg.count;
+                    pc.kind = kind;
+                    cur.kind = kind;
+                    cur.K += take;
+                    used += pc.bytes;
+                    leaf_bytes[l] += pc.bytes;
+                    k += take;
+                }
+            }
+            flush(l2, false);   // a stage holds one kind
+        }
+        if ((int)l2.size() == leaf0[l]) flush(l2, true);   // every leaf has a record, so its rows are written
+    }
+    leaf0[nl] = (int)l2.size();
+    std::vector<int> order(nl);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return leaf_bytes[a] > leaf_bytes[b]; });
+    std::vector<int2> items;
+    items.reserve((size_t)nl * op.F);
+    for (int l : order)
+        for (int f = 0; f < op.F; ++f) items.push_back(make_int2(l, f));
+    HsLoad *d1 = nullptr, *d2 = nullptr;
+    int* d0 = nullptr;
+    int2* di = nullptr;
+    if (!l1.empty() && ((rc = dev_alloc(op, &d1, l1.size(), err)) || (rc = upload_async(op, d1, l1.data(), l1.size(), err))))
+        return rc;
+    if ((rc = dev_alloc(op, &d2, l2.size(), err)) || (rc = upload_async(op, d2, l2.data(), l2.size(), err))) return rc;
+    if ((rc = dev_alloc(op, &d0, leaf0.size(), err)) || (rc = upload_async(op, d0, leaf0.data(), leaf0.size(), err)))
+        return rc;
+    if ((rc = dev_alloc(op, &di, items.size(), err)) || (rc = upload_async(op, di, items.data(), items.size(), err)))
+        return rc;
+    op.d_hs1 = d1;
+    op.n_hs1 = (int)l1.size();
+    op.d_hs2 = d2;
+    op.n_hs2 = (int)l2.size();
+    op.d_hs2_leaf0 = d0;
+    op.d_hs2_items = di;
+    op.n_hs2_items = (int)items.size();
+    const int smem = (int)hs_smem_bytes();
+    RT_CUDA_TRY(cudaFuncSetAttribute(hmv_s1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    RT_CUDA_TRY(cudaFuncSetAttribute(hmv_s1<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    RT_CUDA_TRY(cudaFuncSetAttribute(hmv_s1<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    RT_CUDA_TRY(cudaFuncSetAttribute(hmv_s2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    RT_CUDA_TRY(cudaFuncSetAttribute(hmv_s2<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    RT_CUDA_TRY(cudaFuncSetAttribute(hmv_s2<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    op.hs_enabled = 1;
+    return RT_OK;
 }
 
 int hmatvec_prepare(Operator& op, std::string& err)
@@ -198,12 +363,18 @@ int hmatvec_prepare(Operator& op, std::string& err)
     op.h_p1_rows.assign(reinterpret_cast<const char*>(rows.data()),
                         reinterpret_cast<const char*>(rows.data()) + sizeof(P1Row) * rows.size());
     op.n_p1 = (int)items.size();
+    op.n_p1_long = 0;
+    while (op.n_p1_long < op.n_p1 && hs_long_row(rows[items[op.n_p1_long].row0].n, esz_far))
+        ++op.n_p1_long;
     op.d_p2_leaf = d_l;
     op.n_p2 = nl;
     op.d_p2_segs = d_s;
     op.n_p2_segs = (int)segs.size();
     op.w_len = wl;
     if ((rc = dev_alloc(op, &op.d_w, (size_t)std::max<int64_t>(wl, 1), err))) return rc;
+    if ((rc = dev_alloc(op, &op.apply_err, 1, err))) return rc;
+    RT_CUDA_TRY(cudaMemsetAsync(op.apply_err, 0, sizeof(int), op.stream));
+    if ((rc = hs_prepare(op, w_base, per_leaf, leaves, esz_far, err))) return rc;
     // algorithmic bytes of one apply: operator data once per frequency, X read, Y written
     int64_t far_e = 0, near_e = 0;
     for (int b = 0; b < op.n_far; ++b) far_e += (int64_t)op.rank[b] * (op.far_blocks[b].m + op.far_blocks[b].n);
@@ -227,6 +398,34 @@ static int launch_hmv(Operator& op, const float* x, float* w, float* y, cudaStre
     const P2Leaf* lv = (const P2Leaf*)op.d_p2_leaf;
     const P2Seg* sg = (const P2Seg*)op.d_p2_segs;
     dim3 g1(op.n_p1, F), g2(op.n_p2, F);
+    if (op.hs_enabled && !lo) {
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int per_sm = hs::kCtasPerSm;
+        const int smem = (int)hs_smem_bytes();
+        const HsLoad* l1 = (const HsLoad*)op.d_hs1;
+        const HsLoad* l2 = (const HsLoad*)op.d_hs2;
+        const int2* itm = (const int2*)op.d_hs2_items;
+        const int gs1 = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)op.n_hs1 * F, (int64_t)per_sm * sms));
+        const int gs2 = std::max(1, std::min(op.n_hs2_items, per_sm * sms));
+#define RT_HMS(T)                                                                                                 \
+    do {                                                                                                          \
+        const T* fp = (const T*)op.d_far;                                                                         \
+        if (op.n_p1_long > 0)                                                                                     \
+            hmv_phase1<T, false><<<dim3(op.n_p1_long, F), 256, 0, s>>>(it, rw, fp, nullptr, x, w, N, op.d_fq_group); \
+        if (op.n_hs1 > 0)                                                                                         \
+            hmv_s1<T><<<gs1, hs::kThreads, smem, s>>>(l1, op.n_hs1, fp, x, w, N, F, op.d_fq_group, op.apply_err);  \
+        hmv_s2<T><<<gs2, hs::kThreads, smem, s>>>(l2, op.d_hs2_leaf0, itm, op.n_hs2_items, lv, fp, op.d_near, x, w, \
+                                                 y, N, op.d_fq_group, op.apply_err);                              \
+    } while (0)
+        if (op.far_prec == RT_PREC_F32) RT_HMS(float);
+        else if (op.far_prec == RT_PREC_BF16) RT_HMS(__nv_bfloat16);
+        else RT_HMS(__half);
+#undef RT_HMS
+        RT_CUDA_TRY(cudaGetLastError());
+        return RT_OK;
+    }
 #define RT_HMV(T, LO)                                                                                             \
     do {                                                                                                          \
         const T* fp = (const T*)op.d_far;                                                                         \

@@ -206,6 +206,17 @@ struct Operator {
     void* d_p2_leaf = nullptr;  int n_p2 = 0;
     void* d_p2_segs = nullptr;  int n_p2_segs = 0;
     float* d_w = nullptr;       int64_t w_len = 0;   // phase-1 scratch [sum r][F]
+    // streamed form of the two phases (bulk copies into a shared-memory ring):
+    // stage records of phase 1 and phase 2, the first record of every leaf,
+    // the (leaf, frequency) items in launch order, and the number of phase-1
+    // items (a prefix of d_p1_items) whose rows are too long for one stage
+    int hs_enabled = 0;
+    void* d_hs1 = nullptr;      int n_hs1 = 0;
+    void* d_hs2 = nullptr;      int n_hs2 = 0;
+    int* d_hs2_leaf0 = nullptr;
+    void* d_hs2_items = nullptr; int n_hs2_items = 0;
+    int n_p1_long = 0;
+    int* apply_err = nullptr;   // set by a bounded wait of an apply kernel that gave up
     float* d_xt = nullptr;      // permuted input scratch [F][N]
     float* d_yt = nullptr;      // permuted output scratch [F][N]
     // solver scratch
@@ -260,7 +271,8 @@ int apply_noalloc(Operator& op, const void* X, void* Y, cudaStream_t s, std::str
 size_t apply_noalloc_limit();
 int tc_prepare(Operator& op, std::string& err);
 int tc_apply(Operator& op, const float* X, float* Y, cudaStream_t s, std::string& err);
-int tc_check_error(Operator& op, cudaStream_t s, std::string& err);
+// RT_ETIMEOUT (and clears the flags) if a bounded wait of an apply kernel gave up
+int apply_check_error(Operator& op, cudaStream_t s, std::string& err);
 int solve_fixed_point(Operator& op, const rt_solve_opts& o, void* J, double* T, rt_solve_stats& st,
                       cudaStream_t s, std::string& err);
 

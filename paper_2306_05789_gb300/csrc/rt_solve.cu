@@ -317,7 +317,7 @@ static int solve_impl(Operator& op, const rt_solve_opts& o, void* J_out, double*
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
     op.use_lo = 0;
-    if ((rc = tc_check_error(op, s, err))) return rc;   // a bounded tensor-core wait gave up
+    if ((rc = apply_check_error(op, s, err))) return rc;   // a bounded apply wait gave up
     int fail = 0;
     RT_CUDA_TRY(cudaMemcpyAsync(&fail, d_ctr + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
     // results back to caller order

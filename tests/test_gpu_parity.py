@@ -311,6 +311,35 @@ def test_invalid_inputs_are_rejected():
         rt.rt_build_operator(p, rt.hparams(mode=rt.RT_MODE_DENSE, prec=rt.RT_PREC_BF16))
 
 
+def test_far_rows_longer_than_a_stage_match_the_oracle():
+    """A 26^3 box stretched 8x along x has admissible blocks with 4394 columns.
+    Their FP32 V^T rows (17.6 KB) exceed one 16 KB stage of the streamed
+    phase 1 and go to the register kernel, while every other row is streamed.
+    Rows of those blocks must still match dense FP64 rows (Section 2.1)."""
+    p = W.cube_problem(26, W.sinprod_kappa(0.5), W.midpoint_freqs(2, albedo=0.3, c_offset=0.5), R0=0.5,
+                       name="box26x8")
+    p.xyz = p.xyz * np.array([8.0, 1.0, 1.0])
+    perm, blocks, _ = rt.rt_plan(p.xyz, 64, 2.0)
+    adm = blocks[blocks[:, 4] == 1]
+    long = adm[((adm[:, 3] + 7) // 8 * 8) * 4 > 16384]
+    assert len(long) > 0
+    rows = np.unique(np.concatenate([perm[long[0, 0] + np.linspace(0, long[0, 1] - 1, 5).astype(int)],
+                                     W.sample_rows(p.N, 3, seed=2)]))
+    op = rt.rt_build_operator(p, rt.hparams())
+    try:
+        X = W.rand_vectors((p.freqs.F, p.N), seed=3)
+        Xd = torch.tensor(X, dtype=torch.float32, device=DEV)
+        Y = torch.zeros_like(Xd)
+        op.apply(Xd, Y)
+        torch.cuda.synchronize()
+        R = O.G_rows(p, rows)
+        _, gidx = O.groups_of(p.freqs)
+        ref = np.stack([R[:, gidx[f], :] @ X[f] for f in range(p.freqs.F)])
+        assert rel_l2(Y.cpu().numpy()[:, rows], ref) < 1e-4
+    finally:
+        op.free()
+
+
 # ---------------------------------------------------------------------------
 # benchmark size: 32^3, 16 frequencies (sampled rows)
 # ---------------------------------------------------------------------------
