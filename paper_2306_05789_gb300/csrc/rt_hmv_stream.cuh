@@ -147,39 +147,58 @@ __device__ __forceinline__ HsRing hs_ring_init()
     return R;
 }
 
-// One producer step of stage slot s (the whole producer warp): wait until the
-// slot is free (use u > 0), copy the record's pieces in, gather the vector
-// values, arrive.  Vector values come from X (phase 1; dense pieces) or W (far
-// pieces of phase 2).  Returns false on timeout.
+// A stage record as the producer warp holds it: the header (every lane) and
+// piece `lane`.  Records are fixed-size, so every lane < kMaxPieces may read
+// its slot whatever the piece count: header and pieces arrive in one round
+// trip, and the producer loads the next stage's record while it fills the
+// current one.
+struct HsRec {
+    int4 hdr;     // np, bytes, K, kind
+    HsPiece pc;   // piece `lane` (meaningful for lane < np)
+    int f, g;     // frequency and its kappa group
+};
+
+__device__ __forceinline__ void hs_fetch(HsRec& c, const HsLoad* __restrict__ rec, int f,
+                                         const int* __restrict__ fgroup)
+{
+    const int lane = threadIdx.x & 31;
+    c.hdr = *reinterpret_cast<const int4*>(rec);
+    if (lane < hs::kMaxPieces) c.pc = rec->p[lane];
+    c.f = f;
+    c.g = fgroup[f];
+}
+
+// Fill stage slot s for its use u (the whole producer warp): wait until the
+// slot is free (u > 0), copy the record's pieces in, gather the vector values,
+// arrive.  Vector values come from X (phase 1; dense pieces) or W (far pieces
+// of phase 2).  Returns false on timeout.
 template <class T>
-__device__ __forceinline__ bool hs_produce(const HsRing& R, int s, uint32_t u, const HsLoad* __restrict__ rec, int f,
-                                           int g, const T* __restrict__ far, const float* __restrict__ nearp,
-                                           const float* __restrict__ X, const float* __restrict__ W, int N,
-                                           bool phase2)
+__device__ __forceinline__ bool hs_fill(const HsRing& R, int s, uint32_t u, const HsRec& c, const T* __restrict__ far,
+                                        const float* __restrict__ nearp, const float* __restrict__ X,
+                                        const float* __restrict__ W, int N, bool phase2)
 {
     const int lane = threadIdx.x & 31;
     // every lane observes the phase it depends on (its writes overwrite the slot)
     if (u > 0 && !__all_sync(0xffffffffu, bulk::wait(R.empty(s), (u - 1) & 1u))) return false;
-    const int4 hdr = *reinterpret_cast<const int4*>(rec);   // np, bytes, K, kind
-    HsPiece pc{};
+    const int np = c.hdr.x;
+    const HsPiece& pc = c.pc;
     const float* vb = nullptr;   // vector values of this lane's piece
-    if (lane < hdr.x) {
-        pc = rec->p[lane];
+    if (lane < np) {
         R.meta[s].p[lane] = pc;
-        vb = (!phase2 || pc.kind == 1) ? X + (int64_t)f * N + pc.vsrc : W + pc.vsrc + (int64_t)f * pc.r;
+        vb = (!phase2 || pc.kind == 1) ? X + (int64_t)c.f * N + pc.vsrc : W + pc.vsrc + (int64_t)c.f * pc.r;
     }
     if (lane == 0) {
-        *reinterpret_cast<int4*>(&R.meta[s]) = hdr;
-        bulk::expect_tx(R.full(s), (uint32_t)hdr.y);
+        *reinterpret_cast<int4*>(&R.meta[s]) = c.hdr;
+        bulk::expect_tx(R.full(s), (uint32_t)c.hdr.y);
     }
     __syncwarp();
-    if (lane < hdr.x) {
-        const void* src = pc.kind == 1 ? (const void*)(nearp + pc.a + (int64_t)g * pc.gstride)
-                                       : (const void*)(far + pc.a + (int64_t)g * pc.gstride);
+    if (lane < np) {
+        const void* src = pc.kind == 1 ? (const void*)(nearp + pc.a + (int64_t)c.g * pc.gstride)
+                                       : (const void*)(far + pc.a + (int64_t)c.g * pc.gstride);
         bulk::copy(bulk::saddr(R.stage + (size_t)s * hs::kStageBytes + pc.soff), src, (uint32_t)pc.bytes, R.full(s));
     }
     float* sv = R.vec + s * hs::kVecFloats;
-    for (int p = 0; p < hdr.x; ++p) {
+    for (int p = 0; p < np; ++p) {
         const int vlen = __shfl_sync(0xffffffffu, pc.vlen, p);
         if (vlen == 0) continue;
         const int vo = __shfl_sync(0xffffffffu, pc.vo, p), valid = __shfl_sync(0xffffffffu, pc.valid, p);
@@ -222,10 +241,14 @@ __global__ void __launch_bounds__(hs::kThreads) hmv_s1(const HsLoad* __restrict_
     const int64_t total = (int64_t)nloads * F;
     if (warp >= hs::kConsumerWarps) {
         const int s = warp - hs::kConsumerWarps;
-        uint32_t u = 0;
-        for (int64_t j = blockIdx.x + (int64_t)s * gridDim.x; j < total; j += (int64_t)hs::kStages * gridDim.x, ++u) {
-            const int f = (int)(j % F);
-            if (!hs_produce<T>(R, s, u, loads + j / F, f, fgroup[f], far, nullptr, X, nullptr, N, false)) {
+        const int64_t step = (int64_t)hs::kStages * gridDim.x;
+        int64_t j = blockIdx.x + (int64_t)s * gridDim.x;
+        HsRec nxt;
+        if (j < total) hs_fetch(nxt, loads + j / F, (int)(j % F), fgroup);
+        for (uint32_t u = 0; j < total; j += step, ++u) {
+            const HsRec cur = nxt;
+            if (j + step < total) hs_fetch(nxt, loads + (j + step) / F, (int)((j + step) % F), fgroup);
+            if (!hs_fill<T>(R, s, u, cur, far, nullptr, X, nullptr, N, false)) {
                 if (lane == 0) atomicExch(err, 1);
                 hs_drain(R, s, u);
                 return;
@@ -245,56 +268,69 @@ __global__ void __launch_bounds__(hs::kThreads) hmv_s1(const HsLoad* __restrict_
         const unsigned char* st = R.stage + (size_t)s * hs::kStageBytes;
         const float* sv = R.vec + s * hs::kVecFloats;
         const int np = R.meta[s].np;
-        int bbase = 0;   // row batches of the earlier pieces: warps take batches round robin
-        for (int p = 0; p < np; ++p) {
-            const HsPiece pc = R.meta[s].p[p];
-            const T* V = reinterpret_cast<const T*>(st + pc.soff);
-            const float* xs = sv + pc.vo;
-            // lanes per row: about four 16-byte quads each, and at least 8 so
-            // that the lanes of a row cover all 32 banks (rows are 32-byte
-            // multiples apart)
-            const int nq = pc.n8 / VW;
-            const int sw = nq <= 32 ? 8 : (nq <= 64 ? 16 : 32);
-            const int per = 32 / sw, sl = lane & (sw - 1);
-            const int nb = (pc.rows + per - 1) / per;
-            // the loop bound is warp-uniform, so every lane reaches the shuffles
-            for (int b = (warp - bbase % hs::kConsumerWarps + hs::kConsumerWarps) % hs::kConsumerWarps; b < nb;
-                 b += hs::kConsumerWarps) {
-                const int row = b * per + lane / sw;
-                const bool rok = row < pc.rows;
-                float acc = 0.f, acc2 = 0.f;
-                if (rok) {
-                    const T* vr = V + row * pc.n8;
-                    int q = sl;
-                    for (; q + sw < nq; q += 2 * sw) {
-                        float v[VW], x[VW], v2[VW], x2[VW];
-                        lds16(vr + q * VW, v);
-                        lds16(vr + (q + sw) * VW, v2);
-#pragma unroll
-                        for (int e = 0; e < VW; e += 4) {
-                            lds16(xs + q * VW + e, x + e);
-                            lds16(xs + (q + sw) * VW + e, x2 + e);
-                        }
-#pragma unroll
-                        for (int e = 0; e < VW; ++e) {
-                            acc += v[e] * x[e];
-                            acc2 += v2[e] * x2[e];
-                        }
-                    }
-                    if (q < nq) {
-                        float v[VW], x[VW];
-                        lds16(vr + q * VW, v);
-#pragma unroll
-                        for (int e = 0; e < VW; e += 4) lds16(xs + q * VW + e, x + e);
-#pragma unroll
-                        for (int e = 0; e < VW; ++e) acc += v[e] * x[e];
-                    }
-                    acc += acc2;
-                }
-                for (int o = sw >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, sw);
-                if (rok && sl == 0) W[(int64_t)pc.wv + row + (int64_t)f * pc.r] = acc;
+        // Work units are (piece, row batch) pairs numbered through the stage;
+        // warp w takes units w, w + 8, ...  Each warp walks the piece list
+        // forward once, so a piece's set-up is paid only by warps with a
+        // unit in it, and a stage of few long rows still spreads over all
+        // warps.
+        int p = -1, ubase = 0, nb = 0;
+        int n8 = 0, rows = 0, r = 0, wv = 0, nq = 0, lg = 3;
+        const T* V = nullptr;
+        const float* xs = nullptr;
+        for (int u = warp;; u += hs::kConsumerWarps) {
+            while (u >= ubase + nb) {
+                ubase += nb;
+                if (++p >= np) break;
+                const HsPiece& pm = R.meta[s].p[p];
+                n8 = pm.n8;
+                rows = pm.rows;
+                r = pm.r;
+                wv = pm.wv;
+                V = reinterpret_cast<const T*>(st + pm.soff);
+                xs = sv + pm.vo;
+                // lanes per row: about four 16-byte quads each, and at least 8
+                // so that the lanes of a row cover all 32 banks (rows are
+                // 32-byte multiples apart)
+                nq = n8 / VW;
+                lg = nq <= 32 ? 3 : (nq <= 64 ? 4 : 5);
+                nb = (rows + (32 >> lg) - 1) >> (5 - lg);
             }
-            bbase += nb;
+            if (p >= np) break;
+            const int sw = 1 << lg, sl = lane & (sw - 1);
+            const int row = ((u - ubase) << (5 - lg)) + (lane >> lg);
+            const bool rok = row < rows;
+            float acc = 0.f, acc2 = 0.f;
+            if (rok) {
+                const T* vr = V + row * n8;
+                int q = sl;
+                for (; q + sw < nq; q += 2 * sw) {
+                    float v[VW], x[VW], v2[VW], x2[VW];
+                    lds16(vr + q * VW, v);
+                    lds16(vr + (q + sw) * VW, v2);
+#pragma unroll
+                    for (int e = 0; e < VW; e += 4) {
+                        lds16(xs + q * VW + e, x + e);
+                        lds16(xs + (q + sw) * VW + e, x2 + e);
+                    }
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) {
+                        acc += v[e] * x[e];
+                        acc2 += v2[e] * x2[e];
+                    }
+                }
+                if (q < nq) {
+                    float v[VW], x[VW];
+                    lds16(vr + q * VW, v);
+#pragma unroll
+                    for (int e = 0; e < VW; e += 4) lds16(xs + q * VW + e, x + e);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) acc += v[e] * x[e];
+                }
+                acc += acc2;
+            }
+            // p, u and lg are warp-uniform, so every lane reaches the shuffles
+            for (int o = sw >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, sw);
+            if (rok && sl == 0) W[(int64_t)wv + row + (int64_t)f * r] = acc;
         }
         __syncwarp();
         if (lane == 0) bulk::arrive(R.empty(s));
@@ -333,19 +369,34 @@ __global__ void __launch_bounds__(hs::kThreads) hmv_s2(const HsLoad* __restrict_
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp >= hs::kConsumerWarps) {
         const int s = warp - hs::kConsumerWarps;
-        int64_t i = 0;   // stage sequence of this CTA; this warp takes i % kStages == s
-        for (int j = blockIdx.x; j < nitems; j += gridDim.x) {
-            const int2 it = items[j];
-            const int g = fgroup[it.y];
-            const int ld0 = leaf_load0[it.x], ld1 = leaf_load0[it.x + 1];
-            for (int ld = ld0; ld < ld1; ++ld, ++i) {
-                if (i % hs::kStages != s) continue;
-                const uint32_t u = (uint32_t)(i / hs::kStages);
-                if (!hs_produce<T>(R, s, u, loads + ld, it.y, g, far, nearp, X, W, N, true)) {
-                    if (lane == 0) atomicExch(err, 1);
-                    hs_drain(R, s, u);
-                    return;
-                }
+        // cursor over this CTA's stage sequence: item j, its records [ld, ld1)
+        int j = blockIdx.x, ld = 0, ld1 = 0;
+        int2 it = make_int2(0, 0);
+        auto enter = [&]() {   // first record of item j or a later item
+            for (; j < nitems; j += gridDim.x) {
+                it = items[j];
+                ld = leaf_load0[it.x];
+                ld1 = leaf_load0[it.x + 1];
+                if (ld < ld1) return;
+            }
+        };
+        auto next = [&]() {    // the stage after the cursor's
+            if (++ld < ld1) return;
+            j += gridDim.x;
+            enter();
+        };
+        enter();
+        for (int k = 0; k < s && j < nitems; ++k) next();
+        HsRec nxt;
+        if (j < nitems) hs_fetch(nxt, loads + ld, it.y, fgroup);
+        for (uint32_t u = 0; j < nitems; ++u) {
+            const HsRec cur = nxt;
+            for (int k = 0; k < hs::kStages && j < nitems; ++k) next();
+            if (j < nitems) hs_fetch(nxt, loads + ld, it.y, fgroup);
+            if (!hs_fill<T>(R, s, u, cur, far, nearp, X, W, N, true)) {
+                if (lane == 0) atomicExch(err, 1);
+                hs_drain(R, s, u);
+                return;
             }
         }
         return;
