@@ -89,8 +89,9 @@ int permute_vectors(Operator& op, const void* in, void* out, int to_tree, int is
 
 // Stage records of the streamed phases.
 //  phase 1: far blocks ordered by (padded row length, first column), so the
-//    pieces of a stage mostly share one x segment; whole V^T rows fill a stage
-//    up to kStageBytes, kMaxPieces pieces and kVecFloats gathered x values.
+//    pieces of a stage mostly share one x segment; whole V^T rows of one
+//    length fill a stage up to kStageBytes, kMaxPieces pieces and kVecFloats
+//    gathered x values.
 //  phase 2: per leaf, its far chunks, then its dense chunks, as whole k-rows;
 //    a stage holds one kind only, so it is one [K][m8] array.
 static bool hs_long_row(int n, int esz_far)
@@ -134,7 +135,8 @@ static int hs_prepare(Operator& op, const std::vector<int64_t>& w_base, const st
             for (int q = 0; q < cur.np; ++q)
                 if (cur.p[q].vlen > 0 && cur.p[q].vsrc == fb.col0 && cur.p[q].valid == fb.n) vo = cur.p[q].vo;
             const int fit = (hs::kStageBytes - used) / rowb;
-            if (fit == 0 || cur.np == hs::kMaxPieces || (vo < 0 && vtot + n8 > hs::kVecFloats)) {
+            if (fit == 0 || cur.np == hs::kMaxPieces || (vo < 0 && vtot + n8 > hs::kVecFloats) ||
+                (cur.np > 0 && cur.p[0].n8 != n8)) {   // a stage's rows have one length
                 flush(l1, false);
                 continue;
             }

@@ -267,70 +267,86 @@ __global__ void __launch_bounds__(hs::kThreads) hmv_s1(const HsLoad* __restrict_
         const int f = (int)(j % F);
         const unsigned char* st = R.stage + (size_t)s * hs::kStageBytes;
         const float* sv = R.vec + s * hs::kVecFloats;
+        // The stage is one [Rt][n8] row matrix (its pieces are whole rows of
+        // one length, back to back).  Lane p holds piece p: its first row
+        // (prefix sum of the row counts), x offset, w index and rank.
         const int np = R.meta[s].np;
-        // Work units are (piece, row batch) pairs numbered through the stage;
-        // warp w takes units w, w + 8, ...  Each warp walks the piece list
-        // forward once, so a piece's set-up is paid only by warps with a
-        // unit in it, and a stage of few long rows still spreads over all
-        // warps.
-        int p = -1, ubase = 0, nb = 0;
-        int n8 = 0, rows = 0, r = 0, wv = 0, nq = 0, lg = 3;
-        const T* V = nullptr;
-        const float* xs = nullptr;
-        for (int u = warp;; u += hs::kConsumerWarps) {
-            while (u >= ubase + nb) {
-                ubase += nb;
-                if (++p >= np) break;
-                const HsPiece& pm = R.meta[s].p[p];
-                n8 = pm.n8;
-                rows = pm.rows;
-                r = pm.r;
-                wv = pm.wv;
-                V = reinterpret_cast<const T*>(st + pm.soff);
-                xs = sv + pm.vo;
-                // lanes per row: about four 16-byte quads each, and at least 8
-                // so that the lanes of a row cover all 32 banks (rows are
-                // 32-byte multiples apart)
-                nq = n8 / VW;
-                lg = nq <= 32 ? 3 : (nq <= 64 ? 4 : 5);
-                nb = (rows + (32 >> lg) - 1) >> (5 - lg);
+        int rows = 0, vo = 0, wv = 0, r = 0;
+        if (lane < np) {
+            const HsPiece& pm = R.meta[s].p[lane];
+            rows = pm.rows;
+            vo = pm.vo;
+            wv = pm.wv;
+            r = pm.r;
+        }
+        int rend = rows;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, rend, o);
+            if (lane >= o) rend += t;
+        }
+        const int rs = rend - rows;
+        const int Rt = __shfl_sync(0xffffffffu, rend, 31);
+        const int n8 = R.meta[s].p[0].n8;
+        // lanes per row: at least four 16-byte quads per lane (few shuffle
+        // levels), at least 4 lanes; when a row's lanes span less than 128
+        // bytes, the rows of a unit visit their quads in rotated order so
+        // that they fall on different banks
+        const int nq = n8 / VW;
+        const int lg = nq <= 16 ? 2 : (nq <= 32 ? 3 : (nq <= 64 ? 4 : 5));
+        const int sw = 1 << lg, sl = lane & (sw - 1), sub = lane >> lg;
+        const int per = 32 >> lg;
+        const int nql = nq >> lg;                 // quads per lane when sw divides nq
+        const bool rot = (nql << lg) == nq;
+        const T* V0 = reinterpret_cast<const T*>(st);
+        // the loop bound is warp-uniform, so every lane reaches the shuffles
+        for (int u = warp; u * per < Rt; u += hs::kConsumerWarps) {
+            const int row = u * per + sub;
+            // piece of each sub-warp's row: the last lane whose first row is <= it
+            int pp = 0;
+            for (int k = 0; k < per; ++k) {
+                const unsigned m = __ballot_sync(0xffffffffu, lane < np && rs <= u * per + k);
+                if (k == sub) pp = 31 - __clz(m);
             }
-            if (p >= np) break;
-            const int sw = 1 << lg, sl = lane & (sw - 1);
-            const int row = ((u - ubase) << (5 - lg)) + (lane >> lg);
-            const bool rok = row < rows;
+            const int pvo = __shfl_sync(0xffffffffu, vo, pp), pwv = __shfl_sync(0xffffffffu, wv, pp);
+            const int pr = __shfl_sync(0xffffffffu, r, pp), prs = __shfl_sync(0xffffffffu, rs, pp);
+            const bool rok = row < Rt;
             float acc = 0.f, acc2 = 0.f;
             if (rok) {
-                const T* vr = V + row * n8;
-                int q = sl;
-                for (; q + sw < nq; q += 2 * sw) {
-                    float v[VW], x[VW], v2[VW], x2[VW];
-                    lds16(vr + q * VW, v);
-                    lds16(vr + (q + sw) * VW, v2);
+                const T* vr = V0 + row * n8;
+                const float* xs = sv + pvo;
+                if (rot) {
+                    int t = sub % nql;
+                    for (int k = 0; k < nql; ++k) {
+                        const int q = sl + (t << lg);
+                        float v[VW], x[VW];
+                        lds16(vr + q * VW, v);
 #pragma unroll
-                    for (int e = 0; e < VW; e += 4) {
-                        lds16(xs + q * VW + e, x + e);
-                        lds16(xs + (q + sw) * VW + e, x2 + e);
+                        for (int e = 0; e < VW; e += 4) lds16(xs + q * VW + e, x + e);
+#pragma unroll
+                        for (int e = 0; e < VW; e += 2) {
+                            acc += v[e] * x[e];
+                            acc2 += v[e + 1] * x[e + 1];
+                        }
+                        t = t + 1 == nql ? 0 : t + 1;
                     }
+                } else {
+                    for (int q = sl; q < nq; q += sw) {
+                        float v[VW], x[VW];
+                        lds16(vr + q * VW, v);
 #pragma unroll
-                    for (int e = 0; e < VW; ++e) {
-                        acc += v[e] * x[e];
-                        acc2 += v2[e] * x2[e];
+                        for (int e = 0; e < VW; e += 4) lds16(xs + q * VW + e, x + e);
+#pragma unroll
+                        for (int e = 0; e < VW; e += 2) {
+                            acc += v[e] * x[e];
+                            acc2 += v[e + 1] * x[e + 1];
+                        }
                     }
-                }
-                if (q < nq) {
-                    float v[VW], x[VW];
-                    lds16(vr + q * VW, v);
-#pragma unroll
-                    for (int e = 0; e < VW; e += 4) lds16(xs + q * VW + e, x + e);
-#pragma unroll
-                    for (int e = 0; e < VW; ++e) acc += v[e] * x[e];
                 }
                 acc += acc2;
             }
-            // p, u and lg are warp-uniform, so every lane reaches the shuffles
             for (int o = sw >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, sw);
-            if (rok && sl == 0) W[(int64_t)wv + row + (int64_t)f * r] = acc;
+            if (rok && sl == 0) W[(int64_t)pwv + (row - prs) + (int64_t)f * pr] = acc;
         }
         __syncwarp();
         if (lane == 0) bulk::arrive(R.empty(s));
