@@ -302,11 +302,16 @@ __global__ void __launch_bounds__(hs::kThreads) hmv_s1(const HsLoad* __restrict_
         // the loop bound is warp-uniform, so every lane reaches the shuffles
         for (int u = warp; u * per < Rt; u += hs::kConsumerWarps) {
             const int row = u * per + sub;
-            // piece of each sub-warp's row: the last lane whose first row is <= it
-            int pp = 0;
-            for (int k = 0; k < per; ++k) {
-                const unsigned m = __ballot_sync(0xffffffffu, lane < np && rs <= u * per + k);
-                if (k == sub) pp = 31 - __clz(m);
+            // piece of each sub-warp's row: the last lane whose first row is <= it.
+            // Usually one piece holds all rows of the unit: two ballots decide it.
+            const unsigned m0 = __ballot_sync(0xffffffffu, lane < np && rs <= u * per);
+            const unsigned m1 = __ballot_sync(0xffffffffu, lane < np && rs <= u * per + per - 1);
+            int pp = 31 - __clz(m0);
+            if (m0 != m1) {
+                for (int k = 1; k < per; ++k) {
+                    const unsigned m = __ballot_sync(0xffffffffu, lane < np && rs <= u * per + k);
+                    if (k == sub) pp = 31 - __clz(m);
+                }
             }
             const int pvo = __shfl_sync(0xffffffffu, vo, pp), pwv = __shfl_sync(0xffffffffu, wv, pp);
             const int pr = __shfl_sync(0xffffffffu, r, pp), prs = __shfl_sync(0xffffffffu, rs, pp);
@@ -315,7 +320,22 @@ __global__ void __launch_bounds__(hs::kThreads) hmv_s1(const HsLoad* __restrict_
             if (rok) {
                 const T* vr = V0 + row * n8;
                 const float* xs = sv + pvo;
-                if (rot) {
+                if (nql == 4) {
+                    // four quads per lane, visited from quad (sub mod 4)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int q = sl + (((sub + k) & 3) << lg);
+                        float v[VW], x[VW];
+                        lds16(vr + q * VW, v);
+#pragma unroll
+                        for (int e = 0; e < VW; e += 4) lds16(xs + q * VW + e, x + e);
+#pragma unroll
+                        for (int e = 0; e < VW; e += 2) {
+                            acc += v[e] * x[e];
+                            acc2 += v[e + 1] * x[e + 1];
+                        }
+                    }
+                } else if (rot) {
                     int t = sub % nql;
                     for (int k = 0; k < nql; ++k) {
                         const int q = sl + (t << lg);
