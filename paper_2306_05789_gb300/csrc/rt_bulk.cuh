@@ -50,16 +50,20 @@ __device__ __forceinline__ void copy(uint32_t dst, const void* src, uint32_t byt
 }
 
 // wait for the completion of the phase with the given parity; false when the
-// clock budget runs out first
+// clock budget runs out first.  Each probe may suspend the thread for up to
+// kSuspendNs (it resumes as soon as the phase completes), so waiting warps
+// leave the issue slots to the working ones.
+constexpr uint32_t kSuspendNs = 20000;
+
 __device__ __forceinline__ bool wait(uint32_t bar, uint32_t parity)
 {
     const long long t0 = clock64();
     for (;;) {
         uint32_t done = 0;
         asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(bar), "r"(parity)
+            : "r"(bar), "r"(parity), "r"(kSuspendNs)
             : "memory");
         if (done) return true;
         if (clock64() - t0 > kWaitCycles) return false;
