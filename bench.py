@@ -497,7 +497,7 @@ def run_gpu(args):
         "roofline": {"bound": "hbm",
                      "kernel": ("dense_apply" if dense else
                                 ("tc_phase1+tc_phase2 (tcgen05, rt_apply)" if info["apply_tensor_cores"]
-                                 else "hmv_s1+hmv_s2 (streamed, rt_apply)")),
+                                 else "hmv_s1+hmv_s2 streamed (+hmv_phase1 for rows over 1024 columns), rt_apply")),
                      "achieved": apply_gbs, "peak": hbm, "unit": "GB/s", "frac": apply_gbs / hbm,
                      "traffic": measured_traffic(args.workload, kind), "peak_kind": peak_kind,
                      "algorithmic_bytes": info["apply_bytes"], "ms": t_apply * 1e3},

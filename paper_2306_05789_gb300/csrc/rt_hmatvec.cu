@@ -448,6 +448,21 @@ static int launch_hmv(Operator& op, const float* x, float* w, float* y, cudaStre
     return RT_OK;
 }
 
+int apply_check_error(Operator& op, cudaStream_t s, std::string& err)
+{
+    int rc = tc_check_error(op, s, err);
+    if (rc || !op.apply_err) return rc;
+    int h = 0;
+    RT_CUDA_TRY(cudaMemcpyAsync(&h, op.apply_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) {
+        cudaMemsetAsync(op.apply_err, 0, sizeof(int), s);
+        err = "streamed H-matvec: an mbarrier wait timed out";
+        return RT_ETIMEOUT;
+    }
+    return RT_OK;
+}
+
 static int launch_dense(Operator& op, const void* X, void* Y, cudaStream_t s, std::string& err)
 {
     const int N = op.N, F = op.F;

@@ -271,7 +271,8 @@ int apply_noalloc(Operator& op, const void* X, void* Y, cudaStream_t s, std::str
 size_t apply_noalloc_limit();
 int tc_prepare(Operator& op, std::string& err);
 int tc_apply(Operator& op, const float* X, float* Y, cudaStream_t s, std::string& err);
-// RT_ETIMEOUT (and clears the flags) if a bounded wait of an apply kernel gave up
+int tc_check_error(Operator& op, cudaStream_t s, std::string& err);
+// RT_ETIMEOUT if a bounded wait of an apply kernel (tensor-core or streamed) gave up
 int apply_check_error(Operator& op, cudaStream_t s, std::string& err);
 int solve_fixed_point(Operator& op, const rt_solve_opts& o, void* J, double* T, rt_solve_stats& st,
                       cudaStream_t s, std::string& err);

@@ -823,20 +823,15 @@ int tc_apply(Operator& op, const float* X, float* Y, cudaStream_t s, std::string
     return tc_launch<__half>(op, X, Y, s, err);
 }
 
-int apply_check_error(Operator& op, cudaStream_t s, std::string& err)
+int tc_check_error(Operator& op, cudaStream_t s, std::string& err)
 {
-    int* flags[2] = {op.tc_enabled ? op.tc_err : nullptr, op.apply_err};
-    for (int* fl : flags) {
-        if (!fl) continue;
-        int h = 0;
-        RT_CUDA_TRY(cudaMemcpyAsync(&h, fl, sizeof(int), cudaMemcpyDeviceToHost, s));
-        RT_CUDA_TRY(cudaStreamSynchronize(s));
-        if (h) {
-            cudaMemsetAsync(fl, 0, sizeof(int), s);
-            err = fl == op.apply_err ? "streamed H-matvec: an mbarrier wait timed out"
-                                     : "tensor-core apply: an mbarrier wait timed out";
-            return RT_ETIMEOUT;
-        }
+    if (!op.tc_enabled) return RT_OK;
+    int h = 0;
+    RT_CUDA_TRY(cudaMemcpyAsync(&h, op.tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) {
+        err = "tensor-core apply: an mbarrier wait timed out";
+        return RT_ETIMEOUT;
     }
     return RT_OK;
 }
