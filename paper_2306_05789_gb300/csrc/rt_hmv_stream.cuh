@@ -320,8 +320,8 @@ __global__ void __launch_bounds__(hs::kThreads) hmv_s1(const HsLoad* __restrict_
             if (rok) {
                 const T* vr = V0 + row * n8;
                 const float* xs = sv + pvo;
-                if (nql == 4) {
-                    // four quads per lane, visited from quad (sub mod 4)
+                if (rot && nql == 4) {
+                    // exactly four quads per lane, visited from quad (sub mod 4)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const int q = sl + (((sub + k) & 3) << lg);

@@ -340,6 +340,32 @@ def test_far_rows_longer_than_a_stage_match_the_oracle():
         op.free()
 
 
+def test_apply_with_uneven_cluster_sizes_matches_the_oracle():
+    """26^3 = 17576 vertices bisect into clusters of uneven sizes (549, 550,
+    1098, ...), so far blocks have row lengths that are not powers of two and
+    that 32 lanes do not divide (138 quads of 4 columns for 549 columns).
+    Sampled rows of the apply against dense FP64 rows (Section 2.1)."""
+    p = W.cube_problem(26, W.sinprod_kappa(0.5), W.midpoint_freqs(2, albedo=0.3, c_offset=0.5), R0=0.5)
+    _, blocks, _ = rt.rt_plan(p.xyz, 64, 2.0)
+    adm = blocks[blocks[:, 4] == 1]
+    n8 = (adm[:, 3] + 7) // 8 * 8
+    assert ((n8 > 512) & (n8 % 128 != 0)).any()
+    rows = W.sample_rows(p.N, 10, seed=4)
+    op = rt.rt_build_operator(p, rt.hparams())
+    try:
+        X = W.rand_vectors((p.freqs.F, p.N), seed=5)
+        Xd = torch.tensor(X, dtype=torch.float32, device=DEV)
+        Y = torch.zeros_like(Xd)
+        op.apply(Xd, Y)
+        torch.cuda.synchronize()
+        R = O.G_rows(p, rows)
+        _, gidx = O.groups_of(p.freqs)
+        ref = np.stack([R[:, gidx[f], :] @ X[f] for f in range(p.freqs.F)])
+        assert rel_l2(Y.cpu().numpy()[:, rows], ref) < 1e-4
+    finally:
+        op.free()
+
+
 # ---------------------------------------------------------------------------
 # benchmark size: 32^3, 16 frequencies (sampled rows)
 # ---------------------------------------------------------------------------
