@@ -200,7 +200,11 @@ int rt_operator_info(const rt_operator* op, rt_info* info);
 
 /* Y = Gbar X per frequency (Y_nu = G_{g(nu)} X_nu), X and Y device arrays
  * [F][N] in the caller's vertex order; element type double for a dense FP64
- * operator, float otherwise.  X and Y must not overlap. */
+ * operator, float otherwise.  X and Y must not overlap.  Asynchronous on
+ * `stream`: it returns once the kernels are queued.  The H-matrix kernels'
+ * device-side waits are bounded (about 2 s); a wait that gives up leaves Y
+ * unspecified and sets a flag that the operator's next rt_solve_fixed_point
+ * returns as RT_ETIMEOUT. */
 int rt_apply(rt_operator* op, const void* X, void* Y, void* stream);
 
 /* Y = Gbar X exactly as rt_apply computes it, for callers that must not
@@ -238,7 +242,9 @@ int rt_eval_entries(rt_operator* op, int group, int64_t count, const int32_t* ro
  * B_nu(T), J <- Sbar^E + Gbar S, T <- Planck balance per vertex (FP64
  * Newton, or (J/sigma)^(1/4) for grey).  J_dev [F][N] (vector element type),
  * T_dev [N] doubles; both receive the final iterate.  Returns RT_ENOCONV
- * (with J, T and stats filled) if tol is not reached within max_iter. */
+ * (with J, T and stats filled) if tol is not reached within max_iter, and
+ * RT_ETIMEOUT if a bounded device-side wait of an apply (this solve's or an
+ * earlier rt_apply's) gave up. */
 int rt_solve_fixed_point(rt_operator* op, const rt_solve_opts* opts, void* J_dev, double* T_dev,
                          rt_solve_stats* stats, void* stream);
 
