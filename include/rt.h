@@ -98,14 +98,29 @@ typedef struct {
 } rt_wall;
 
 /* Frequency grid: F channels with quadrature weight w, absorption scale c
- * (kappa_nu = c * kappa(x)) and albedo a.  Channels with equal c share one
- * operator group (Remark of Section 2.1: one matrix per distinct kappa_nu). */
+ * (kappa_nu = c * kappa(x)) and albedo a.  Operators are built per group of
+ * channels (Remark of Section 2.1: one matrix pair per value of kappa_nu, and
+ * fewer than ten values usually represent kappa_nu piecewise constantly;
+ * Section 4, Test 2: 583 frequencies, 8 values of kappa_nu in the
+ * exponentials).
+ *   - group == NULL and rt_hparams.kappa_bins == 0: channels with equal c share
+ *     one group (exact, no approximation).
+ *   - group == NULL and kappa_bins = K > 0: the channels are binned by c into K
+ *     equal-width intervals of [min c, max c] (empty intervals dropped).
+ *   - group != NULL: group[f] in [0, G) is the caller's group of channel f;
+ *     every index in [0, G) must be used.
+ * A group's scale c_g is the midpoint (min c + max c) / 2 of its channels'
+ * scales.  The optical depths in the exponentials use c_g; the kappa_nu(y)
+ * factor in front keeps the channel's own c, so channel f applies
+ * (c_f / c_g) G_g (G_g built with c_g in both places; the factor is 1
+ * without binning).  The temperature balance uses every channel's own c. */
 typedef struct {
     int F;
     const double* nu;
     const double* w;
     const double* c;
     const double* albedo;
+    const int32_t* group;   /* [F] or NULL */
 } rt_freqs;
 
 /* One problem instance.  Emitting boundary: n_emit triangles (vertex ids of
@@ -146,6 +161,8 @@ typedef struct {
     int64_t wave_bytes; /* ACA runs over consecutive waves of admissible blocks whose FP32 term
                            scratch (estimated at 24 terms per block) stays below this many bytes;
                            each wave is packed and its scratch freed before the next (0 = 8 GiB) */
+    int kappa_bins;  /* 0: one operator group per distinct c; K > 0: bin the channels by c into at
+                        most K groups (see rt_freqs); ignored when the problem gives a group map */
 } rt_hparams;
 
 typedef struct rt_operator rt_operator;
@@ -160,7 +177,9 @@ typedef struct {
     int64_t rank_min, rank_max, rank_sum;
     int64_t aca_steps;           /* ACA sweeps until every block finished */
     int64_t entries_evaluated;   /* kernel entries evaluated during assembly (all groups count once) */
-    int64_t apply_bytes;         /* algorithmic bytes moved by one rt_apply (all groups, see DESIGN) */
+    int64_t apply_bytes;         /* algorithmic bytes moved by one rt_apply (all groups): stored operator
+                                    entries x element size (once per frequency, or once in all for the
+                                    tcgen05 apply) + X read + Y written */
     int64_t apply_flops;
     int64_t device_bytes;        /* device memory held by the operator */
     double ms_tree, ms_near, ms_aca, ms_pack, ms_source; /* assembly phase times */
@@ -198,34 +217,53 @@ int rt_build_operator(const rt_problem* prob, const rt_hparams* hp, void* stream
 /* Statistics of a built operator. */
 int rt_operator_info(const rt_operator* op, rt_info* info);
 
-/* Y = Gbar X per frequency (Y_nu = G_{g(nu)} X_nu), X and Y device arrays
- * [F][N] in the caller's vertex order; element type double for a dense FP64
- * operator, float otherwise.  X and Y must not overlap.  Asynchronous on
- * `stream`: it returns once the kernels are queued.  The H-matrix kernels'
- * device-side waits are bounded (about 2 s); a wait that gives up leaves Y
- * unspecified and sets a flag that the operator's next rt_solve_fixed_point
- * returns as RT_ETIMEOUT. */
+/* Y = Gbar X per frequency, Y_nu = G_{g(nu)} X_nu: the matrix-vector product
+ * that is the whole per-iteration cost of the fixed point (abstract; the
+ * discrete operator J_i = Sbar^E_i + sum_j G^{ij} S_j of Section 2, applied in
+ * its compressed form of Section 2.1: dense near blocks plus U V^T far blocks).
+ * X and Y are device arrays [F][N] in the caller's vertex order; element type
+ * double for a dense FP64 operator, float otherwise.  X and Y must not
+ * overlap.  Asynchronous on `stream`: it returns once the kernels are queued.
+ * The H-matrix kernels' device-side waits are bounded (about 2 s); a wait
+ * that gives up leaves Y unspecified and sets a flag that the operator's next
+ * rt_solve_fixed_point returns as RT_ETIMEOUT.  Errors: RT_EINVAL (null
+ * operator or vectors), RT_ECUDA (a launch failed). */
 int rt_apply(rt_operator* op, const void* X, void* Y, void* stream);
 
-/* Y = Gbar X exactly as rt_apply computes it, for callers that must not
- * allocate device memory while they run -- for example code that is being
- * recorded into another component's CUDA graph, where an allocation would
- * break or serialise the capture, or a host loop with a fixed time budget in
- * an application whose device memory is handed out by its own allocator.
+/* Y_j = G_group X_j for nrhs vectors of one operator group (Section 2.1:
+ * one matrix per value of kappa_nu), without the per-channel factor
+ * c_f / c_g of a binned grid.  X_j = X + j * ldx and Y_j = Y + j * ldy
+ * (j < nrhs, ldx, ldy >= N) are device vectors of N elements in the caller's
+ * vertex order, element type as in rt_apply; X and Y must not overlap.  The
+ * right-hand sides run in chunks of F (the operator's channel count) through
+ * rt_apply's kernels and scratch, so calls on one operator must be ordered.
+ * Asynchronous on `stream`.  RT_EINVAL for a group outside [0, G), nrhs < 0,
+ * ld < N or null vectors; RT_ECUDA if a launch fails. */
+int rt_apply_group(rt_operator* op, int group, const void* X, int64_t ldx, int nrhs, void* Y, int64_t ldy,
+                   void* stream);
+
+/* Y = Gbar X with the same kernels and arithmetic as rt_apply (its tcgen05
+ * pair where rt_apply takes it, its CUDA-core phases otherwise), for callers
+ * that cannot allocate device memory while they run: for example an
+ * application whose device memory is entirely handed out by its own pool
+ * allocator, or a host loop with a fixed time budget that cannot afford the
+ * synchronisation a cudaMalloc or cudaFree may imply.
  * (The paper has no counterpart: this is a deployment convenience.)
  * The scratch rt_apply keeps in the operator -- X and Y in the internal vertex
- * order and one FP32 value per (far-block rank term, frequency) -- is taken
- * from a static 8 MiB device array instead (2 * 4 F N bytes + 4 F sum(rank)
- * bytes, each rounded up to 256, must fit; larger operators get RT_EINVAL).
+ * order and, on CUDA cores, one FP32 value per (far-block rank term,
+ * frequency) -- is taken from a static 8 MiB device array instead
+ * (2 * 4 F N bytes, plus 4 F sum(rank) bytes on CUDA cores, each rounded up to
+ * 256, must fit; larger operators get RT_EINVAL).  The tcgen05 path's other
+ * buffers belong to the operator and were allocated when it was built.
  * The array exists once per GPU that loads the library and stays allocated
  * until the process exits.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) and caches it; make that first call
- * before any stream capture.  All calls share the array: calls whose work
- * overlaps on the GPU (different streams or threads without ordering) race on
- * it.  Nothing needs clearing between calls (each region is overwritten before
- * it is read).  The current device must be the operator's device.  Dense
- * operators need no scratch and are applied directly.  Allocates nothing:
- * no cudaMalloc, cudaFree or allocating library call. */
+ * device address (cudaGetSymbolAddress) and caches it.  All calls share the
+ * array: calls whose work overlaps on the GPU (different streams or threads
+ * without ordering) race on it.  Nothing needs clearing between calls (each
+ * region is overwritten before it is read).  The current device must be the
+ * operator's device.  Dense operators need no scratch and are applied
+ * directly.  Allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * call. */
 int rt_apply_noalloc(rt_operator* op, const void* X, void* Y, void* stream);
 
 /* Sbar^E_nu (Proposition 2 / Example of Section 1.2, discretised as in
@@ -237,6 +275,14 @@ int rt_source(rt_operator* op, void* out, void* stream);
  * of vertex ids (caller order), out is a device double array [count]. */
 int rt_eval_entries(rt_operator* op, int group, int64_t count, const int32_t* rows, const int32_t* cols,
                     double* out, void* stream);
+
+/* Diagnostic (no paper counterpart): the library's FP32 sin(2 pi x), used by
+ * the sin-product kappa on the FP32 paths, for n device values x: lib_out[i]
+ * receives it and ref_out[i] CUDA's sinpif(2 x[i]) for comparison.  All three
+ * are caller-owned device float arrays of n elements.  Asynchronous on
+ * `stream`.  RT_EINVAL for n < 0 or null arrays, RT_ECUDA if the launch
+ * fails. */
+int rt_eval_sin2pi(const float* x, float* lib_out, float* ref_out, int64_t n, void* stream);
 
 /* Fixed point of Section 1.3 (eq. (algo)) on the device: S = a J + (1-a)
  * B_nu(T), J <- Sbar^E + Gbar S, T <- Planck balance per vertex (FP64
@@ -291,6 +337,16 @@ int rt_batch_apply(rt_batch* b, const float* X, float* Y, void* stream);
  * instance did not reach tol; RT_ETIMEOUT if a bounded device wait gave up. */
 int rt_solve_batch(rt_batch* b, const rt_solve_opts* opts, float* J_dev, double* T_dev, int32_t* iters,
                    rt_solve_stats* stats, void* stream);
+
+/* Diagnostic (no paper counterpart): the clock budget, in SM clock cycles, of
+ * the wait with which a phase-2 item of the batch apply waits for its
+ * instance's phase-1 items (0 restores the default of about 1 s).  With
+ * unreachable != 0 every such wait targets one more completed phase-1 item
+ * than exist, so every wait runs out: the apply then finishes with Y
+ * unspecified and rt_solve_batch returns RT_ETIMEOUT.  This drives the
+ * timeout path without faulting or hanging the GPU.  RT_EINVAL for a null
+ * batch or a negative budget. */
+int rt_batch_set_wait(rt_batch* b, int64_t wait_cycles, int unreachable);
 
 void rt_batch_free(rt_batch* b);
 

@@ -12,7 +12,7 @@ Layers:
 * this module: the Planck function, the per-vertex temperature solve and the
   fixed-point iteration of Section 1.3 (equation (algo)), written with numpy.
 
-Readings of the paper taken here (each is listed in the design doc):
+Readings of the paper taken here:
 
 * grey case (Section 3, eq. (grey)): B(T) = sigma T^4, sigma = pi^4/15, and the
   temperature update is kappa sigma T^4 = kappa J, i.e. T = (J/sigma)^(1/4).
@@ -160,9 +160,33 @@ def kernel_point(kappa, wall, x, y, c, ngauss: int = 16):
     return d, r
 
 
-def groups_of(freqs):
-    """Distinct kappa scales c (exact equality) and the group index of each frequency."""
+def groups_of(freqs, bins: int = 0):
+    """Operator groups of the frequency channels (Remark of Section 2.1: one matrix per value
+    of kappa_nu, a few values representing kappa_nu piecewise constantly; Section 4, Test 2).
+
+    Returns (c_g per group, group index of each channel).
+      * freqs.group given: the caller's map; c_g = (min + max)/2 of the member scales.
+      * bins = K > 0: channels binned by c into K equal-width intervals of [min c, max c]
+        (empty intervals dropped, groups in interval order); c_g as above.
+      * otherwise: one group per distinct c (exact equality), in order of first appearance.
+    """
     c = np.asarray(freqs.c, dtype=np.float64)
+    grp = getattr(freqs, "group", None)
+    if grp is not None or bins > 0:
+        if grp is not None:
+            gidx = np.asarray(grp, dtype=np.int64).copy()
+        else:
+            cmin, cmax = c.min(), c.max()
+            if cmax > cmin:
+                b = np.floor((c - cmin) / (cmax - cmin) * bins).astype(np.int64)
+            else:
+                b = np.zeros(c.shape[0], dtype=np.int64)
+            b = np.clip(b, 0, bins - 1)
+            used = np.unique(b)
+            gidx = np.searchsorted(used, b)
+        G = int(gidx.max()) + 1
+        cg = np.array([0.5 * (c[gidx == g].min() + c[gidx == g].max()) for g in range(G)])
+        return cg, gidx
     uniq = []
     gidx = np.zeros(c.shape[0], dtype=np.int64)
     for f, cv in enumerate(c):
@@ -174,6 +198,12 @@ def groups_of(freqs):
             gidx[f] = len(uniq)
             uniq.append(cv)
     return np.array(uniq, dtype=np.float64), gidx
+
+
+def channel_scale(freqs, cg, gidx):
+    """c_f / c_{g(f)}: channel f applies (c_f / c_g) G_g -- the kappa_nu(y) factor in front keeps
+    the channel's own scale while the optical depths in the exponentials use the group's."""
+    return np.asarray(freqs.c, dtype=np.float64) / np.asarray(cg)[np.asarray(gidx)]
 
 
 def G_rows(prob, rows, c=None, ngauss: int = 16, refine: int = 0, R0=None, moments: bool = False):
@@ -344,9 +374,10 @@ def temperature_bisection(J, freqs, iters: int = 200):
 class DenseOperator:
     """All rows of every group's G plus the emitter source, FP64, dense."""
 
-    def __init__(self, prob, ngauss: int = 16, refine: int = 0):
+    def __init__(self, prob, ngauss: int = 16, refine: int = 0, bins: int = 0):
         self.prob = prob
-        self.c, self.gidx = groups_of(prob.freqs)
+        self.c, self.gidx = groups_of(prob.freqs, bins)
+        self.scale = channel_scale(prob.freqs, self.c, self.gidx)
         N = prob.N
         rows = np.arange(N, dtype=np.int32)
         R = G_rows(prob, rows, self.c, ngauss=ngauss, refine=refine)  # [N, G, N]
@@ -356,9 +387,9 @@ class DenseOperator:
         self.SE = Q[:, None] * shat[:, self.gidx].T  # [F, N]
 
     def apply(self, X):
-        """Y_nu = G_{g(nu)} X_nu for X [F, N]."""
+        """Y_nu = (c_nu / c_g) G_{g(nu)} X_nu for X [F, N] (the factor is 1 without binning)."""
         X = np.asarray(X, dtype=np.float64)
-        return np.stack([self.G[self.gidx[f]] @ X[f] for f in range(X.shape[0])])
+        return np.stack([self.scale[f] * (self.G[self.gidx[f]] @ X[f]) for f in range(X.shape[0])])
 
 
 def source_update(prob, J, T):
@@ -404,14 +435,15 @@ def fixed_point(prob, op: DenseOperator, T0=0.0, J0=None, tol: float = 1e-10, ma
     return out
 
 
-def one_step_residual(prob, rows, J, T, ngauss: int = 16):
+def one_step_residual(prob, rows, J, T, ngauss: int = 16, bins: int = 0):
     """F(J,T)_i = Sbar^E_i + (G S(J,T))_i - J_i at the sampled vertices `rows` (FP64 rows on the fly)."""
-    c, gidx = groups_of(prob.freqs)
+    c, gidx = groups_of(prob.freqs, bins)
+    sc = channel_scale(prob.freqs, c, gidx)
     R = G_rows(prob, rows, c, ngauss=ngauss)  # [r, G, N]
     S = source_update(prob, np.asarray(J, dtype=np.float64), np.asarray(T, dtype=np.float64))
     shat = source_geometric(prob, rows, c, ngauss=ngauss)  # [r, G]
     Q = emitter_intensity(prob)
     out = np.zeros((prob.freqs.F, len(rows)))
     for f in range(prob.freqs.F):
-        out[f] = Q[f] * shat[:, gidx[f]] + R[:, gidx[f], :] @ S[f] - np.asarray(J, dtype=np.float64)[f, rows]
+        out[f] = Q[f] * shat[:, gidx[f]] + sc[f] * (R[:, gidx[f], :] @ S[f]) - np.asarray(J, dtype=np.float64)[f, rows]
     return out

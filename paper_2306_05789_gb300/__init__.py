@@ -48,7 +48,7 @@ class RtWall(ctypes.Structure):
 
 
 class RtFreqs(ctypes.Structure):
-    _fields_ = [("F", _c_int), ("nu", _P), ("w", _P), ("c", _P), ("albedo", _P)]
+    _fields_ = [("F", _c_int), ("nu", _P), ("w", _P), ("c", _P), ("albedo", _P), ("group", _P)]
 
 
 class RtProblem(ctypes.Structure):
@@ -59,7 +59,8 @@ class RtProblem(ctypes.Structure):
 class RtHparams(ctypes.Structure):
     _fields_ = [("mode", _c_int), ("prec", _c_int), ("far_prec", _c_int), ("aca_eps", _c_dbl), ("leaf", _c_int),
                 ("eta", _c_dbl), ("gauss_pts", _c_int), ("rank_max", _c_int), ("adm", _c_int),
-                ("line_eval", _c_int), ("refine", _c_int), ("tensor_cores", _c_int), ("wave_bytes", _c_i64)]
+                ("line_eval", _c_int), ("refine", _c_int), ("tensor_cores", _c_int), ("wave_bytes", _c_i64),
+                ("kappa_bins", _c_int)]
 
 
 class RtInfo(ctypes.Structure):
@@ -122,10 +123,10 @@ class RtSolveStats(ctypes.Structure):
 
 
 # every symbol declared in include/rt.h
-EXPORTS = ("rt_build_operator", "rt_operator_info", "rt_apply", "rt_apply_noalloc", "rt_source", "rt_eval_entries",
-           "rt_solve_fixed_point", "rt_free", "rt_last_error", "rt_plan", "rt_build_batch", "rt_batch_info",
-           "rt_batch_apply", "rt_solve_batch", "rt_batch_free", "rt_batch_last_error", "rt_server_create",
-           "rt_submit", "rt_poll", "rt_server_info", "rt_server_free")
+EXPORTS = ("rt_build_operator", "rt_operator_info", "rt_apply", "rt_apply_group", "rt_apply_noalloc", "rt_source", "rt_eval_entries",
+           "rt_eval_sin2pi", "rt_solve_fixed_point", "rt_free", "rt_last_error", "rt_plan", "rt_build_batch",
+           "rt_batch_info", "rt_batch_apply", "rt_solve_batch", "rt_batch_set_wait", "rt_batch_free",
+           "rt_batch_last_error", "rt_server_create", "rt_submit", "rt_poll", "rt_server_info", "rt_server_free")
 
 _lib = None
 
@@ -143,8 +144,10 @@ def lib():
     L.rt_operator_info.argtypes = [_P, ctypes.POINTER(RtInfo)]
     L.rt_apply.argtypes = [_P, _P, _P, _P]
     L.rt_apply_noalloc.argtypes = [_P, _P, _P, _P]
+    L.rt_apply_group.argtypes = [_P, _c_int, _P, _c_i64, _c_int, _P, _c_i64, _P]
     L.rt_source.argtypes = [_P, _P, _P]
     L.rt_eval_entries.argtypes = [_P, _c_int, _c_i64, _P, _P, _P, _P]
+    L.rt_eval_sin2pi.argtypes = [_P, _P, _P, _c_i64, _P]
     L.rt_solve_fixed_point.argtypes = [_P, ctypes.POINTER(RtSolveOpts), _P, _P, ctypes.POINTER(RtSolveStats), _P]
     L.rt_free.argtypes = [_P]
     L.rt_free.restype = None
@@ -154,6 +157,7 @@ def lib():
     L.rt_batch_info.argtypes = [_P, ctypes.POINTER(RtBatchInfo), _P, _P]
     L.rt_batch_apply.argtypes = [_P, _P, _P, _P]
     L.rt_solve_batch.argtypes = [_P, ctypes.POINTER(RtSolveOpts), _P, _P, _P, ctypes.POINTER(RtSolveStats), _P]
+    L.rt_batch_set_wait.argtypes = [_P, _c_i64, _c_int]
     L.rt_batch_free.argtypes = [_P]
     L.rt_batch_free.restype = None
     L.rt_batch_last_error.restype = ctypes.c_char_p
@@ -193,11 +197,11 @@ def _stream_ptr(stream):
 
 def hparams(mode=RT_MODE_HMATRIX, prec=None, far_prec=RT_PREC_F32, aca_eps=1e-4, leaf=64, eta=2.0, gauss_pts=16,
             rank_max=0, adm=RT_ADM_GAP, line_eval=RT_LINE_CLOSED, refine=0, tensor_cores=0,
-            wave_bytes=0) -> RtHparams:
+            wave_bytes=0, kappa_bins=0) -> RtHparams:
     if prec is None:
         prec = RT_PREC_F32
     return RtHparams(mode, prec, far_prec, aca_eps, leaf, eta, gauss_pts, rank_max, adm, line_eval, refine,
-                     tensor_cores, int(wave_bytes))
+                     tensor_cores, int(wave_bytes), int(kappa_bins))
 
 
 class _ProblemArgs:
@@ -212,6 +216,8 @@ class _ProblemArgs:
         self.w = np.ascontiguousarray(fr.w, dtype=np.float64)
         self.c = np.ascontiguousarray(fr.c, dtype=np.float64)
         self.a = np.ascontiguousarray(fr.albedo, dtype=np.float64)
+        grp = getattr(fr, "group", None)
+        self.group = None if grp is None else np.ascontiguousarray(grp, dtype=np.int32)
         self.walls = None
         n_walls = 0
         if prob.wall is not None:
@@ -231,7 +237,8 @@ class _ProblemArgs:
         self.s.Q0 = float(prob.Q0)
         self.s.T_emit = float(prob.T_emit)
         self.s.grey = 1 if prob.grey else 0
-        self.s.freqs = RtFreqs(self.nu.shape[0], _ptr(self.nu), _ptr(self.w), _ptr(self.c), _ptr(self.a))
+        self.s.freqs = RtFreqs(self.nu.shape[0], _ptr(self.nu), _ptr(self.w), _ptr(self.c), _ptr(self.a),
+                               _ptr(self.group) if self.group is not None else None)
 
 
 class Operator:
@@ -251,6 +258,14 @@ class Operator:
     def apply(self, X, Y, stream=None):
         """rt_apply: Y = Gbar X, torch tensors [F, N] on the device."""
         _check(lib().rt_apply(self.h, _P(X.data_ptr()), _P(Y.data_ptr()), _stream_ptr(stream)))
+
+    def apply_group(self, group, X, Y, nrhs=None, ldx=None, ldy=None, stream=None):
+        """rt_apply_group: Y_j = G_group X_j for nrhs vectors (rows of X, Y with leading dimensions)."""
+        nrhs = X.shape[0] if nrhs is None else nrhs
+        ldx = X.stride(0) if ldx is None else ldx
+        ldy = Y.stride(0) if ldy is None else ldy
+        _check(lib().rt_apply_group(self.h, int(group), _P(X.data_ptr()), int(ldx), int(nrhs), _P(Y.data_ptr()),
+                                    int(ldy), _stream_ptr(stream)))
 
     def apply_noalloc(self, X, Y, stream=None):
         """rt_apply_noalloc: Y = Gbar X using the library's static scratch array (no allocation)."""
@@ -299,6 +314,12 @@ def rt_build_operator(prob, hp: RtHparams, stream=None) -> Operator:
     _check(lib().rt_build_operator(ctypes.byref(args.s), ctypes.byref(hp), _stream_ptr(stream), ctypes.byref(out)))
     vec64 = hp.mode == RT_MODE_DENSE and hp.prec == RT_PREC_F64
     return Operator(out, args.xyz.shape[0], args.nu.shape[0], vec64)
+
+
+def rt_eval_sin2pi(x, lib_out, ref_out, stream=None):
+    """rt_eval_sin2pi (diagnostic): the library's FP32 sin(2 pi x) and CUDA's sinpif(2x)."""
+    _check(lib().rt_eval_sin2pi(_P(x.data_ptr()), _P(lib_out.data_ptr()), _P(ref_out.data_ptr()), x.numel(),
+                                _stream_ptr(stream)))
 
 
 def rt_plan(xyz, leaf=64, eta=2.0, adm=RT_ADM_GAP):
@@ -350,6 +371,10 @@ class Batch:
         if rc != RT_OK and (raise_on_noconv or rc != RT_ENOCONV):
             _check_batch(rc)
         return iters, st.as_dict()
+
+    def set_wait(self, wait_cycles: int = 0, unreachable: bool = False):
+        """rt_batch_set_wait (diagnostic): budget of the phase-2 waits; unreachable makes them run out."""
+        _check_batch(lib().rt_batch_set_wait(self.h, int(wait_cycles), 1 if unreachable else 0))
 
     def free(self):
         if self.h:

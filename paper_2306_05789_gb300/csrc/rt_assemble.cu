@@ -1670,4 +1670,23 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
     return RT_OK;
 }
 
+// diagnostic: the library's FP32 sin(2 pi x) beside CUDA's sinpif(2x)
+__global__ void sin2pi_probe(const float* __restrict__ x, float* __restrict__ lib, float* __restrict__ ref, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        lib[i] = sin2pi(x[i]);
+        ref[i] = sinpif(2.0f * x[i]);
+    }
+}
+
+int eval_sin2pi(const float* x, float* lib, float* ref, int64_t n, cudaStream_t s, std::string& err)
+{
+    if (n <= 0) return RT_OK;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    sin2pi_probe<<<grid, 256, 0, s>>>(x, lib, ref, n);
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
 }  // namespace rt
+

@@ -39,6 +39,7 @@ struct BatchInst {
     float* W;
     const int* fgroup;
     const double* fq;     // [F][4]: nu, w c (1-a), a, group
+    const double* fscale; // [F] c_f / c_g of binned channels, or null
     const int* perm;      // tree position -> caller vertex id
     int N, F, grey, n1;
     int64_t voff;         // offset of the instance's [F][N] vectors
@@ -65,6 +66,8 @@ struct Batch {
     int64_t* d_toff = nullptr;
     int ctas = 0;
     int p1_bytes = 48 << 10, ctas_per_sm = 4;
+    long long spin_cycles = 0;   // wait budget of the phase-2 items (0: kSpinCycles)
+    int spin_extra = 0;          // diagnostic: completed phase-1 items a wait needs beyond all of them
     double tune_ms = 0.0, build_ms = 0.0;
     // solver buffers (tree order, concatenated)
     float *d_xt = nullptr, *d_yt = nullptr, *d_J = nullptr, *d_S = nullptr, *d_Y = nullptr, *d_SE = nullptr;
@@ -110,7 +113,8 @@ __global__ void __launch_bounds__(256) batch_apply_kernel(const BatchInst* __res
                                                           const BatchWork* __restrict__ works, int nworks,
                                                           const float* __restrict__ X, float* __restrict__ Y,
                                                           int* __restrict__ next, int* __restrict__ done1,
-                                                          const int* __restrict__ active, int* __restrict__ err)
+                                                          const int* __restrict__ active, int* __restrict__ err,
+                                                          long long spin_cycles, int extra)
 {
     __shared__ int s_w;
     __shared__ float4 red[256];
@@ -132,8 +136,8 @@ __global__ void __launch_bounds__(256) batch_apply_kernel(const BatchInst* __res
         } else {
             if (threadIdx.x == 0) {
                 const long long t0 = clock64();
-                while (*(volatile int*)&done1[wk.inst] < I.n1) {
-                    if (clock64() - t0 > kSpinCycles) {
+                while (*(volatile int*)&done1[wk.inst] < I.n1 + extra) {
+                    if (clock64() - t0 > spin_cycles) {
                         atomicOr(err, 1);
                         break;
                     }
@@ -148,8 +152,10 @@ __global__ void __launch_bounds__(256) batch_apply_kernel(const BatchInst* __res
 }
 
 // caller order <-> tree order for every instance of the batch
+// (scale != 0: the output of an apply, times c_f / c_g for binned channels)
 __global__ void batch_permute(const BatchInst* __restrict__ insts, const int64_t* __restrict__ voff, int n,
-                              int64_t total, const float* __restrict__ in, float* __restrict__ out, int to_tree)
+                              int64_t total, const float* __restrict__ in, float* __restrict__ out, int to_tree,
+                              int scale = 0)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int b = find_seg(voff, n, e);
@@ -158,7 +164,7 @@ __global__ void batch_permute(const BatchInst* __restrict__ insts, const int64_t
         const int64_t f = loc / I.N;
         const int t = (int)(loc - f * I.N);
         if (to_tree) out[e] = in[I.voff + f * I.N + I.perm[t]];
-        else out[I.voff + f * I.N + I.perm[t]] = in[e];
+        else out[I.voff + f * I.N + I.perm[t]] = (scale && I.fscale) ? (float)(in[e] * I.fscale[f]) : in[e];
     }
 }
 
@@ -210,7 +216,8 @@ __global__ void batch_source(const BatchInst* __restrict__ insts, const int64_t*
         const double a = I.fq[4 * f + 2];
         const double t = T[I.toff + i];
         const double B = I.grey ? kSigmaB * t * t * t * t : planck_b(I.fq[4 * f], t);
-        S[e] = (float)(a * (double)J[e] + (1.0 - a) * B);
+        const double v = a * (double)J[e] + (1.0 - a) * B;
+        S[e] = (float)(I.fscale ? v * I.fscale[f] : v);
     }
 }
 
@@ -420,6 +427,7 @@ static int upload_works(Batch& B, int p1_bytes, cudaStream_t s, std::string& err
         I.W = op.d_w;
         I.fgroup = op.d_fq_group;
         I.fq = op.d_fq;
+        I.fscale = op.binned ? op.d_fscale : nullptr;
         I.perm = op.d_perm;
         I.N = op.N;
         I.F = op.F;
@@ -449,7 +457,8 @@ static int launch_apply(Batch& B, const float* X, float* Y, const int* active, c
     RT_CUDA_TRY(cudaMemsetAsync(B.d_next, 0, sizeof(int), s));
     RT_CUDA_TRY(cudaMemsetAsync(B.d_done1, 0, sizeof(int) * B.n, s));
     batch_apply_kernel<<<B.ctas, 256, 0, s>>>(B.d_inst, B.d_items, B.d_works, B.nworks, X, Y, B.d_next, B.d_done1,
-                                              active, B.d_err);
+                                              active, B.d_err, B.spin_cycles > 0 ? B.spin_cycles : kSpinCycles,
+                                              B.spin_extra);
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
 }
@@ -670,7 +679,7 @@ int rt_batch_apply(rt_batch* h, const float* X, float* Y, void* stream)
     rt::batch_permute<<<grid, 256, 0, s>>>(B.d_inst, B.d_voff, B.n, B.total_vec, X, B.d_xt, 1);
     int rc = rt::launch_apply(B, B.d_xt, B.d_yt, nullptr, s, err);
     if (rc) return bfail(rc, err);
-    rt::batch_permute<<<grid, 256, 0, s>>>(B.d_inst, B.d_voff, B.n, B.total_vec, B.d_yt, Y, 0);
+    rt::batch_permute<<<grid, 256, 0, s>>>(B.d_inst, B.d_voff, B.n, B.total_vec, B.d_yt, Y, 0, 1);
     if (cudaGetLastError() != cudaSuccess) return bfail(RT_ECUDA, "batch permute launch failed");
     return RT_OK;
 }
@@ -770,6 +779,14 @@ int rt_solve_batch(rt_batch* h, const rt_solve_opts* o, float* J, double* T, int
         return bfail(RT_ETIMEOUT, "a bounded device wait gave up or a Newton solve failed");
     }
     if (nactive > 0) return bfail(RT_ENOCONV, "some instances did not reach tol within max_iter");
+    return RT_OK;
+}
+
+int rt_batch_set_wait(rt_batch* h, int64_t wait_cycles, int unreachable)
+{
+    if (!h || wait_cycles < 0) return bfail(RT_EINVAL, "null batch or negative wait budget");
+    h->b.spin_cycles = (long long)wait_cycles;
+    h->b.spin_extra = unreachable ? 1 : 0;
     return RT_OK;
 }
 

@@ -77,6 +77,7 @@ int validate(const rt_problem* P, const rt_hparams* H)
         if (H->adm != RT_ADM_GAP && H->adm != RT_ADM_CENTER) return fail(RT_EINVAL, "adm must be RT_ADM_GAP or RT_ADM_CENTER");
         if (H->wave_bytes < 0) return fail(RT_EINVAL, "wave_bytes must be >= 0");
     }
+    if (H->kappa_bins < 0 || H->kappa_bins > rt::kMaxGroups) return fail(RT_EINVAL, "kappa_bins must be in [0, 64]");
     if (H->gauss_pts < 1 || H->gauss_pts > rt::kMaxGauss) return fail(RT_EINVAL, "gauss_pts must be in [1, 32]");
     if (H->line_eval != RT_LINE_CLOSED && H->line_eval != RT_LINE_NODES) return fail(RT_EINVAL, "line_eval");
     if (M.n_vert * (int64_t)M.n_vert * Fq.F > ((int64_t)1 << 40) && H->mode == RT_MODE_DENSE)
@@ -90,6 +91,91 @@ int upload(rt::Operator& op, T** dst, const std::vector<T>& src, std::string& er
     int rc = rt::dev_alloc(op, dst, src.size(), err);
     if (rc) return rc;
     return rt::upload_async(op, *dst, src.data(), src.size(), err);
+}
+
+// Operator groups of the frequency channels (Remark of Section 2.1): exact
+// equality of c, K equal-width bins of [min c, max c], or the caller's map.
+// A group's scale is the midpoint of its channels' scales; channel f applies
+// (c_f / c_g) G_g.
+int group_channels(rt::Operator& op, const rt_freqs& Fq, int bins, std::string& err)
+{
+    using namespace rt;
+    const int F = Fq.F;
+    op.fgroup.assign(F, 0);
+    op.gc.clear();
+    if (Fq.group) {
+        int G = 0;
+        for (int f = 0; f < F; ++f) {
+            if (Fq.group[f] < 0 || Fq.group[f] >= kMaxGroups) {
+                err = "group map entries must lie in [0, 64)";
+                return RT_EINVAL;
+            }
+            G = std::max(G, Fq.group[f] + 1);
+            op.fgroup[f] = Fq.group[f];
+        }
+        std::vector<int> used(G, 0);
+        for (int f = 0; f < F; ++f) used[op.fgroup[f]] = 1;
+        for (int g = 0; g < G; ++g)
+            if (!used[g]) {
+                err = "group map leaves group " + std::to_string(g) + " empty";
+                return RT_EINVAL;
+            }
+        std::vector<double> lo(G, 1e300), hi(G, -1e300);
+        for (int f = 0; f < F; ++f) {
+            lo[op.fgroup[f]] = std::min(lo[op.fgroup[f]], Fq.c[f]);
+            hi[op.fgroup[f]] = std::max(hi[op.fgroup[f]], Fq.c[f]);
+        }
+        for (int g = 0; g < G; ++g) op.gc.push_back(lo[g] == hi[g] ? lo[g] : 0.5 * (lo[g] + hi[g]));
+    } else if (bins > 0) {
+        double cmin = Fq.c[0], cmax = Fq.c[0];
+        for (int f = 1; f < F; ++f) {
+            cmin = std::min(cmin, Fq.c[f]);
+            cmax = std::max(cmax, Fq.c[f]);
+        }
+        std::vector<int> bin(F);
+        std::vector<double> lo(bins, 1e300), hi(bins, -1e300);
+        for (int f = 0; f < F; ++f) {
+            int b = cmax > cmin ? (int)std::floor((Fq.c[f] - cmin) / (cmax - cmin) * bins) : 0;
+            b = std::min(std::max(b, 0), bins - 1);
+            bin[f] = b;
+            lo[b] = std::min(lo[b], Fq.c[f]);
+            hi[b] = std::max(hi[b], Fq.c[f]);
+        }
+        std::vector<int> gid(bins, -1);
+        for (int b = 0; b < bins; ++b)
+            if (lo[b] <= hi[b]) {
+                gid[b] = (int)op.gc.size();
+                op.gc.push_back(lo[b] == hi[b] ? lo[b] : 0.5 * (lo[b] + hi[b]));
+            }
+        if ((int)op.gc.size() > kMaxGroups) {
+            err = "more than 64 kappa groups";
+            return RT_EINVAL;
+        }
+        for (int f = 0; f < F; ++f) op.fgroup[f] = gid[bin[f]];
+    } else {
+        for (int f = 0; f < F; ++f) {
+            int g = -1;
+            for (int k = 0; k < (int)op.gc.size(); ++k)
+                if (op.gc[k] == Fq.c[f]) g = k;
+            if (g < 0) {
+                if ((int)op.gc.size() >= kMaxGroups) {
+                    err = "more than 64 distinct kappa scales c";
+                    return RT_EINVAL;
+                }
+                g = (int)op.gc.size();
+                op.gc.push_back(Fq.c[f]);
+            }
+            op.fgroup[f] = g;
+        }
+    }
+    op.G = (int)op.gc.size();
+    op.fscale.assign(F, 1.0);
+    op.binned = 0;
+    for (int f = 0; f < F; ++f) {
+        op.fscale[f] = Fq.c[f] / op.gc[op.fgroup[f]];
+        if (op.fscale[f] != 1.0) op.binned = 1;
+    }
+    return RT_OK;
 }
 
 int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream_t s, std::string& err,
@@ -123,22 +209,7 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
     op.w.assign(Fq.w, Fq.w + Fq.F);
     op.c.assign(Fq.c, Fq.c + Fq.F);
     op.albedo.assign(Fq.albedo, Fq.albedo + Fq.F);
-    op.fgroup.assign(Fq.F, 0);
-    for (int f = 0; f < Fq.F; ++f) {
-        int g = -1;
-        for (int k = 0; k < (int)op.gc.size(); ++k)
-            if (op.gc[k] == Fq.c[f]) g = k;
-        if (g < 0) {
-            if ((int)op.gc.size() >= kMaxGroups) {
-                err = "more than 64 distinct kappa scales c";
-                return RT_EINVAL;
-            }
-            g = (int)op.gc.size();
-            op.gc.push_back(Fq.c[f]);
-        }
-        op.fgroup[f] = g;
-    }
-    op.G = (int)op.gc.size();
+    if ((rc = group_channels(op, Fq, H->kappa_bins, err))) return rc;
     op.Q.assign(Fq.F, 0.0);
     for (int f = 0; f < Fq.F; ++f)
         op.Q[f] = P->grey ? P->Q0 * 6.493939402266829 * std::pow(P->T_emit, 4.0) : P->Q0 * planck_host(Fq.nu[f], P->T_emit);
@@ -422,12 +493,27 @@ int rt_apply(rt_operator* h, const void* X, void* Y, void* stream)
     int rc;
     if (op.mode == RT_MODE_DENSE) {
         rc = rt::apply_tree(op, X, Y, s, err);
+        if (!rc && op.binned) rc = rt::scale_rows(op, Y, s);
     } else {
         rc = rt::permute_vectors(op, X, op.d_xt, 1, op.vec64, op.F, s);
         if (!rc) rc = rt::apply_tree(op, op.d_xt, op.d_yt, s, err);
-        if (!rc) rc = rt::permute_vectors(op, op.d_yt, Y, 0, op.vec64, op.F, s);
-        if (rc && err.empty()) err = "kernel launch failed";
+        if (!rc) rc = rt::permute_vectors(op, op.d_yt, Y, 0, op.vec64, op.F, s, op.binned ? op.d_fscale : nullptr);
     }
+    if (rc && err.empty()) err = "kernel launch failed";
+    if (rc) return fail(rc, err);
+    return RT_OK;
+}
+
+int rt_apply_group(rt_operator* h, int group, const void* X, int64_t ldx, int nrhs, void* Y, int64_t ldy,
+                   void* stream)
+{
+    if (!h || (nrhs > 0 && (!X || !Y))) return fail(RT_EINVAL, "null argument");
+    rt::Operator& op = h->op;
+    if (group < 0 || group >= op.G) return fail(RT_EINVAL, "group out of range");
+    if (nrhs < 0 || ldx < op.N || ldy < op.N) return fail(RT_EINVAL, "nrhs < 0 or leading dimension < N");
+    std::string err;
+    int rc = rt::apply_group(op, group, X, ldx, nrhs, Y, ldy, (cudaStream_t)stream, err);
+    if (rc && err.empty()) err = "kernel launch failed";
     if (rc) return fail(rc, err);
     return RT_OK;
 }
@@ -437,6 +523,15 @@ int rt_apply_noalloc(rt_operator* h, const void* X, void* Y, void* stream)
     if (!h || !X || !Y) return fail(RT_EINVAL, "null argument");
     std::string err;
     int rc = rt::apply_noalloc(h->op, X, Y, (cudaStream_t)stream, err);
+    if (rc) return fail(rc, err);
+    return RT_OK;
+}
+
+int rt_eval_sin2pi(const float* x, float* lib_out, float* ref_out, int64_t n, void* stream)
+{
+    if (n < 0 || (n > 0 && (!x || !lib_out || !ref_out))) return fail(RT_EINVAL, "null argument");
+    std::string err;
+    int rc = rt::eval_sin2pi(x, lib_out, ref_out, n, (cudaStream_t)stream, err);
     if (rc) return fail(rc, err);
     return RT_OK;
 }

@@ -21,6 +21,7 @@
 // [r][m8]) and dense blocks column-major per leaf chunk (A^T [n][m8]), padded
 // to multiples of 8 elements with zeros so every chunk row is 16-byte aligned.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <numeric>
 #include <string>
@@ -40,14 +41,15 @@ namespace rt {
 // dense mode: y_f[i] = sum_j A_g[i][j] x_f[j], A row-major [G][N][N]; warp per (i, f)
 template <class V>
 __global__ void __launch_bounds__(256) dense_apply(const V* __restrict__ A, const V* __restrict__ X,
-                                                   V* __restrict__ Y, int N, int F, const int* __restrict__ fgroup)
+                                                   V* __restrict__ Y, int N, int F, const int* __restrict__ fgroup,
+                                                   int64_t ldx, int64_t ldy)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < (int64_t)N * F; w += nw) {
         const int f = (int)(w / N), i = (int)(w % N);
         const V* __restrict__ a = A + ((int64_t)fgroup[f] * N + i) * N;
-        const V* __restrict__ x = X + (int64_t)f * N;
+        const V* __restrict__ x = X + (int64_t)f * ldx;
         V s0 = 0, s1 = 0;
         int j = lane;
         for (; j + 32 < N; j += 64) {
@@ -58,33 +60,73 @@ __global__ void __launch_bounds__(256) dense_apply(const V* __restrict__ A, cons
         V s = s0 + s1;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) Y[(int64_t)f * N + i] = s;
+        if (lane == 0) Y[(int64_t)f * ldy + i] = s;
     }
 }
 
-// permutation between caller order and tree order, rows of length N
+// permutation between caller order and tree order, rows of length N; with a
+// scale, row r of the output is multiplied by scale[r]
 template <class V>
 __global__ void permute_kernel(const V* __restrict__ in, V* __restrict__ out, const int* __restrict__ perm, int N,
-                               int rows, int to_tree)
+                               int rows, int to_tree, const double* __restrict__ scale)
 {
     const int64_t total = (int64_t)N * rows;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = e / N;
         const int t = (int)(e % N);
-        if (to_tree) out[e] = in[r * N + perm[t]];
-        else out[r * N + perm[t]] = in[e];
+        const V v = to_tree ? in[r * N + perm[t]] : in[e];
+        const V o = scale ? (V)((double)v * scale[r]) : v;
+        if (to_tree) out[e] = o;
+        else out[r * N + perm[t]] = o;
     }
 }
 
-int permute_vectors(Operator& op, const void* in, void* out, int to_tree, int is64, int rows, cudaStream_t s)
+int permute_vectors(Operator& op, const void* in, void* out, int to_tree, int is64, int rows, cudaStream_t s,
+                    const double* scale)
 {
     const int64_t total = (int64_t)op.N * rows;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 32));
     if (is64)
-        permute_kernel<double><<<grid, 256, 0, s>>>((const double*)in, (double*)out, op.d_perm, op.N, rows, to_tree);
+        permute_kernel<double><<<grid, 256, 0, s>>>((const double*)in, (double*)out, op.d_perm, op.N, rows, to_tree,
+                                                    scale);
     else
-        permute_kernel<float><<<grid, 256, 0, s>>>((const float*)in, (float*)out, op.d_perm, op.N, rows, to_tree);
+        permute_kernel<float><<<grid, 256, 0, s>>>((const float*)in, (float*)out, op.d_perm, op.N, rows, to_tree,
+                                                   scale);
     return cudaGetLastError() == cudaSuccess ? RT_OK : RT_ECUDA;
+}
+
+// Y_f *= scale[f] in place (the c_f / c_g factor of binned channels, dense operators)
+template <class V>
+__global__ void scale_rows_kernel(V* __restrict__ Y, int N, int rows, const double* __restrict__ scale)
+{
+    const int64_t total = (int64_t)N * rows;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+        Y[e] = (V)((double)Y[e] * scale[e / N]);
+}
+
+int scale_rows(Operator& op, void* Y, cudaStream_t s)
+{
+    const int64_t total = (int64_t)op.N * op.F;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 32));
+    if (op.vec64) scale_rows_kernel<double><<<grid, 256, 0, s>>>((double*)Y, op.N, op.F, op.d_fscale);
+    else scale_rows_kernel<float><<<grid, 256, 0, s>>>((float*)Y, op.N, op.F, op.d_fscale);
+    return cudaGetLastError() == cudaSuccess ? RT_OK : RT_ECUDA;
+}
+
+// caller vectors with leading dimensions <-> tree-order rows [F][N]: rows
+// r < cnt are copied (gathered with perm, or scattered back), rows cnt..F-1 of
+// a tree-order destination are zeroed
+template <class V>
+__global__ void permute_ld_kernel(const V* __restrict__ in, int64_t ldin, V* __restrict__ out, int64_t ldout,
+                                  const int* __restrict__ perm, int N, int rows, int cnt, int to_tree)
+{
+    const int64_t total = (int64_t)N * (to_tree ? rows : cnt);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / N;
+        const int t = (int)(e % N);
+        if (to_tree) out[e] = r < cnt ? in[r * ldin + perm[t]] : V(0);
+        else out[r * ldout + perm[t]] = in[r * N + t];
+    }
 }
 
 // Stage records of the streamed phases.
@@ -253,6 +295,17 @@ int hmatvec_prepare(Operator& op, std::string& err)
     if ((rc = dev_alloc(op, &d_fg, op.F, err))) return rc;
     if ((rc = upload_async(op, d_fg, op.fgroup.data(), op.F, err))) return rc;
     op.d_fq_group = d_fg;
+    if (op.binned) {
+        if ((rc = dev_alloc(op, &op.d_fscale, op.F, err))) return rc;
+        if ((rc = upload_async(op, op.d_fscale, op.fscale.data(), op.F, err))) return rc;
+    }
+    {   // rt_apply_group: every channel of a chunk mapped to one group
+        std::vector<int> gm((size_t)op.G * op.F);
+        for (int g = 0; g < op.G; ++g)
+            for (int f = 0; f < op.F; ++f) gm[(size_t)g * op.F + f] = g;
+        if ((rc = dev_alloc(op, &op.d_gmap, gm.size(), err))) return rc;
+        if ((rc = upload_async(op, op.d_gmap, gm.data(), gm.size(), err))) return rc;
+    }
     // frequency table for the solver: nu, w c (1-a), a, group
     {
         std::vector<double> fq((size_t)op.F * 4);
@@ -463,17 +516,21 @@ int apply_check_error(Operator& op, cudaStream_t s, std::string& err)
     return RT_OK;
 }
 
-static int launch_dense(Operator& op, const void* X, void* Y, cudaStream_t s, std::string& err)
+static int launch_dense(Operator& op, const void* X, void* Y, cudaStream_t s, std::string& err,
+                        const int* fgroup = nullptr, int rows = 0, int64_t ldx = 0, int64_t ldy = 0)
 {
-    const int N = op.N, F = op.F;
+    const int N = op.N, F = rows > 0 ? rows : op.F;
     const int64_t warps = (int64_t)N * F;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, 152 * 16));
+    if (!fgroup) fgroup = op.d_fq_group;
+    if (ldx <= 0) ldx = N;
+    if (ldy <= 0) ldy = N;
     if (op.vec64)
         dense_apply<double><<<grid, 256, 0, s>>>((const double*)op.d_dense, (const double*)X, (double*)Y, N, F,
-                                                 op.d_fq_group);
+                                                 fgroup, ldx, ldy);
     else
         dense_apply<float><<<grid, 256, 0, s>>>((const float*)op.d_dense, (const float*)X, (float*)Y, N, F,
-                                                op.d_fq_group);
+                                                fgroup, ldx, ldy);
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
 }
@@ -485,21 +542,65 @@ int apply_tree(Operator& op, const void* X, void* Y, cudaStream_t s, std::string
     return launch_hmv(op, (const float*)X, op.d_w, (float*)Y, s, err);
 }
 
+// Y_j = G_group X_j for nrhs caller vectors with leading dimensions, in
+// chunks of F right-hand sides through the operator's own kernels and scratch
+int apply_group(Operator& op, int group, const void* X, int64_t ldx, int nrhs, void* Y, int64_t ldy, cudaStream_t s,
+                std::string& err)
+{
+    const int N = op.N, F = op.F;
+    const int* gm = op.d_gmap + (int64_t)group * F;
+    for (int j0 = 0; j0 < nrhs; j0 += F) {
+        const int cnt = std::min(F, nrhs - j0);
+        int rc;
+        if (op.mode == RT_MODE_DENSE) {
+            if (op.vec64)
+                rc = launch_dense(op, (const double*)X + j0 * ldx, (double*)Y + j0 * ldy, s, err, gm, cnt, ldx, ldy);
+            else
+                rc = launch_dense(op, (const float*)X + j0 * ldx, (float*)Y + j0 * ldy, s, err, gm, cnt, ldx, ldy);
+            if (rc) return rc;
+            continue;
+        }
+        const int64_t tot_in = (int64_t)N * F;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((tot_in + 255) / 256, 152 * 32));
+        permute_ld_kernel<float><<<grid, 256, 0, s>>>((const float*)X + j0 * ldx, ldx, op.d_xt, N, op.d_perm, N, F,
+                                                      cnt, 1);
+        RT_CUDA_TRY(cudaGetLastError());
+        if (op.tc_enabled && !op.use_lo) {
+            // one group: the tcgen05 pair applies G_0 to all F rows
+            if ((rc = tc_apply(op, op.d_xt, op.d_yt, s, err))) return rc;
+        } else {
+            const int* keep = op.d_fq_group;
+            op.d_fq_group = const_cast<int*>(gm);
+            rc = launch_hmv(op, op.d_xt, op.d_w, op.d_yt, s, err);
+            op.d_fq_group = const_cast<int*>(keep);
+            if (rc) return rc;
+        }
+        permute_ld_kernel<float><<<grid, 256, 0, s>>>(op.d_yt, N, (float*)Y + j0 * ldy, ldy, op.d_perm, N, F, cnt, 0);
+        RT_CUDA_TRY(cudaGetLastError());
+    }
+    return RT_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Apply without allocation.
 //
-// Same kernels and the same arithmetic as apply_tree + the two permutations,
-// but the scratch (X and Y in tree order and the phase-1 w buffer) lives in
-// one file-scope device array instead of buffers owned by the operator.  The
-// array is kNoAllocBytes large, is held by every GPU that loads the library
-// until the process exits, and is shared by every call: it keeps the previous
-// call's contents (every region used is fully overwritten before it is read,
-// so nothing needs clearing), and two calls that overlap on the GPU race on it.
+// Same kernels and the same arithmetic as apply_tree + the two permutations
+// (the tcgen05 pair when rt_apply takes it, otherwise the CUDA-core phases),
+// but the scratch (X and Y in tree order and, for the CUDA-core phases, the
+// phase-1 w buffer) lives in one file-scope device array instead of buffers
+// owned by the operator.  The tcgen05 pair's W panels and split X belong to
+// the operator and were allocated when it was built.  The array is
+// kNoAllocBytes large, is held by every GPU that loads the library until the
+// process exits, and is shared by every call: it keeps the previous call's
+// contents (every region used is fully overwritten before it is read, so
+// nothing needs clearing), and two calls that overlap on the GPU race on it.
 // ---------------------------------------------------------------------------
 static constexpr size_t kNoAllocBytes = (size_t)8 << 20;
 static constexpr int kNoAllocMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
-static void* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};   // device address per device, set on first use
+// device address of the array per device, set on first use; two threads making
+// their first call on one device at once both look it up and store the same value
+static std::atomic<void*> g_noalloc_addr[kNoAllocMaxDevices];
 
 static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -515,9 +616,14 @@ int apply_noalloc(Operator& op, const void* X, void* Y, cudaStream_t s, std::str
     }
     const int N = op.N, F = op.F;
     // the dense apply reads X and writes Y directly: no scratch at all
-    if (op.mode == RT_MODE_DENSE) return launch_dense(op, X, Y, s, err);
+    if (op.mode == RT_MODE_DENSE) {
+        int rc = launch_dense(op, X, Y, s, err);
+        if (!rc && op.binned) rc = scale_rows(op, Y, s);
+        return rc;
+    }
+    const bool tc = op.tc_enabled && !op.use_lo;   // the path apply_tree takes
     const size_t vbytes = round256((size_t)F * N * sizeof(float));
-    const size_t wbytes = round256((size_t)std::max<int64_t>(op.w_len, 1) * sizeof(float));
+    const size_t wbytes = tc ? 0 : round256((size_t)std::max<int64_t>(op.w_len, 1) * sizeof(float));
     const size_t need = 2 * vbytes + wbytes;
     if (need > kNoAllocBytes) {
         err = "rt_apply_noalloc: operator needs " + std::to_string(need) + " bytes of scratch, limit is " +
@@ -528,18 +634,18 @@ int apply_noalloc(Operator& op, const void* X, void* Y, cudaStream_t s, std::str
         err = "rt_apply_noalloc: device index out of range";
         return RT_EINVAL;
     }
-    if (!g_noalloc_addr[dev]) {
+    void* addr = g_noalloc_addr[dev].load(std::memory_order_acquire);
+    if (!addr) {
         // one-time set-up on this device (the device is current): the host-side
         // name of a __device__ array is not a device address; ask the runtime for it
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
+        cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+        if (e != cudaSuccess || !addr) {
             err = std::string("rt_apply_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
             return RT_ECUDA;
         }
-        g_noalloc_addr[dev] = p;
+        g_noalloc_addr[dev].store(addr, std::memory_order_release);
     }
-    unsigned char* base = (unsigned char*)g_noalloc_addr[dev];
+    unsigned char* base = (unsigned char*)addr;
     float* xt = (float*)base;
     float* yt = (float*)(base + vbytes);
     float* w = (float*)(base + 2 * vbytes);
@@ -548,8 +654,12 @@ int apply_noalloc(Operator& op, const void* X, void* Y, cudaStream_t s, std::str
         err = "rt_apply_noalloc: permute launch failed";
         return rc;
     }
-    if ((rc = launch_hmv(op, xt, w, yt, s, err))) return rc;
-    rc = permute_vectors(op, yt, Y, 0, 0, F, s);
+    if (tc) {
+        if ((rc = tc_apply(op, xt, yt, s, err))) return rc;
+    } else if ((rc = launch_hmv(op, xt, w, yt, s, err))) {
+        return rc;
+    }
+    rc = permute_vectors(op, yt, Y, 0, 0, F, s, op.binned ? op.d_fscale : nullptr);
     if (rc) {
         err = "rt_apply_noalloc: permute launch failed";
         return rc;

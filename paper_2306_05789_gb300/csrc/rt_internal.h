@@ -162,6 +162,10 @@ struct Operator {
     std::vector<double> nu, w, c, albedo, Q;
     std::vector<int> fgroup;
     std::vector<double> gc;     // group scales
+    std::vector<double> fscale; // per channel c_f / c_{g(f)} (1 unless channels are binned)
+    int binned = 0;             // some fscale != 1
+    double* d_fscale = nullptr; // device copy [F] when binned
+    int* d_gmap = nullptr;      // [G][F]: row g has every entry g (rt_apply_group)
     Plan plan;
     // device geometry
     float4* d_xyz32 = nullptr;
@@ -265,11 +269,16 @@ int eval_entries(Operator& op, int group, int64_t count, const int32_t* rows, co
 int hmatvec_prepare(Operator& op, std::string& err);
 // X, Y in tree order, [F][N], element type float (H-matrix / dense F32) or double (dense F64)
 int apply_tree(Operator& op, const void* X, void* Y, cudaStream_t s, std::string& err);
-int permute_vectors(Operator& op, const void* in, void* out, int to_tree, int is64, int rows, cudaStream_t s);
+int permute_vectors(Operator& op, const void* in, void* out, int to_tree, int is64, int rows, cudaStream_t s,
+                    const double* scale = nullptr);
+int scale_rows(Operator& op, void* Y, cudaStream_t s);   // Y_f *= fscale[f] (binned channels)
+int apply_group(Operator& op, int group, const void* X, int64_t ldx, int nrhs, void* Y, int64_t ldy, cudaStream_t s,
+                std::string& err);
 // rt_apply with its scratch in a file-scope device array (no allocation)
 int apply_noalloc(Operator& op, const void* X, void* Y, cudaStream_t s, std::string& err);
 size_t apply_noalloc_limit();
 int tc_prepare(Operator& op, std::string& err);
+int eval_sin2pi(const float* x, float* lib, float* ref, int64_t n, cudaStream_t s, std::string& err);
 int tc_apply(Operator& op, const float* X, float* Y, cudaStream_t s, std::string& err);
 int tc_check_error(Operator& op, cudaStream_t s, std::string& err);
 // RT_ETIMEOUT if a bounded wait of an apply kernel (tensor-core or streamed) gave up

@@ -41,6 +41,7 @@ struct Request {
     std::vector<int32_t> tet, emit;
     std::vector<rt_wall> walls;
     std::vector<double> nu, w, c, albedo;
+    std::vector<int32_t> group;
     Plan plan;
     int64_t est_peak = 0, est_resident = 0;
     int64_t held = 0;            // budget this request holds now
@@ -295,6 +296,7 @@ int rt_submit(rt_server* h, const rt_problem* P, int64_t* id)
         r->w.assign(P->freqs.w, P->freqs.w + F);
         r->c.assign(P->freqs.c, P->freqs.c + F);
         r->albedo.assign(P->freqs.albedo, P->freqs.albedo + F);
+        if (P->freqs.group) r->group.assign(P->freqs.group, P->freqs.group + F);
         r->prob = *P;
         r->prob.mesh.xyz = r->xyz.data();
         r->prob.mesh.tet = r->tet.data();
@@ -304,6 +306,8 @@ int rt_submit(rt_server* h, const rt_problem* P, int64_t* id)
         r->prob.freqs.w = r->w.data();
         r->prob.freqs.c = r->c.data();
         r->prob.freqs.albedo = r->albedo.data();
+        r->prob.freqs.group = r->group.empty() ? nullptr : r->group.data();   // the estimate below
+        // counts distinct c, an upper bound on the groups of a binned grid
         rc = rt::plan_build(r->xyz.data(), N, S.o.hp.leaf, S.o.hp.eta, S.o.hp.adm, r->plan, err);
         if (rc) {
             rt::set_last_error(err);

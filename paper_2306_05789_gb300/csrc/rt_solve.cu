@@ -37,9 +37,12 @@ __global__ void fp_init(V* J, double* T, int64_t nJ, int N, double T0, int keepJ
 }
 
 // S = a J + (1-a) B(T)
+// S = a J + (1-a) B(T), times c_f / c_g for binned channels (fscale non-null),
+// so that the group operator G_g applied to S gives the channel's c_f kappa(y)
+// prefactor
 template <class V>
 __global__ void fp_source(const V* __restrict__ J, const double* __restrict__ T, V* __restrict__ S,
-                          const double* __restrict__ fq, int N, int F, int grey)
+                          const double* __restrict__ fq, int N, int F, int grey, const double* __restrict__ fscale)
 {
     const int64_t total = (int64_t)N * F;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -47,7 +50,8 @@ __global__ void fp_source(const V* __restrict__ J, const double* __restrict__ T,
         const double a = fq[4 * f + 2];
         const double t = T[i];
         const double B = grey ? kSigma * t * t * t * t : planck(fq[4 * f + 0], t);
-        S[e] = (V)(a * (double)J[e] + (1.0 - a) * B);
+        const double v = a * (double)J[e] + (1.0 - a) * B;
+        S[e] = (V)(fscale ? v * fscale[f] : v);
     }
 }
 
@@ -211,7 +215,8 @@ static int one_iteration(Operator& op, cudaStream_t s, int grey, int* d_counter,
 {
     const int N = op.N, F = op.F;
     const int64_t tot = (int64_t)N * F;
-    fp_source<V><<<grid_elem(tot), 256, 0, s>>>((const V*)op.d_J, op.d_T, (V*)op.d_S, op.d_fq, N, F, grey);
+    fp_source<V><<<grid_elem(tot), 256, 0, s>>>((const V*)op.d_J, op.d_T, (V*)op.d_S, op.d_fq, N, F, grey,
+                                                  op.binned ? op.d_fscale : nullptr);
     RT_CUDA_TRY(cudaGetLastError());
     int rc = apply_tree(op, op.d_S, op.d_Y, s, err);
     if (rc) return rc;

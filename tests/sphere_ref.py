@@ -106,3 +106,53 @@ def square_view(y0, z0, d, ylo=0.0, yhi=1.0, zlo=0.0, zhi=1.0):
             return 0.0
         return su * sv * rect_view(abs(u), abs(v), d)
     return (F(yhi - y0, zhi - z0) - F(ylo - y0, zhi - z0) - F(yhi - y0, zlo - z0) + F(ylo - y0, zlo - z0))
+
+
+def _composite_gauss_square(npan, nq):
+    """Composite tensor Gauss-Legendre rule on [0,1]^2: points (s, t) and weights."""
+    g, wg = np.polynomial.legendre.leggauss(nq)
+    edges = np.linspace(0.0, 1.0, npan + 1)
+    s = (0.5 * (edges[:-1, None] + edges[1:, None]) + 0.5 * (edges[1:, None] - edges[:-1, None]) * g[None, :]).ravel()
+    ws = (0.5 * (edges[1:, None] - edges[:-1, None]) * wg[None, :]).ravel()
+    S, T = np.meshgrid(s, s, indexing="ij")
+    W2 = np.outer(ws, ws)
+    return S.ravel(), T.ravel(), W2.ravel()
+
+
+def emitter_source_reference(x, kappa_kind, k0, amp, c, R0, npan=24, nq=10):
+    """Emitter source (without the intensity Q) at an interior point x of the unit cube,
+    emitter = the face x = 0, reflective wall z = 0 (Example of Section 1.2, squared-cosine form):
+
+      (1/4pi) int_{[0,1]^2} d^2 e^{-c tau(x, y)} / |x - y|^4 dA(y)
+      + R0 (1/4pi) int_{[0,1]^2} d^2 e^{-c tau_R(x, y)} / |xbar - y|^4 dA(y),
+
+    d = x_1, xbar = (x_1, x_2, -x_3), and tau_R the optical depth along the broken
+    path x -> x' -> y through the wall, i.e. the straight line from xbar to y in
+    the doubled domain with kappa extended evenly in z.  Optical depths are exact
+    line integrals (closed form), the face integral a composite tensor Gauss rule."""
+    x = np.asarray(x, dtype=np.float64)
+    S, T, Wq = _composite_gauss_square(npan, nq)
+    Y = np.stack([np.zeros_like(S), S, T], axis=1)
+    d = x[0]
+
+    def line_tau(a, b, zsign=1.0):
+        v = b - a
+        L = np.linalg.norm(v, axis=-1)
+        if kappa_kind == 0:
+            return k0 * L
+        return sinprod_line_integral(np.broadcast_to(a, v.shape), v / L[:, None], np.zeros_like(L), L, k0, amp, zsign)
+
+    r2 = ((Y - x) ** 2).sum(axis=1)
+    direct = (Wq * d * d * np.exp(-c * line_tau(x, Y)) / (r2 * r2)).sum() / (4 * math.pi)
+    if R0 == 0:
+        return direct
+    xb = np.array([x[0], x[1], -x[2]])
+    v = Y - xb
+    rb2 = (v ** 2).sum(axis=1)
+    # the crossing x' of z = 0 on [xbar, y]: below it kappa is taken at the mirror point
+    sc = (-xb[2]) / v[:, 2]
+    Xp = xb + sc[:, None] * v
+    t_low = line_tau(np.broadcast_to(xb, Y.shape).copy(), Xp, zsign=-1.0) if kappa_kind else k0 * np.linalg.norm(Xp - xb, axis=1)
+    t_up = line_tau(Xp, Y) if kappa_kind else k0 * np.linalg.norm(Y - Xp, axis=1)
+    refl = (Wq * d * d * np.exp(-c * (t_low + t_up)) / (rb2 * rb2)).sum() / (4 * math.pi)
+    return direct + R0 * refl

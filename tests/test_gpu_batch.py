@@ -69,3 +69,31 @@ def test_batch_solve_equals_single_instance_solves_and_oracle(batch):
         if k < 3:
             ref = O.fixed_point(p, O.DenseOperator(p), tol=1e-10)
             assert np.linalg.norm(Tk - ref["T"]) / np.linalg.norm(ref["T"]) < 1e-5
+
+
+def test_bounded_wait_gives_up_with_a_timeout_status_and_the_batch_stays_usable():
+    """Failure detection on the device without a fault or a hang: every phase-2 wait of the
+    persistent apply is made to target a completion count that no phase-1 item provides, with
+    a short clock budget.  Each wait gives up, the solve reports RT_ETIMEOUT, the context stays
+    usable, and with the normal wait restored the same batch solves and matches the oracle."""
+    probs = W.batch_instances(count=3, seed=5, nmin=5, nmax=7, fmin=1, fmax=2)
+    b = rt.rt_build_batch(probs, rt.hparams(leaf=32), threads=3, tune=False)
+    try:
+        nv, nt = int(b.vec_off[-1]), int(b.vert_off[-1])
+        J = torch.zeros(nv, dtype=torch.float32, device=DEV)
+        T = torch.zeros(nt, dtype=torch.float64, device=DEV)
+        b.set_wait(20000, unreachable=True)   # ~10 microseconds per wait
+        with pytest.raises(rt.RtError) as e:
+            b.solve(J, T, tol=1e-6, max_iter=2, check_every=1, use_graph=False)
+        assert e.value.code == rt.RT_ETIMEOUT
+        torch.cuda.synchronize()   # the context is still usable
+        b.set_wait(0, unreachable=False)
+        iters, st = b.solve(J, T, tol=1e-6, max_iter=300, check_every=4)
+        assert st["converged"] == 1
+        Th = T.cpu().numpy()
+        for k, p in enumerate(probs):
+            ref = O.fixed_point(p, O.DenseOperator(p), tol=1e-10)
+            t = Th[int(b.vert_off[k]):int(b.vert_off[k + 1])]
+            assert np.linalg.norm(t - ref["T"]) / np.linalg.norm(ref["T"]) < 1e-5
+    finally:
+        b.free()

@@ -284,7 +284,7 @@ def test_hmatrix_handles_ragged_and_tiny_meshes():
 
 def test_literal_center_admissibility_is_kept_as_an_option():
     """The literal centre-distance reading admits touching clusters; it still builds and
-    applies (with a larger ACA error, reported in the design doc)."""
+    applies, with a larger ACA error than the gap reading."""
     p = W.cube_problem(8, W.sinprod_kappa(0.5), W.midpoint_freqs(2, albedo=0.3), R0=0.5)
     op = rt.rt_build_operator(p, rt.hparams(leaf=32, adm=rt.RT_ADM_CENTER))
     info = op.info()
@@ -394,16 +394,123 @@ def test_32cube_sampled_rows_of_the_apply(op32):
     assert info["compression"] > 0.7
 
 
+def test_32cube_apply_on_1000_stored_oracle_rows(op32):
+    """The apply at the 32^3, 16-group benchmark size against 1000 dense FP64 oracle rows
+    (written by tests/golden/make_golden.py from oracle/ alone, for the seeded input
+    X = rand_vectors((16, N), seed=0)): relative L2 error over all rows and frequencies,
+    and the worst single row."""
+    import os
+    p, op = op32
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "cube32_F16_apply_rows1000.npz"))
+    rows, ref = g["rows"], g["Y"]
+    np.testing.assert_array_equal(rows, W.sample_rows(p.N, 1000, seed=0))
+    X = W.rand_vectors((p.freqs.F, p.N), seed=0)
+    Xd = torch.tensor(X, dtype=torch.float32, device=DEV)
+    Y = torch.zeros_like(Xd)
+    op.apply(Xd, Y)
+    torch.cuda.synchronize()
+    got = Y.double().cpu().numpy()[:, rows]
+    assert rel_l2(got, ref) < 1e-4
+    per_row = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert per_row.max() < 1e-3
+
+
 def test_32cube_solve_one_step_residual(op32):
     p, op = op32
     J = torch.zeros(p.freqs.F, p.N, dtype=torch.float32, device=DEV)
     T = torch.zeros(p.N, dtype=torch.float64, device=DEV)
     st = op.solve_fixed_point(J, T, tol=1e-6, max_iter=200, check_every=4)
     assert st["converged"] == 1
-    rows = W.sample_rows(p.N, 8, seed=1)
+    rows = W.sample_rows(p.N, 128, seed=1)
     Jh = J.double().cpu().numpy()
     Th = T.cpu().numpy()
     res = O.one_step_residual(p, rows, Jh, Th)
     assert np.linalg.norm(res) / np.linalg.norm(Jh[:, rows]) < 1e-4
     # the temperature solves the Planck balance for the returned J
     np.testing.assert_allclose(O.temperature_newton(Jh[:, rows], p.freqs), Th[rows], rtol=1e-9)
+
+
+def test_library_sin2pi_matches_cuda_sinpi_on_a_dense_grid():
+    """The FP32 sin(2 pi x) of the sin-product kappa (range reduction to 2x = n + t,
+    |t| <= 1/2, and the odd Taylor series of sin(pi t) through t^11) against CUDA's
+    sinpif(2x) and against FP64 on a dense grid over [-2, 2]: max abs error <= 2e-7."""
+    x = torch.linspace(-2.0, 2.0, 4_000_001, dtype=torch.float32, device=DEV)
+    lib_v = torch.empty_like(x)
+    ref_v = torch.empty_like(x)
+    rt.rt_eval_sin2pi(x, lib_v, ref_v)
+    torch.cuda.synchronize()
+    lv = lib_v.double().cpu().numpy()
+    rv = ref_v.double().cpu().numpy()
+    exact = np.sin(2 * np.pi * x.double().cpu().numpy())
+    assert np.abs(lv - rv).max() <= 2e-7
+    assert np.abs(lv - exact).max() <= 2e-7
+
+
+# ---------------------------------------------------------------------------
+# kappa_nu binned into a few operator groups; one group applied to many vectors
+# ---------------------------------------------------------------------------
+def test_binned_channels_apply_and_solve_match_the_binned_oracle():
+    """16 channels binned into 4 kappa groups (Remark of Section 2.1): the H-matrix apply and
+    the fixed point against the oracle's binned dense operator."""
+    fr = W.midpoint_freqs(16, albedo=0.3)
+    p = W.cube_problem(10, W.sinprod_kappa(0.5), fr, R0=0.5)
+    op = rt.rt_build_operator(p, rt.hparams(leaf=32, kappa_bins=4))
+    try:
+        assert op.info()["G"] == 4
+        ora = O.DenseOperator(p, bins=4)
+        X = W.rand_vectors((16, p.N), seed=6)
+        Xd = torch.tensor(X, dtype=torch.float32, device=DEV)
+        Y = torch.zeros_like(Xd)
+        op.apply(Xd, Y)
+        torch.cuda.synchronize()
+        assert rel_l2(Y.double().cpu().numpy(), ora.apply(X)) < 1e-4
+        J = torch.zeros(16, p.N, dtype=torch.float32, device=DEV)
+        T = torch.zeros(p.N, dtype=torch.float64, device=DEV)
+        st = op.solve_fixed_point(J, T, tol=1e-7, max_iter=200, check_every=2)
+        assert st["converged"] == 1
+        ref = O.fixed_point(p, ora, tol=1e-11)
+        assert rel_l2(T.cpu().numpy(), ref["T"]) < 1e-5
+    finally:
+        op.free()
+
+
+def test_caller_group_map_and_dense_binned_apply():
+    """A caller's channel -> group map (3 groups over 6 channels) on the dense FP64 path: every
+    channel's apply equals (c_f / c_g) G_g X_f of the oracle to FP64 round-off."""
+    fr = W.midpoint_freqs(6, albedo=0.3)
+    fr = W.Freqs(fr.nu, fr.w, fr.c, fr.albedo, group=np.array([0, 0, 1, 1, 2, 2], dtype=np.int32))
+    p = W.cube_problem(6, W.sinprod_kappa(0.5), fr, R0=0.5)
+    op = rt.rt_build_operator(p, dense_hp())
+    try:
+        X = W.rand_vectors((6, p.N), seed=7)
+        Xd = torch.tensor(X, dtype=torch.float64, device=DEV)
+        Y = torch.zeros_like(Xd)
+        op.apply(Xd, Y)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(Y.cpu().numpy(), O.DenseOperator(p).apply(X), rtol=1e-11, atol=1e-14)
+    finally:
+        op.free()
+
+
+@pytest.mark.parametrize("mode", ["hmatrix", "dense"])
+def test_apply_group_on_many_vectors_with_leading_dimensions(mode):
+    """rt_apply_group: one group's operator on 37 vectors (more than F = 3 and not a multiple
+    of it) stored with leading dimensions larger than N, against the oracle's rows."""
+    fr = W.midpoint_freqs(3, albedo=0.3)
+    p = W.cube_problem(9, W.sinprod_kappa(0.5), fr, R0=0.5)
+    hp = rt.hparams(leaf=32) if mode == "hmatrix" else dense_hp(rt.RT_PREC_F32)
+    op = rt.rt_build_operator(p, hp)
+    try:
+        nrhs, ldx, ldy = 37, p.N + 5, p.N + 11
+        X = W.rand_vectors((nrhs, p.N), seed=8)
+        Xd = torch.zeros(nrhs, ldx, dtype=torch.float32, device=DEV)
+        Xd[:, :p.N] = torch.tensor(X, dtype=torch.float32)
+        Yd = torch.full((nrhs, ldy), -7.0, dtype=torch.float32, device=DEV)
+        op.apply_group(1, Xd, Yd, nrhs=nrhs, ldx=ldx, ldy=ldy)
+        torch.cuda.synchronize()
+        Yh = Yd.cpu().numpy()
+        R = O.G_rows(p, np.arange(p.N, dtype=np.int32))[:, 1, :]
+        assert rel_l2(Yh[:, :p.N], X @ R.T) < (1e-4 if mode == "hmatrix" else 1e-5)
+        assert (Yh[:, p.N:] == -7.0).all()   # nothing written beyond N
+    finally:
+        op.free()

@@ -76,3 +76,22 @@ def test_tensor_core_apply_matches_cuda_core_apply(far, n, F):
     assert rel_l2(y_tc, ref) < (3e-3 if far == rt.RT_PREC_BF16 else 1e-4)
     op_tc.free()
     op_cc.free()
+
+
+@pytest.mark.parametrize("far,bound", [(rt.RT_PREC_BF16, 3e-3), (rt.RT_PREC_F16, 2e-4)])
+def test_tensor_core_apply_at_64_right_hand_sides_matches_the_oracle(far, bound):
+    """The 64-right-hand-side tile width of the 64^3 workload on a 20^3 mesh (several
+    column clusters per M = 128 tile, ragged leaves): the tcgen05 apply against dense FP64
+    oracle rows at 200 sampled vertices, per far-field precision."""
+    F = 64
+    p = W.cube_problem(20, W.sinprod_kappa(0.5), W.midpoint_freqs(F, albedo=0.3, c_offset=None), R0=0.5)
+    op = rt.rt_build_operator(p, rt.hparams(far_prec=far))
+    assert op.info()["apply_tensor_cores"] == 1
+    X = W.rand_vectors((F, p.N), seed=4)
+    Y = apply(op, X)
+    rows = W.sample_rows(p.N, 200, seed=5)
+    R = O.G_rows(p, rows)[:, 0, :]          # one operator group: [rows, N]
+    ref = (R @ X.T).T                        # [F, rows]
+    err = rel_l2(Y[:, rows], ref)
+    assert err < bound, err
+    op.free()

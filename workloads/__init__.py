@@ -106,11 +106,13 @@ class Kappa:
 
 @dataclasses.dataclass
 class Freqs:
-    """Frequency grid. kappa_nu = c[nu] * kappa(x); albedo a_nu; quadrature weight w_nu."""
+    """Frequency grid. kappa_nu = c[nu] * kappa(x); albedo a_nu; quadrature weight w_nu;
+    optional caller-chosen operator group of each channel (None: chosen by the consumer)."""
     nu: np.ndarray
     w: np.ndarray
     c: np.ndarray
     albedo: np.ndarray
+    group: np.ndarray | None = None
 
     @property
     def F(self) -> int:
