@@ -538,7 +538,7 @@ static int launch_dense(Operator& op, const void* X, void* Y, cudaStream_t s, st
 int apply_tree(Operator& op, const void* X, void* Y, cudaStream_t s, std::string& err)
 {
     if (op.mode == RT_MODE_DENSE) return launch_dense(op, X, Y, s, err);
-    if (op.tc_enabled && !op.use_lo) return tc_apply(op, (const float*)X, (float*)Y, s, err);
+    if (tc_serves(op)) return tc_apply(op, (const float*)X, (float*)Y, s, err);
     return launch_hmv(op, (const float*)X, op.d_w, (float*)Y, s, err);
 }
 
@@ -565,7 +565,7 @@ int apply_group(Operator& op, int group, const void* X, int64_t ldx, int nrhs, v
         permute_ld_kernel<float><<<grid, 256, 0, s>>>((const float*)X + j0 * ldx, ldx, op.d_xt, N, op.d_perm, N, F,
                                                       cnt, 1);
         RT_CUDA_TRY(cudaGetLastError());
-        if (op.tc_enabled && !op.use_lo) {
+        if (tc_serves(op)) {
             // one group: the tcgen05 pair applies G_0 to all F rows
             if ((rc = tc_apply(op, op.d_xt, op.d_yt, s, err))) return rc;
         } else {
@@ -621,7 +621,7 @@ int apply_noalloc(Operator& op, const void* X, void* Y, cudaStream_t s, std::str
         if (!rc && op.binned) rc = scale_rows(op, Y, s);
         return rc;
     }
-    const bool tc = op.tc_enabled && !op.use_lo;   // the path apply_tree takes
+    const bool tc = tc_serves(op);   // the path apply_tree takes
     const size_t vbytes = round256((size_t)F * N * sizeof(float));
     const size_t wbytes = tc ? 0 : round256((size_t)std::max<int64_t>(op.w_len, 1) * sizeof(float));
     const size_t need = 2 * vbytes + wbytes;

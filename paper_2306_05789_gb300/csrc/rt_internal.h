@@ -249,6 +249,17 @@ struct Operator {
     int tc_xal = 0;             // X columns of every cluster 16-byte aligned: X split once per apply
     void* tc_xsplit = nullptr;  // X high / low parts (BF16; then FP16 for an FP16 far field)
     int* tc_err = nullptr;
+    // streamed tcgen05 apply (rt_tc2.cu; F = 64): swizzled operator images,
+    // phase-1 tiles, phase-2 leaves with their stages and copy pieces
+    int tc2 = 0;
+    void *t2_tiles = nullptr, *t2_leaves = nullptr, *t2_steps = nullptr, *t2_pieces = nullptr;
+    int t2_ntiles = 0, t2_nleaves = 0;
+    void *t2_vhi = nullptr, *t2_vlo = nullptr, *t2_uhi = nullptr, *t2_ulo = nullptr;
+    void *t2_nhi = nullptr, *t2_nlo = nullptr, *t2_whi = nullptr, *t2_wlo = nullptr;
+    void *t2_xs = nullptr, *t2_zero = nullptr;
+    int64_t t2_xrows = 0, t2_wrows = 0;
+    float* t2_scale = nullptr;   // [s, 1/s, max|X| bits, -]
+    int64_t t2_stats[4] = {0, 0, 0, 0};   // stages, pieces, U image rows, near image rows
     // stats
     rt_info info{};
     std::vector<void*> allocations;
@@ -280,6 +291,10 @@ size_t apply_noalloc_limit();
 int tc_prepare(Operator& op, std::string& err);
 int eval_sin2pi(const float* x, float* lib, float* ref, int64_t n, cudaStream_t s, std::string& err);
 int tc_apply(Operator& op, const float* X, float* Y, cudaStream_t s, std::string& err);
+int tc2_prepare(Operator& op, std::string& err);
+int tc2_apply(Operator& op, const float* X, float* Y, cudaStream_t s, std::string& err);
+// the tcgen05 path serves this apply (the streamed one also serves refinement sweeps)
+inline bool tc_serves(const Operator& op) { return op.tc_enabled && (!op.use_lo || op.tc2); }
 int tc_check_error(Operator& op, cudaStream_t s, std::string& err);
 // RT_ETIMEOUT if a bounded wait of an apply kernel (tensor-core or streamed) gave up
 int apply_check_error(Operator& op, cudaStream_t s, std::string& err);

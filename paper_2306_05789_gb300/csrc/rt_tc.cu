@@ -662,6 +662,8 @@ int tc_prepare(Operator& op, std::string& err)
 {
     op.tc_enabled = 0;
     if (op.tc_off) return RT_OK;
+    int rc0 = tc2_prepare(op, err);   // the streamed form, when it applies (F = 64)
+    if (rc0 || op.tc2) return rc0;
     if (op.mode != RT_MODE_HMATRIX || op.G != 1 || op.F % 16 != 0 || op.F < 16 || op.F > 128) return RT_OK;
     if (op.far_prec != RT_PREC_BF16 && op.far_prec != RT_PREC_F16) return RT_OK;
     for (int l = 0; l < (int)op.plan.leaf_size.size(); ++l)
@@ -819,6 +821,7 @@ static int tc_launch(Operator& op, const float* X, float* Y, cudaStream_t s, std
 // Y = Gbar X for all F right-hand sides (tree order), tensor cores
 int tc_apply(Operator& op, const float* X, float* Y, cudaStream_t s, std::string& err)
 {
+    if (op.tc2) return tc2_apply(op, X, Y, s, err);
     if (op.far_prec == RT_PREC_BF16) return tc_launch<__nv_bfloat16>(op, X, Y, s, err);
     return tc_launch<__half>(op, X, Y, s, err);
 }

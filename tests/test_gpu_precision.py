@@ -95,3 +95,28 @@ def test_tensor_core_apply_at_64_right_hand_sides_matches_the_oracle(far, bound)
     err = rel_l2(Y[:, rows], ref)
     assert err < bound, err
     op.free()
+
+
+@pytest.fixture(scope="module")
+def cube64_golden():
+    import os
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "cube64_F64s_apply_rows1000.npz"))
+    return g["rows"], g["Y"]
+
+
+@pytest.mark.parametrize("far,bound", [(rt.RT_PREC_BF16, 2e-4), (rt.RT_PREC_F16, 1e-4)])
+def test_64cube_tensor_core_apply_on_1000_stored_oracle_rows(cube64_golden, far, bound):
+    """The 64^3 workload (262144 vertices, one operator, 64 right-hand sides) on the streamed
+    tcgen05 path against 1000 dense FP64 oracle rows stored by tests/golden/make_golden.py
+    for X = rand_vectors((64, N), seed=0): BF16 and FP16 far fields, each with its bound."""
+    rows, ref = cube64_golden
+    p = W.shared_kappa_64()
+    np.testing.assert_array_equal(rows, W.sample_rows(p.N, 1000, seed=0))
+    op = rt.rt_build_operator(p, rt.hparams(far_prec=far))
+    try:
+        assert op.info()["apply_tensor_cores"] == 1
+        Y = apply(op, W.rand_vectors((64, p.N), seed=0))
+        err = rel_l2(Y[:, rows], ref)
+        assert err < bound, err
+    finally:
+        op.free()
