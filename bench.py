@@ -51,7 +51,8 @@ def peaks():
 KERNEL_SOURCES = {
     "hmv": ["paper_2306_05789_gb300/csrc/rt_hmv_dev.cuh", "paper_2306_05789_gb300/csrc/rt_hmatvec.cu",
             "paper_2306_05789_gb300/csrc/rt_hmv_stream.cuh", "paper_2306_05789_gb300/csrc/rt_bulk.cuh"],
-    "tc": ["paper_2306_05789_gb300/csrc/rt_tc.cu"],
+    "tc": ["paper_2306_05789_gb300/csrc/rt_tc.cu", "paper_2306_05789_gb300/csrc/rt_tc2.cu",
+           "paper_2306_05789_gb300/csrc/rt_tcgen05.cuh"],
     "dense": ["paper_2306_05789_gb300/csrc/rt_hmatvec.cu"],
     "batch": ["paper_2306_05789_gb300/csrc/rt_batch.cu", "paper_2306_05789_gb300/csrc/rt_hmv_dev.cuh"],
 }
@@ -184,6 +185,7 @@ def run_batch(args):
         J = torch.zeros(int(b.vec_off[-1]), dtype=torch.float32, device=dev)
         T = torch.zeros(int(b.vert_off[-1]), dtype=torch.float64, device=dev)
         iters, st = b.solve(J, T, tol=args.tol, max_iter=300, check_every=4, stream=stream)
+        step.J, step.T = J, T
         return b, iters, st
 
     for _ in range(args.warmup):
@@ -224,10 +226,23 @@ def run_batch(args):
     torch.cuda.synchronize()
     t_apply = a0.elapsed_time(a1) / 20 / 1e3
     b.free()
+    # end to end: the instances' host arrays in (rt_build_batch copies them), J and T back
+    # into pinned host buffers, inside the timed region
+    Jh = torch.empty(int(info["total_vec"]), dtype=torch.float32).pin_memory()
+    Th = torch.empty(int(info["total_vert"]), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b, _, _ = step()
+    Jh.copy_(step.J, non_blocking=True)
+    Th.copy_(step.T, non_blocking=True)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    b.free()
     if rank != 0:
         return
     hbm, _, peak_kind = peaks()
     n = len(probs)
+    h2d = sum(p.xyz.nbytes + p.tet.nbytes + p.emit_tri.nbytes for p in probs)
     gbs = info["apply_bytes"] / t_apply / 1e9
     print(json.dumps({
         "metric": METRIC, "value": world * n * args.steps / (ms / 1e3), "unit": "solves/s", "n_gpus": world,
@@ -246,8 +261,42 @@ def run_batch(args):
         # the same instances with the operators already built: the fixed point alone
         "excluding_assembly": {"value": world * n / max(statistics.mean(solve_ms) / 1e3, 1e-12),
                                "unit": "solves/s"},
+        "e2e": {"value": n / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(Jh.numel() * 4 + Th.numel() * 8),
+                "note": "one step: build and solve of every instance from host arrays, J and T copied to "
+                        "pinned host memory"},
+        "cpu_baseline": None if args.no_cpu_baseline else batch_cpu_baseline(probs, iters, args.cpu_rows),
         "clocks": clk,
     }))
+
+
+def batch_cpu_baseline(probs, iters, rows):
+    """The FP64 oracle on two sampled instances of the batch: `rows` dense rows of each
+    (all groups, plus the source) extrapolated to the instance's N rows and the dense
+    applies of its solve (its GPU iteration count), scaled to the whole batch."""
+    from oracle import oracle as O
+    O.build()
+    rng = np.random.default_rng(7)
+    pick = rng.choice(len(probs), size=min(2, len(probs)), replace=False)
+    M = np.random.default_rng(0).random((4096, 4096))
+    x = np.random.default_rng(1).random((4096, 8))
+    t0 = time.perf_counter()
+    for _ in range(3):
+        M @ x
+    rate = 2 * 4096 * 4096 * 8 / ((time.perf_counter() - t0) / 3)
+    est = []
+    for b in pick:
+        p = probs[int(b)]
+        sel = W.sample_rows(p.N, min(rows, p.N), seed=0)
+        t0 = time.perf_counter()
+        O.G_rows(p, sel)
+        O.source_geometric(p, sel)
+        t_row = (time.perf_counter() - t0) / len(sel)
+        est.append(p.N * t_row + float(iters[int(b)]) * 2.0 * p.freqs.F * p.N * p.N / rate)
+    t_batch = statistics.mean(est) * len(probs)
+    return {"value": len(probs) / t_batch, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{len(pick)} of {len(probs)} instances, {rows} dense FP64 rows each, extrapolated to "
+                      f"N rows + the GPU's iteration count of dense applies, scaled to all instances"}
 
 
 def run_serve(args):
@@ -379,7 +428,8 @@ def run_gpu(args):
         if "--tol" not in sys.argv:
             args.tol = 1e-10
     else:
-        hp = rt.hparams(far_prec=far)
+        hp = rt.hparams(far_prec=far, refine=1 if (args.refine and far != rt.RT_PREC_F32) else 0)
+    refine_tol = 1e-3 if (args.refine and far != rt.RT_PREC_F32 and not dense) else 0.0
     vdt = torch.float64 if dense else torch.float32
     stream = torch.cuda.current_stream(dev)
     F, N = prob.freqs.F, prob.N
@@ -390,7 +440,8 @@ def run_gpu(args):
 
     def step(e2e=False):
         op = rt.rt_build_operator(prob, hp, stream)
-        st = op.solve_fixed_point(J, T, tol=args.tol, max_iter=300, check_every=4, stream=stream)
+        st = op.solve_fixed_point(J, T, tol=args.tol, max_iter=300, check_every=4, stream=stream,
+                                  refine_tol=refine_tol)
         if e2e:
             Jh.copy_(J, non_blocking=True)
             Th.copy_(T, non_blocking=True)
@@ -428,6 +479,23 @@ def run_gpu(args):
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop() if rank == 0 else None
     info = last.info()
+    J_last = J.double().cpu().numpy()
+    T_last = T.cpu().numpy()
+    # accuracy of the last operator's apply against stored FP64 oracle rows (when the
+    # workload has them; tests/golden/make_golden.py) for X = rand_vectors((F, N), seed=0)
+    err_apply = None
+    gpath = os.path.join(ROOT, "tests", "golden", f"{args.workload}_apply_rows1000.npz")
+    if rank == 0 and os.path.exists(gpath):
+        g = np.load(gpath)
+        Xg = torch.tensor(W.rand_vectors((F, N), seed=0), dtype=vdt, device=dev)
+        Yg = torch.zeros_like(Xg)
+        last.apply(Xg, Yg, stream)
+        torch.cuda.synchronize()
+        got = Yg.double().cpu().numpy()[:, g["rows"]]
+        err_apply = {"rel_l2": float(np.linalg.norm(got - g["Y"]) / np.linalg.norm(g["Y"])),
+                     "rows": int(len(g["rows"])), "what": "rt_apply of X = rand_vectors((F, N), seed=0) against "
+                     "dense FP64 oracle rows stored in tests/golden"}
+        del Xg, Yg
     # H-matvec: timed live on the last operator (the per-iteration kernel pair)
     X = torch.rand(F, N, dtype=vdt, device=dev, generator=torch.Generator(device=dev).manual_seed(0))
     Y = torch.zeros_like(X)
@@ -498,12 +566,13 @@ def run_gpu(args):
                    "kappa": "1" if dense else "1+0.5 sin sin sin", "gauss_pts": 16,
                    "operator": "dense FP64" if dense else f"H-matrix, far field {args.far_prec}",
                    "aca_eps": None if dense else 1e-4, "leaf": 64, "eta": 2.0, "R0": 0.5,
+                   "refine": bool(refine_tol > 0),
                    "albedo": 0.0 if dense else 0.3, "tol": args.tol, "far_prec": args.far_prec,
                    "parallelism": f"replicas{world}",
                    "l2": "L2 flushed before each timed apply" if l2_flush else "operator larger than L2 (no flush needed)"},
         "roofline": {"bound": "hbm",
                      "kernel": ("dense_apply" if dense else
-                                ("tc_phase1+tc_phase2 (tcgen05, rt_apply)" if info["apply_tensor_cores"]
+                                ("t2_xsplit+t2_phase1+t2_phase2 (streamed tcgen05, rt_apply)" if info["apply_tensor_cores"]
                                  else "hmv_s1+hmv_s2 streamed (+hmv_phase1 for rows over 1024 columns), rt_apply")),
                      "achieved": apply_gbs, "peak": hbm, "unit": "GB/s", "frac": apply_gbs / hbm,
                      "traffic": measured_traffic(args.workload, kind), "peak_kind": peak_kind,
@@ -515,6 +584,7 @@ def run_gpu(args):
                      "entries_evaluated": info["entries_evaluated"], "compression": info["compression"],
                      "rank_max": info["rank_max"], "n_far": info["n_far"],
                      "n_dense_fallback": info["n_dense_fallback"]},
+        "assembly_roofline": assembly_roofline(info),
         "solve": {"iters_mean": statistics.mean(iters), "ms_solve_mean": statistics.mean(s["ms_total"] for s in stats)},
         "e2e": {"value": world / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": int(prob.xyz.nbytes + prob.tet.nbytes
                                                                                       + prob.emit_tri.nbytes),
@@ -522,11 +592,100 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    out["err_vs_oracle"] = oracle_errors(prob, J_last, T_last, err_apply, args, dense)
+    if args.compare_f32 and not dense and far != rt.RT_PREC_F32:
+        out["plain_fp32"] = compare_fp32(prob, args, dev, stream)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(prob, np.mean(iters), args.cpu_rows)
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def assembly_roofline(info):
+    """Entry evaluation (ACA rows and columns, near blocks) is bound by instruction issue
+    (FP32 pipe and SFU), not memory.  Work units counted on the device: kernel terms (one
+    direct or reflected value of the kernel at a point pair, every group at once) and
+    optical depths (16-point Gauss line integrals, evaluated in closed form).  The peak is
+    the FP32 issue rate, 152 SMs x 128 FP32 lanes x the maximum SM clock of
+    MEASURED_PEAKS.json, with thread instructions per kernel term taken from the committed
+    ncu instruction counts of the two assembly kernels (profiles/assembly_*.md)."""
+    ms = info["ms_aca"] + info["ms_near"]
+    terms, depths = info.get("assembly_terms", 0), info.get("assembly_depths", 0)
+    if ms <= 0 or terms <= 0:
+        return None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", 2070.0))
+    except Exception:
+        mhz = 2070.0
+    lanes_peak = 152 * 128 * mhz * 1e6          # FP32 lane-instructions per second
+    sfu_peak = 152 * 16 * mhz * 1e6             # SFU (MUFU) lane-operations per second
+    out = {"bound": "alu", "ms": ms, "terms": terms, "optical_depths": depths,
+           "terms_per_s": terms / (ms / 1e3), "optical_depths_per_s": depths / (ms / 1e3),
+           "kappa_evals_per_s_16pt_equiv": 16 * depths / (ms / 1e3),
+           "fp32_lane_peak_per_s": lanes_peak, "sfu_peak_per_s": sfu_peak, "peak_clock_mhz": mhz}
+    try:
+        with open(os.path.join(ROOT, "profiles", "assembly_instructions.json")) as f:
+            c = json.load(f)
+        ipt, xpt = float(c["thread_inst_per_term"]), float(c["sfu_thread_inst_per_term"])
+        out.update({"thread_inst_per_term": ipt, "sfu_inst_per_term": xpt,
+                    "achieved_lane_inst_per_s": out["terms_per_s"] * ipt,
+                    "frac_fp32_issue": out["terms_per_s"] * ipt / lanes_peak,
+                    "frac_sfu": out["terms_per_s"] * xpt / sfu_peak, "per_term_counts": c.get("how")})
+    except Exception:
+        pass
+    return out
+
+
+def oracle_errors(prob, J, T, err_apply, args, dense):
+    """Error of this run's result against the FP64 oracle.  Small problems
+    (N <= 4096): the oracle's own fixed point, solved densely.  Larger ones: the
+    one-step fixed-point residual F(J, T) = Sbar^E + G S(J, T) - J on sampled
+    rows computed by the oracle from dense FP64 rows (relative to J there; by
+    contraction the solution error is at most residual / (1 - rho))."""
+    from oracle import oracle as O
+    O.build()
+    out = {"apply": err_apply}
+    if prob.N <= 4096:
+        ref = O.fixed_point(prob, O.DenseOperator(prob), tol=1e-12 if dense else 1e-10, max_iter=600)
+        out["solve"] = {"T_rel_l2": float(np.linalg.norm(T - ref["T"]) / np.linalg.norm(ref["T"])),
+                        "J_rel_l2": float(np.linalg.norm(J - ref["J"]) / np.linalg.norm(ref["J"])),
+                        "what": "against the dense FP64 oracle's fixed point (all vertices)"}
+        return out
+    rows = W.sample_rows(prob.N, args.residual_rows, seed=1)
+    t0 = time.perf_counter()
+    res = O.one_step_residual(prob, rows, J, T)
+    out["solve"] = {"residual_rel_l2": float(np.linalg.norm(res) / np.linalg.norm(J[:, rows])),
+                    "rows": int(len(rows)), "oracle_s": time.perf_counter() - t0,
+                    "what": "one-step fixed-point residual of the returned J, T on sampled dense FP64 oracle rows"}
+    return out
+
+
+def compare_fp32(prob, args, dev, stream):
+    """The same workload with an FP32 far field (CUDA cores), one timed solve, with
+    its residual on the same sampled rows: the comparison point for a 16-bit far field."""
+    import torch
+
+    import paper_2306_05789_gb300 as rt
+    from oracle import oracle as O
+    F, N = prob.freqs.F, prob.N
+    J = torch.zeros(F, N, dtype=torch.float32, device=dev)
+    T = torch.zeros(N, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    op = rt.rt_build_operator(prob, rt.hparams(far_prec=rt.RT_PREC_F32), stream)
+    st = op.solve_fixed_point(J, T, tol=args.tol, max_iter=300, check_every=4, stream=stream)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    info = op.info()
+    op.free()
+    rows = W.sample_rows(N, args.residual_rows, seed=1)
+    Jh = J.double().cpu().numpy()
+    res = O.one_step_residual(prob, rows, Jh, T.cpu().numpy())
+    return {"value": 1.0 / t, "unit": "solves/s", "iters": st["iters"], "ms_solve": st["ms_total"],
+            "apply_tensor_cores": info["apply_tensor_cores"],
+            "residual_rel_l2": float(np.linalg.norm(res) / np.linalg.norm(Jh[:, rows]))}
 
 
 def cpu_baseline(prob, iters, rows):
@@ -590,6 +749,9 @@ def _dense_matvec_ms(n, reps=5):
     return {"N": N, "ms": ms, "gbs": 8.0 * N * N / ms / 1e6}
 
 
+REF_ITERS = {"cube32_F16": 24, "cube64_F64s": 16}
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle on the host cores.  Small single
     problems (N <= 4096) are built densely and iterated to the fixed point,
@@ -617,7 +779,9 @@ def run_reference(args):
         M @ x
     rate = 2 * 4096 * 4096 * 8 / ((time.perf_counter() - t0) / 3)
     del M, x
-    iters = 30.0
+    # dense applies per solve: the iteration count the GPU solve of the same workload took
+    # (tol 1e-6; 32^3: 24, 64^3 with one shared operator: 16), else 24
+    iters = float(REF_ITERS.get(name, 24))
     full = len(probs) == 1 and probs[0].N <= 4096
 
     def extrapolated(prob, seed):
@@ -642,8 +806,9 @@ def run_reference(args):
             full_solve(probs[0])
         else:
             O.G_rows(probs[0], W.sample_rows(probs[0].N, 1, seed=99))
-    t_steps, fp_iters = [], []
+    t_steps, fp_iters, elapsed = [], [], []
     for k in range(args.steps):
+        t0 = time.perf_counter()
         if full:
             t, it = full_solve(probs[0])
             fp_iters.append(it)
@@ -652,7 +817,8 @@ def run_reference(args):
             pick = rng.choice(len(probs), size=nsamp, replace=False)
             est = [extrapolated(probs[int(b)], seed=k) for b in pick]
             t_steps.append(statistics.mean(est) * len(probs))
-    t_step = statistics.mean(t_steps)
+        elapsed.append(time.perf_counter() - t0)
+    t_step = statistics.mean(t_steps)   # one whole-workload oracle solve (measured or extrapolated)
     v = len(probs) / t_step
     if full:
         sample = (f"full dense FP64 build of all {probs[0].N} rows + fixed point to {tol:g} "
@@ -666,7 +832,11 @@ def run_reference(args):
                   "scaled to all instances")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": 0, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": statistics.mean(elapsed) * 1e3, "higher_is_better": True,
+        "scaling": "weak",
+        "oracle_seconds_per_workload": {"value": t_step, "extrapolated": not full,
+                                        "note": "ms_per_step is the measured time of one bounded sample step; "
+                                                "value = instances / this time"},
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": name, "instances": len(probs), "N": probs[0].N if len(probs) == 1 else None,
                    "F": probs[0].freqs.F if len(probs) == 1 else None, "tol": tol},
@@ -687,6 +857,9 @@ def main():
     ap.add_argument("--far-prec", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--cpu-rows", type=int, default=16)
+    ap.add_argument("--refine", action="store_true", help="16-bit far field with refinement sweeps")
+    ap.add_argument("--compare-f32", action="store_true", help="also time one plain FP32 solve of the workload")
+    ap.add_argument("--residual-rows", type=int, default=32, help="oracle rows of the one-step residual")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", dest="tune", action="store_false")
     ap.add_argument("--requests", type=int, default=24, help="serve: requests in the stream")

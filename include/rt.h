@@ -186,6 +186,10 @@ typedef struct {
     int64_t peak_bytes;          /* largest device footprint during assembly (operator + ACA scratch) */
     int64_t aca_waves;           /* waves of admissible blocks the ACA ran in */
     int64_t apply_tensor_cores;  /* 1 if rt_apply runs on the tcgen05 multi-right-hand-side path */
+    int64_t assembly_terms;      /* H-matrix assembly: kernel terms evaluated (one direct or one reflected
+                                    value of the kernel at a point pair, all groups at once) */
+    int64_t assembly_depths;     /* H-matrix assembly: optical depths evaluated (one per direct term,
+                                    two per reflected term) */
 } rt_info;
 
 /* Fixed-point options (Section 1.3).  The iteration starts from T = T0 at

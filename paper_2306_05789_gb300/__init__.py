@@ -71,7 +71,7 @@ class RtInfo(ctypes.Structure):
                 ("apply_bytes", _c_i64), ("apply_flops", _c_i64), ("device_bytes", _c_i64),
                 ("ms_tree", _c_dbl), ("ms_near", _c_dbl), ("ms_aca", _c_dbl), ("ms_pack", _c_dbl),
                 ("ms_source", _c_dbl), ("peak_bytes", _c_i64), ("aca_waves", _c_i64),
-                ("apply_tensor_cores", _c_i64)]
+                ("apply_tensor_cores", _c_i64), ("assembly_terms", _c_i64), ("assembly_depths", _c_i64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -261,6 +261,21 @@ __device__ __forceinline__ void row_accumulate(const KernelParams& P, float (&ac
     }
 }
 
+// add this thread's counts to the work counters (one atomic per warp and counter)
+__device__ __forceinline__ void count_work(const KernelParams& P, unsigned terms, unsigned depths)
+{
+    if (!P.work) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        terms += __shfl_xor_sync(0xffffffffu, terms, o);
+        depths += __shfl_xor_sync(0xffffffffu, depths, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(P.work, (unsigned long long)terms);
+        atomicAdd(P.work + 1, (unsigned long long)depths);
+    }
+}
+
 template <int MG>
 __global__ void __launch_bounds__(kColRows) aca_col_kernel(KernelParams P, const AcaActive* __restrict__ act, int na,
                                                            int64_t nchunks, const int* __restrict__ jstar,
@@ -285,6 +300,7 @@ __global__ void __launch_bounds__(kColRows) aca_col_kernel(KernelParams P, const
 #pragma unroll
         for (int g = 0; g < MG; ++g) acc[g] = 0.f;
         const int t0 = P.vt_ptr[j], t1 = P.vt_ptr[j + 1];
+        unsigned n_terms = 0, n_depths = 0;
         for (int b0 = t0; b0 < t1; b0 += kColTets) {
             const int nt = min(kColTets, t1 - b0);
             __syncthreads();   // the previous batch's table is no longer read
@@ -318,6 +334,8 @@ __global__ void __launch_bounds__(kColRows) aca_col_kernel(KernelParams P, const
                     const Vec3<float> cen = {ce.x, ce.y, ce.z};
                     const int nd = dist2<float>(xi, cen) < ce.w ? 14 : 4;
                     const int nr = P.has_wall ? (dist2<float>(xb, cen) < ce.w ? 14 : 4) : 0;
+                    n_terms += nd + nr;
+                    n_depths += nd + 2 * nr;
                     // direct points first, then the mirror-reflected ones: two
                     // loops, so that lanes whose rules differ never run the
                     // direct and the reflected branch at the same step
@@ -343,6 +361,7 @@ __global__ void __launch_bounds__(kColRows) aca_col_kernel(KernelParams P, const
             for (int g = 0; g < MG; ++g)
                 if (g < P.G) buf[a.cbuf + (int64_t)g * a.m + pos] = acc[g];
         }
+        count_work(P, n_terms, n_depths);
     }
 }
 
@@ -651,7 +670,7 @@ struct RowItem {
 // handed out through a shared counter so that the few tetrahedra near x_i
 // (14-point rules) do not hold up a fixed partition.
 template <int MG>
-__global__ void __launch_bounds__(256) row_cluster_kernel(KernelParams P, const RowItem* __restrict__ items,
+__global__ void __launch_bounds__(256, MG <= 16 ? 2 : 1) row_cluster_kernel(KernelParams P, const RowItem* __restrict__ items,
                                                           const int* __restrict__ sub_tets,
                                                           const int* __restrict__ istar, float* __restrict__ out)
 {
@@ -667,6 +686,7 @@ __global__ void __launch_bounds__(256) row_cluster_kernel(KernelParams P, const 
     Vec3<float> xb = xi;
     if (P.has_wall) xb = mirror_point<float>(P, xi);
     const float inv4pi = (float)(1.0 / (4.0 * kPi));
+    unsigned n_terms = 0, n_depths = 0;
     for (;;) {
         const int t = atomicAdd(&s_next, 1);
         if (t >= it.ntet) break;
@@ -683,6 +703,8 @@ __global__ void __launch_bounds__(256) row_cluster_kernel(KernelParams P, const 
         const float lim = 4.f * diam * diam;
         const int nd = dist2<float>(xi, cen) < lim ? 14 : 4;
         const int nr = P.has_wall ? (dist2<float>(xb, cen) < lim ? 14 : 4) : 0;
+        n_terms += nd + nr;
+        n_depths += nd + 2 * nr;
         float a0[MG > 0 ? MG : 1], a1[MG > 0 ? MG : 1], a2[MG > 0 ? MG : 1], a3[MG > 0 ? MG : 1];
         if constexpr (MG > 0) {
 #pragma unroll
@@ -760,6 +782,7 @@ __global__ void __launch_bounds__(256) row_cluster_kernel(KernelParams P, const 
                 }
         }
     }
+    count_work(P, n_terms, n_depths);
     __syncthreads();
     for (int k = threadIdx.x; k < G * n; k += blockDim.x) {
         const int g = k / n, j = k - g * n;

@@ -362,6 +362,9 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
     kp.tvol64 = op.d_tvol64;
     kp.vt_ptr = op.d_vt_ptr;
     kp.vt_idx = op.d_vt_idx;
+    if ((rc = dev_alloc(op, &op.d_work, 2, err))) return rc;
+    RT_CUDA_TRY(cudaMemsetAsync(op.d_work, 0, 2 * sizeof(unsigned long long), s));
+    kp.work = op.d_work;
     if ((rc = assemble_setup_constants(op, err))) return rc;
 
     cudaEventRecord(e0, s);
@@ -397,6 +400,12 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
     RT_CUDA_TRY(cudaGetLastError());
     // statistics
     rt_info& I = op.info;
+    {
+        unsigned long long w[2] = {0, 0};
+        RT_CUDA_TRY(cudaMemcpy(w, op.d_work, sizeof(w), cudaMemcpyDeviceToHost));
+        I.assembly_terms = (int64_t)w[0];
+        I.assembly_depths = (int64_t)w[1];
+    }
     I.N = N;
     I.F = op.F;
     I.G = op.G;

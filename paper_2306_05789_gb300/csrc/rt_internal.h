@@ -65,6 +65,9 @@ struct KernelParams {
     const double* tvol64;
     const int* vt_ptr;
     const int* vt_idx;
+    // assembly work counters (may be null): [0] kernel terms evaluated (one direct or
+    // one reflected value e^{-c tau} / r^2 at a point pair), [1] optical depths
+    unsigned long long* work;
 };
 
 // A rectangular set of entries G_g[i0 + ii][j0 + jj], ii < ni, jj < nj, written
@@ -249,6 +252,7 @@ struct Operator {
     int tc_xal = 0;             // X columns of every cluster 16-byte aligned: X split once per apply
     void* tc_xsplit = nullptr;  // X high / low parts (BF16; then FP16 for an FP16 far field)
     int* tc_err = nullptr;
+    unsigned long long* d_work = nullptr;   // assembly work counters (KernelParams::work)
     // streamed tcgen05 apply (rt_tc2.cu; F = 64): swizzled operator images,
     // phase-1 tiles, phase-2 leaves with their stages and copy pieces
     int tc2 = 0;

@@ -27,6 +27,7 @@ def test_reference_arm_times_the_plain_method_in_full():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
     assert "no extrapolation" in cb["sample"]
+    assert d["oracle_seconds_per_workload"]["extrapolated"] is False
     assert d["e2e"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     mv = d["dense_matvec_fp64"]
@@ -38,3 +39,6 @@ def test_reference_arm_extrapolates_batches_from_sampled_instances():
     d = _run("--workload", "batch8")
     assert d["config"]["instances"] == 8 and d["value"] > 0
     assert "4 of 8 instances" in d["cpu_baseline"]["sample"]
+    # ms_per_step is the measured sample time, the extrapolated solve time has its own field
+    assert d["oracle_seconds_per_workload"]["extrapolated"] is True
+    assert d["ms_per_step"] < 600e3
