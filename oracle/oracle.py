@@ -83,6 +83,7 @@ def lib():
         _lib.or_optical_depth.argtypes = [P, P, P, i]
         _lib.or_optical_depth.restype = ctypes.c_double
         _lib.or_kernel_point.argtypes = [P, P, P, P, i, P, i, P, P]
+        _lib.or_source_hat.argtypes = [i, P, i, P, P, i, P, P, i, P, i, i, i, P, P]
     return _lib
 
 
@@ -256,6 +257,34 @@ def source_geometric(prob, rows=None, c=None, ngauss: int = 16, refine: int = 0,
     w = _wall_struct(prob.wall, R0)
     lib().or_source(N, _ptr(xyz), tri.shape[0], _ptr(tri), ctypes.byref(k), ctypes.byref(w), c.shape[0],
                     _ptr(c), ngauss, refine, rows.shape[0], _ptr(rows), _ptr(out))
+    return out
+
+
+def emitter_vertices(prob):
+    """The emitter-surface vertices (columns of the surface-to-volume matrix): the distinct
+    vertex ids of the emitter triangles, ascending."""
+    return np.unique(np.asarray(prob.emit_tri, dtype=np.int64).ravel()).astype(np.int32)
+
+
+def source_hat_rows(prob, rows, c=None, ngauss: int = 16, refine: int = 0, R0=None):
+    """Rows of the surface-to-volume matrix Sbar^E_{i,l} (Section 2: Q0 replaced by the P1 hat
+    function of emitter vertex l), geometric part per group: [len(rows), G, L], columns in
+    the order of emitter_vertices(prob)."""
+    if c is None:
+        c, _ = groups_of(prob.freqs)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    xyz = np.ascontiguousarray(prob.xyz, dtype=np.float64)
+    tri = np.ascontiguousarray(prob.emit_tri, dtype=np.int32)
+    sv = emitter_vertices(prob)
+    col = np.full(xyz.shape[0], -1, dtype=np.int32)
+    col[sv] = np.arange(sv.shape[0], dtype=np.int32)
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    L = sv.shape[0]
+    out = np.zeros((rows.shape[0], c.shape[0], L))
+    k = _kappa_struct(prob.kappa)
+    w = _wall_struct(prob.wall, R0)
+    lib().or_source_hat(xyz.shape[0], _ptr(xyz), tri.shape[0], _ptr(tri), _ptr(col), L, ctypes.byref(k),
+                        ctypes.byref(w), c.shape[0], _ptr(c), ngauss, refine, rows.shape[0], _ptr(rows), _ptr(out))
     return out
 
 

@@ -653,3 +653,147 @@ void or_kernel_point(const or_kappa* kap, const or_wall* wall, const double* x, 
         for (int g = 0; g < G; ++g) out_refl[g] = 0.0;
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* Surface-to-volume matrix Sbar^E_{i,l} (Section 2, last paragraph)    */
+/* ------------------------------------------------------------------ */
+/*
+ * The emitter source with Q0(y) replaced by the P1 hat function w_l(y) of
+ * emitter-surface vertex l, so that Sbar^E_i = sum_l Sbar^E_{i,l} Q0_l when
+ * Q0(y) = sum_l Q0_l w_l(y).  col[v] is the column of mesh vertex v (-1 if v
+ * is not an emitter vertex); out[r][g][l] (L columns) receives the geometric
+ * part per group, as or_source does, quadrature and limit rules unchanged:
+ * each quadrature point's value is split over the triangle's three vertices
+ * by its barycentric coordinates, and the limit value at a source point that
+ * is a vertex of the triangle goes to that vertex's column (w_l(x_i) = 1).
+ */
+void or_source_hat(int nv, const double* xyz, int ne, const int* tri, const int* col, int L, const or_kappa* kap,
+                   const or_wall* wall, int G, const double* c, int ngauss, int refine, int nrows, const int* rows,
+                   double* out)
+{
+    (void)nv;
+    gauss_t ga;
+    ga.n = ngauss;
+    or_gauss_legendre(ngauss, ga.t, ga.w);
+    double b3[9], w3[3], b7[21], w7[7];
+    or_tri_rule(3, b3, w3);
+    or_tri_rule(7, b7, w7);
+    int nsub = 1;
+    for (int l = 0; l < refine; ++l) nsub *= 4;
+    double* sub = (double*)malloc((size_t)nsub * 9 * sizeof(double));
+    {
+        double* cur = (double*)malloc(9 * sizeof(double));
+        memset(cur, 0, 9 * sizeof(double));
+        cur[0] = cur[4] = cur[8] = 1.0;
+        int cnt = 1;
+        for (int l = 0; l < refine; ++l) {
+            double* nxt = (double*)malloc((size_t)cnt * 4 * 9 * sizeof(double));
+            for (int s = 0; s < cnt; ++s) {
+                const double* P = cur + 9 * s;
+                double M[3][3][3];
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j)
+                        for (int d = 0; d < 3; ++d) M[i][j][d] = 0.5 * (P[3 * i + d] + P[3 * j + d]);
+                const double* tv[4][3] = {{&P[0], M[0][1], M[0][2]},
+                                          {M[0][1], &P[3], M[1][2]},
+                                          {M[0][2], M[1][2], &P[6]},
+                                          {M[1][2], M[0][2], M[0][1]}};
+                for (int ch = 0; ch < 4; ++ch)
+                    for (int k = 0; k < 3; ++k)
+                        for (int d = 0; d < 3; ++d) nxt[9 * (4 * s + ch) + 3 * k + d] = tv[ch][k][d];
+            }
+            free(cur);
+            cur = nxt;
+            cnt *= 4;
+        }
+        memcpy(sub, cur, (size_t)nsub * 9 * sizeof(double));
+        free(cur);
+    }
+
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int r = 0; r < nrows; ++r) {
+        int i = rows[r];
+        const double* xi = xyz + 3 * (size_t)i;
+        double xb[3] = {0, 0, 0};
+        int has_refl = wall && wall->present && wall->R0 != 0.0;
+        if (wall && wall->present) mirror(wall, xi, xb);
+        double* o = out + (size_t)r * G * L;
+        for (int k = 0; k < G * L; ++k) o[k] = 0.0;
+        for (int e = 0; e < ne; ++e) {
+            const int* te = tri + 3 * (size_t)e;
+            const double* V[3] = {xyz + 3 * (size_t)te[0], xyz + 3 * (size_t)te[1], xyz + 3 * (size_t)te[2]};
+            const int cl[3] = {col[te[0]], col[te[1]], col[te[2]]};
+            double e1[3], e2[3], nn[3];
+            for (int d = 0; d < 3; ++d) {
+                e1[d] = V[1][d] - V[0][d];
+                e2[d] = V[2][d] - V[0][d];
+            }
+            cross3(e1, e2, nn);
+            double area2 = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+            double area = 0.5 * area2;
+            for (int d = 0; d < 3; ++d) nn[d] /= area2;
+            double cen[3], diam = 0.0;
+            for (int d = 0; d < 3; ++d) cen[d] = (V[0][d] + V[1][d] + V[2][d]) / 3.0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = a + 1; b < 3; ++b) {
+                    double dd = sqrt(dist2(V[a], V[b]));
+                    if (dd > diam) diam = dd;
+                }
+            for (int term = 0; term < 2; ++term) {
+                if (term == 1 && !has_refl) break;
+                const double* src = term == 0 ? xi : xb;
+                double scale = term == 0 ? 1.0 : wall->R0;
+                int vloc = -1;
+                for (int k = 0; k < 3; ++k)
+                    if (dist2(src, V[k]) <= 1e-24) vloc = k;
+                if (vloc >= 0) {
+                    double ang = angle_at(V[vloc], V[(vloc + 1) % 3], V[(vloc + 2) % 3]);
+                    for (int g = 0; g < G; ++g) o[g * L + cl[vloc]] += scale * ang / (8.0 * OR_PI);
+                    continue;
+                }
+                double sd = (src[0] - V[0][0]) * nn[0] + (src[1] - V[0][1]) * nn[1] + (src[2] - V[0][2]) * nn[2];
+                double cm = sd < 0.0 ? -sd : 0.0;
+                if (cm <= 0.0) continue;
+                for (int s = 0; s < nsub; ++s) {
+                    const double* P = sub + 9 * s;
+                    const double* qb;
+                    const double* qw;
+                    int nq;
+                    if (refine == 0) {
+                        int nearp = sqrt(dist2(src, cen)) < 2.0 * diam;
+                        qb = nearp ? b7 : b3;
+                        qw = nearp ? w7 : w3;
+                        nq = nearp ? 7 : 3;
+                    } else {
+                        qb = b7;
+                        qw = w7;
+                        nq = 7;
+                    }
+                    for (int q = 0; q < nq; ++q) {
+                        double lam[3] = {0, 0, 0};
+                        for (int k = 0; k < 3; ++k)
+                            for (int d = 0; d < 3; ++d) lam[d] += qb[3 * q + k] * P[3 * k + d];
+                        double y[3] = {0, 0, 0};
+                        for (int d = 0; d < 3; ++d)
+                            for (int ee = 0; ee < 3; ++ee) y[ee] += lam[d] * V[d][ee];
+                        double r2 = dist2(src, y);
+                        double tau;
+                        if (term == 0) {
+                            tau = optical_depth(kap, xi, y, &ga);
+                        } else {
+                            double xp[3];
+                            reflection_point(wall, xb, y, xp);
+                            tau = optical_depth(kap, xi, xp, &ga) + optical_depth(kap, xp, y, &ga);
+                        }
+                        double geo = scale * area / (double)nsub * qw[q] * cm * cm / (r2 * r2) / (4.0 * OR_PI);
+                        for (int g = 0; g < G; ++g) {
+                            double v = geo * exp(-c[g] * tau);
+                            for (int k = 0; k < 3; ++k) o[g * L + cl[k]] += v * lam[k];
+                        }
+                    }
+                }
+            }
+        }
+    }
+    free(sub);
+}

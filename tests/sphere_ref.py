@@ -119,7 +119,7 @@ def _composite_gauss_square(npan, nq):
     return S.ravel(), T.ravel(), W2.ravel()
 
 
-def emitter_source_reference(x, kappa_kind, k0, amp, c, R0, npan=24, nq=10):
+def emitter_source_reference(x, kappa_kind, k0, amp, c, R0, npan=24, nq=10, q0=None):
     """Emitter source (without the intensity Q) at an interior point x of the unit cube,
     emitter = the face x = 0, reflective wall z = 0 (Example of Section 1.2, squared-cosine form):
 
@@ -133,6 +133,8 @@ def emitter_source_reference(x, kappa_kind, k0, amp, c, R0, npan=24, nq=10):
     x = np.asarray(x, dtype=np.float64)
     S, T, Wq = _composite_gauss_square(npan, nq)
     Y = np.stack([np.zeros_like(S), S, T], axis=1)
+    if q0 is not None:   # emitter coefficient Q0(y) on the face (weights the integrand)
+        Wq = Wq * q0(Y)
     d = x[0]
 
     def line_tau(a, b, zsign=1.0):

@@ -481,3 +481,34 @@ def test_explicit_group_map_equals_the_equivalent_bins():
     cg2, gidx2 = O.groups_of(fr2)
     np.testing.assert_array_equal(gidx2, gidx)
     np.testing.assert_array_equal(cg2, cg)
+
+
+# ---------------------------------------------------------------------------
+# the surface-to-volume matrix Sbar^E_{i,l} (Section 2, last paragraph)
+# ---------------------------------------------------------------------------
+def test_surface_to_volume_rows_sum_to_the_source():
+    """The surface P1 hat functions sum to 1, so sum_l Sbar^E_{i,l} is the source with Q0 = 1,
+    for every row, group and both terms (emitter vertices included)."""
+    p = W.cube_problem(6, W.sinprod_kappa(0.5), W.midpoint_freqs(3, albedo=0.3), R0=0.5)
+    rows = np.arange(p.N, dtype=np.int32)
+    H = O.source_hat_rows(p, rows)
+    np.testing.assert_allclose(H.sum(axis=2), O.source_geometric(p, rows), rtol=1e-13, atol=1e-16)
+    assert H.shape[2] == 36 and (H >= 0).all()
+
+
+@pytest.mark.parametrize("kind,amp", [(W.KAPPA_CONST, 0.0), (W.KAPPA_SINPROD, 0.5)])
+def test_surface_to_volume_rows_integrate_a_linear_emitter_coefficient(kind, amp):
+    """Q0(y) = 1 + 2 y_2 - y_3 is linear on the emitter face, so its P1 interpolation is exact
+    and sum_l Sbar^E_{i,l} Q0(y_l) is the source with that coefficient: checked against an
+    independent face integral weighted by Q0 (tests/sphere_ref.py), direct plus wall term."""
+    n, R0, c = 6, 0.5, 1.3
+    fr = W.Freqs(np.array([1.0]), np.array([1.0]), np.array([c]), np.array([0.3]))
+    p = W.cube_problem(n, W.Kappa(kind, 1.0, amp), fr, R0=R0)
+    verts = [i + n * j + n * n * k for (i, j, k) in [(2, 2, 2), (3, 1, 1), (1, 3, 4), (4, 4, 2)]]
+    H = O.source_hat_rows(p, np.array(verts, dtype=np.int32), refine=4)[:, 0, :]
+    sv = O.emitter_vertices(p)
+    q = 1.0 + 2.0 * p.xyz[sv, 1] - p.xyz[sv, 2]
+    for r, v in enumerate(verts):
+        ref = SR.emitter_source_reference(p.xyz[v], kind, 1.0, amp, c, R0,
+                                          q0=lambda Y: 1.0 + 2.0 * Y[:, 1] - Y[:, 2])
+        assert H[r] @ q == pytest.approx(ref, rel=1e-10)
