@@ -280,6 +280,54 @@ int rt_source(rt_operator* op, void* out, void* stream);
 int rt_eval_entries(rt_operator* op, int group, int64_t count, const int32_t* rows, const int32_t* cols,
                     double* out, void* stream);
 
+/* ---- the surface-to-volume matrix (Section 2, last paragraph; Section 2.1) --
+ * Sbar^E_{i,l} is the emitter source of Section 2 with the emitter coefficient
+ * Q0(y) replaced by the P1 hat function of emitter-surface vertex l (the
+ * distinct vertices of the problem's emitter triangles, in ascending vertex
+ * id).  For per-vertex coefficients Q0_l, Q0(y) = sum_l Q0_l w_l(y) and
+ * Sbar^E_{nu,i} = sum_l Sbar^E_{i,l} Q0_l, times the intensity B_nu(T_emit)
+ * (grey: sigma T_emit^4); with every Q0_l equal to the problem's Q0 this is
+ * rt_source.  One N x L matrix per kappa group (the optical depths use the
+ * group's scale), compressed like Gbar: a rectangular block tree of the
+ * operator's volume clusters against clusters of the emitter vertices, the
+ * operator's admissibility rule, partially pivoted ACA with the operator's
+ * tolerance on admissible blocks (a block that would need more than 32 terms
+ * stays dense), dense blocks elsewhere.  Every entry is evaluated once on the
+ * device during the build (FP32, the quadrature and limit rules of the
+ * source).  Needs an H-matrix operator with at most 16 groups and leaves of at
+ * most 64 rows. */
+typedef struct rt_source_op rt_source_op;
+
+typedef struct {
+    int64_t N, L, G;             /* rows, emitter vertices, kappa groups */
+    int64_t n_blocks, n_far, n_dense; /* blocks; far (block, group) pieces; dense blocks */
+    int64_t rank_sum, rank_max;
+    int64_t stored_entries;      /* all groups: sum r (m + n) + sum m n */
+    double compression;          /* 1 - stored_entries / (N L G) */
+    int64_t apply_bytes;         /* algorithmic bytes of one rt_apply_source */
+    int64_t device_bytes;
+    double ms_eval, ms_aca;      /* entry evaluation and compression times */
+} rt_source_info;
+
+/* Build the surface-to-volume operator of a built operator `op` (which must
+ * outlive it) on `stream`.  RT_EINVAL: dense operator, no emitter, more than
+ * 16 groups, leaves over 64 rows or G x L over the row buffer (200 KB of
+ * FP32); RT_ENOMEM; RT_ECUDA. */
+int rt_build_source_operator(rt_operator* op, void* stream, rt_source_op** out);
+
+/* Sizes and statistics; vertices (may be NULL): [L] vertex ids of the columns. */
+int rt_source_operator_info(const rt_source_op* s, rt_source_info* info, int32_t* vertices);
+
+/* out [F][N] (device floats, caller vertex order) = B_nu(T_emit) sum_l
+ * Sbar^E_{g(nu)}[i, l] Q0[l] for device coefficients Q0 [L] in the column
+ * order of rt_source_operator_info.  Asynchronous on `stream`; calls on one
+ * operator must be ordered (they share its scratch).  RT_EINVAL for null
+ * arguments, RT_ECUDA if a launch fails. */
+int rt_apply_source(rt_source_op* s, const float* Q0, float* out, void* stream);
+
+/* Release the surface-to-volume operator (synchronises the device). */
+void rt_source_free(rt_source_op* s);
+
 /* Diagnostic (no paper counterpart): the library's FP32 sin(2 pi x), used by
  * the sin-product kappa on the FP32 paths, for n device values x: lib_out[i]
  * receives it and ref_out[i] CUDA's sinpif(2 x[i]) for comparison.  All three

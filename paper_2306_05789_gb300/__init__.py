@@ -77,6 +77,16 @@ class RtInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class RtSourceInfo(ctypes.Structure):
+    _fields_ = [("N", _c_i64), ("L", _c_i64), ("G", _c_i64), ("n_blocks", _c_i64), ("n_far", _c_i64),
+                ("n_dense", _c_i64), ("rank_sum", _c_i64), ("rank_max", _c_i64), ("stored_entries", _c_i64),
+                ("compression", _c_dbl), ("apply_bytes", _c_i64), ("device_bytes", _c_i64), ("ms_eval", _c_dbl),
+                ("ms_aca", _c_dbl)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class RtSolveOpts(ctypes.Structure):
     _fields_ = [("tol", _c_dbl), ("max_iter", _c_int), ("check_every", _c_int), ("T0", _c_dbl), ("use_J0", _c_int),
                 ("use_graph", _c_int), ("refine_tol", _c_dbl)]
@@ -124,6 +134,7 @@ class RtSolveStats(ctypes.Structure):
 
 # every symbol declared in include/rt.h
 EXPORTS = ("rt_build_operator", "rt_operator_info", "rt_apply", "rt_apply_group", "rt_apply_noalloc", "rt_source", "rt_eval_entries",
+           "rt_build_source_operator", "rt_source_operator_info", "rt_apply_source", "rt_source_free",
            "rt_eval_sin2pi", "rt_solve_fixed_point", "rt_free", "rt_last_error", "rt_plan", "rt_build_batch",
            "rt_batch_info", "rt_batch_apply", "rt_solve_batch", "rt_batch_set_wait", "rt_batch_free",
            "rt_batch_last_error", "rt_server_create", "rt_submit", "rt_poll", "rt_server_info", "rt_server_free")
@@ -148,6 +159,11 @@ def lib():
     L.rt_source.argtypes = [_P, _P, _P]
     L.rt_eval_entries.argtypes = [_P, _c_int, _c_i64, _P, _P, _P, _P]
     L.rt_eval_sin2pi.argtypes = [_P, _P, _P, _c_i64, _P]
+    L.rt_build_source_operator.argtypes = [_P, _P, ctypes.POINTER(_P)]
+    L.rt_source_operator_info.argtypes = [_P, ctypes.POINTER(RtSourceInfo), _P]
+    L.rt_apply_source.argtypes = [_P, _P, _P, _P]
+    L.rt_source_free.argtypes = [_P]
+    L.rt_source_free.restype = None
     L.rt_solve_fixed_point.argtypes = [_P, ctypes.POINTER(RtSolveOpts), _P, _P, ctypes.POINTER(RtSolveStats), _P]
     L.rt_free.argtypes = [_P]
     L.rt_free.restype = None
@@ -314,6 +330,43 @@ def rt_build_operator(prob, hp: RtHparams, stream=None) -> Operator:
     _check(lib().rt_build_operator(ctypes.byref(args.s), ctypes.byref(hp), _stream_ptr(stream), ctypes.byref(out)))
     vec64 = hp.mode == RT_MODE_DENSE and hp.prec == RT_PREC_F64
     return Operator(out, args.xyz.shape[0], args.nu.shape[0], vec64)
+
+
+class SourceOperator:
+    """The surface-to-volume matrix Sbar^E_{i,l} of an operator (rt_build_source_operator)."""
+
+    def __init__(self, handle, op):
+        self.h = handle
+        self.op = op   # the operator must outlive this one
+        i = RtSourceInfo()
+        _check(lib().rt_source_operator_info(self.h, ctypes.byref(i), None))
+        self._info = i.as_dict()
+        self.vertices = np.zeros(self._info["L"], dtype=np.int32)
+        _check(lib().rt_source_operator_info(self.h, ctypes.byref(i), _ptr(self.vertices)))
+
+    def info(self) -> dict:
+        return dict(self._info)
+
+    def apply(self, Q0, out, stream=None):
+        """rt_apply_source: out [F, N] = B_nu(T_emit) Sbar^E_g Q0 for device Q0 [L] (float32)."""
+        _check(lib().rt_apply_source(self.h, _P(Q0.data_ptr()), _P(out.data_ptr()), _stream_ptr(stream)))
+
+    def free(self):
+        if self.h:
+            lib().rt_source_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def rt_build_source_operator(op: "Operator", stream=None) -> SourceOperator:
+    out = _P()
+    _check(lib().rt_build_source_operator(op.h, _stream_ptr(stream), ctypes.byref(out)))
+    return SourceOperator(out, op)
 
 
 def rt_eval_sin2pi(x, lib_out, ref_out, stream=None):

@@ -16,8 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librt.so")
-SOURCES = ["rt_plan.cpp", "rt_assemble.cu", "rt_hmatvec.cu", "rt_tc.cu", "rt_tc2.cu", "rt_batch.cu", "rt_serve.cu",
-           "rt_vmm.cu", "rt_solve.cu", "rt_capi.cu"]
+SOURCES = ["rt_plan.cpp", "rt_assemble.cu", "rt_hmatvec.cu", "rt_tc.cu", "rt_tc2.cu", "rt_srcop.cu", "rt_batch.cu",
+           "rt_serve.cu", "rt_vmm.cu", "rt_solve.cu", "rt_capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1693,6 +1693,149 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
     return RT_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Rows of the surface-to-volume matrix Sbar^E_{i,l} (Section 2, last
+// paragraph): the emitter source with Q0 replaced by the P1 hat function of
+// emitter vertex l.  Each quadrature value of a triangle is split over the
+// triangle's three vertices by its barycentric weights; a source point that is
+// a vertex of the triangle gives that vertex the limit (angle)/(8 pi).  One CTA
+// per row, threads over the emitter triangles, the row [G][L] accumulated in
+// shared memory (float atomics: the summation order is not fixed).
+// col_of[v] = column (surface tree order) of tree vertex v, -1 off the emitter.
+// out[g * gstride + (i - row0) * L + l], rows i in [row0, row0 + nrows).
+// ---------------------------------------------------------------------------
+template <int MG>
+__global__ void __launch_bounds__(256) srcop_rows_kernel(KernelParams P, int n_emit, const int4* __restrict__ emit,
+                                                         const int* __restrict__ col_of, int L, int row0, int nrows,
+                                                         float* __restrict__ out, int64_t gstride)
+{
+    extern __shared__ float srow[];   // [G][L]
+    const int G = P.G;
+    const float inv4pi = (float)(1.0 / (4.0 * kPi));
+    for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const int i = row0 + r;
+        __syncthreads();
+        for (int k = threadIdx.x; k < G * L; k += blockDim.x) srow[k] = 0.f;
+        __syncthreads();
+        const Vec3<float> xi = load_xyz<float>(P, i);
+        Vec3<float> xb = xi;
+        bool on_wall = false;
+        if (P.has_wall) {
+            xb = mirror_point<float>(P, xi);
+            on_wall = dist2<float>(xi, xb) <= 1e-20f;
+        }
+        for (int e = threadIdx.x; e < n_emit; e += blockDim.x) {
+            const int4 tv = emit[e];
+            const int cl[3] = {col_of[tv.x], col_of[tv.y], col_of[tv.z]};
+            const Vec3<float> V0 = load_xyz<float>(P, tv.x), V1 = load_xyz<float>(P, tv.y),
+                              V2 = load_xyz<float>(P, tv.z);
+            const Vec3<float> e1 = {V1.x - V0.x, V1.y - V0.y, V1.z - V0.z};
+            const Vec3<float> e2 = {V2.x - V0.x, V2.y - V0.y, V2.z - V0.z};
+            Vec3<float> nn = {e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x};
+            const float a2 = sqrtf(nn.x * nn.x + nn.y * nn.y + nn.z * nn.z);
+            nn.x /= a2;
+            nn.y /= a2;
+            nn.z /= a2;
+            const float area = 0.5f * a2;
+            const Vec3<float> cen = {(V0.x + V1.x + V2.x) / 3.f, (V0.y + V1.y + V2.y) / 3.f, (V0.z + V1.z + V2.z) / 3.f};
+            float diam2 = fmaxf(fmaxf(dist2<float>(V0, V1), dist2<float>(V0, V2)), dist2<float>(V1, V2));
+            const int vloc = tv.x == i ? 0 : (tv.y == i ? 1 : (tv.z == i ? 2 : -1));
+            float a[3][MG];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int g = 0; g < MG; ++g) a[k][g] = 0.f;
+            for (int term = 0; term < 2; ++term) {
+                if (term == 1 && !P.has_wall) break;
+                const Vec3<float> src = term == 0 ? xi : xb;
+                const float scale = term == 0 ? 1.f : (float)P.R0;
+                if (vloc >= 0 && (term == 0 || on_wall)) {
+                    const Vec3<float> A = vloc == 0 ? V0 : (vloc == 1 ? V1 : V2);
+                    const Vec3<float> B = vloc == 0 ? V1 : (vloc == 1 ? V2 : V0);
+                    const Vec3<float> Cc = vloc == 0 ? V2 : (vloc == 1 ? V0 : V1);
+                    const Vec3<float> u = {B.x - A.x, B.y - A.y, B.z - A.z}, v = {Cc.x - A.x, Cc.y - A.y, Cc.z - A.z};
+                    float cs = (u.x * v.x + u.y * v.y + u.z * v.z) /
+                               sqrtf((u.x * u.x + u.y * u.y + u.z * u.z) * (v.x * v.x + v.y * v.y + v.z * v.z));
+                    cs = fminf(1.f, fmaxf(-1.f, cs));
+                    const float lim = scale * acosf(cs) * (float)(1.0 / (8.0 * kPi));
+#pragma unroll
+                    for (int g = 0; g < MG; ++g) a[vloc][g] += lim;
+                    continue;
+                }
+                const float sd = (src.x - V0.x) * nn.x + (src.y - V0.y) * nn.y + (src.z - V0.z) * nn.z;
+                if (!(sd < 0.f)) continue;
+                const float cm = -sd;
+                const bool nearp = dist2<float>(src, cen) < 4.f * diam2;
+                const int q0 = nearp ? 3 : 0, nq = nearp ? 7 : 3;
+                for (int q = 0; q < nq; ++q) {
+                    const float b[3] = {(float)c_tri_b[3 * (q0 + q)], (float)c_tri_b[3 * (q0 + q) + 1],
+                                        (float)c_tri_b[3 * (q0 + q) + 2]};
+                    const Vec3<float> y = {b[0] * V0.x + b[1] * V1.x + b[2] * V2.x, b[0] * V0.y + b[1] * V1.y + b[2] * V2.y,
+                                           b[0] * V0.z + b[1] * V1.z + b[2] * V2.z};
+                    const float r2 = dist2<float>(src, y);
+                    float tau;
+                    if (term == 0) {
+                        tau = optical_depth<float>(P, xi, y);
+                    } else {
+                        const Vec3<float> xp = wall_point<float>(P, xb, y);
+                        tau = optical_depth<float>(P, xi, xp) + optical_depth<float>(P, xp, y);
+                    }
+                    const float geo = scale * area * (float)c_tri_w[q0 + q] * cm * cm / (r2 * r2) * inv4pi;
+#pragma unroll
+                    for (int g = 0; g < MG; ++g) {
+                        if (g < G) {
+                            const float v = geo * expf(-P.cf[g] * tau);
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) a[k][g] += v * b[k];
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < MG; ++g)
+                if (g < G)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        if (cl[k] >= 0) atomicAdd(srow + g * L + cl[k], a[k][g]);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < G * L; k += blockDim.x) {
+            const int g = k / L, l = k - g * L;
+            out[g * gstride + (int64_t)r * L + l] = srow[k];
+        }
+    }
+}
+
+int srcop_eval_rows(Operator& op, const int* col_of, int L, int row0, int nrows, float* out, int64_t gstride,
+                    cudaStream_t s, std::string& err)
+{
+    const size_t smem = sizeof(float) * (size_t)op.G * L;
+    if (smem > 200 * 1024) {
+        err = "surface-to-volume operator: G x L too large for one row in shared memory";
+        return RT_EINVAL;
+    }
+    const int grid = std::max(1, std::min(nrows, 152 * 8));
+#define RT_SRC_ROWS(MG)                                                                                        \
+    do {                                                                                                       \
+        RT_CUDA_TRY(cudaFuncSetAttribute(srcop_rows_kernel<MG>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                         (int)smem));                                                          \
+        srcop_rows_kernel<MG><<<grid, 256, smem, s>>>(op.kp, op.n_emit, op.d_emit, col_of, L, row0, nrows, out, \
+                                                      gstride);                                                \
+    } while (0)
+    if (op.G <= 1) RT_SRC_ROWS(1);
+    else if (op.G <= 4) RT_SRC_ROWS(4);
+    else if (op.G <= 8) RT_SRC_ROWS(8);
+    else if (op.G <= 16) RT_SRC_ROWS(16);
+    else {
+        err = "surface-to-volume operator: at most 16 kappa groups";
+        return RT_EINVAL;
+    }
+#undef RT_SRC_ROWS
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
 // diagnostic: the library's FP32 sin(2 pi x) beside CUDA's sinpif(2x)
 __global__ void sin2pi_probe(const float* __restrict__ x, float* __restrict__ lib, float* __restrict__ ref, int64_t n)
 {

@@ -210,6 +210,7 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
     op.c.assign(Fq.c, Fq.c + Fq.F);
     op.albedo.assign(Fq.albedo, Fq.albedo + Fq.F);
     if ((rc = group_channels(op, Fq, H->kappa_bins, err))) return rc;
+    op.q0 = P->Q0;
     op.Q.assign(Fq.F, 0.0);
     for (int f = 0; f < Fq.F; ++f)
         op.Q[f] = P->grey ? P->Q0 * 6.493939402266829 * std::pow(P->T_emit, 4.0) : P->Q0 * planck_host(Fq.nu[f], P->T_emit);

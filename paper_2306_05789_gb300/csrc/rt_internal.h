@@ -163,6 +163,7 @@ struct Operator {
     KernelParams kp{};
     // frequencies (host copies) and the group of each frequency
     std::vector<double> nu, w, c, albedo, Q;
+    double q0 = 0.0;            // the problem's emitter coefficient Q0 (Q[f] = q0 B_nu(T_emit))
     std::vector<int> fgroup;
     std::vector<double> gc;     // group scales
     std::vector<double> fscale; // per channel c_f / c_{g(f)} (1 unless channels are binned)
@@ -294,6 +295,9 @@ int apply_noalloc(Operator& op, const void* X, void* Y, cudaStream_t s, std::str
 size_t apply_noalloc_limit();
 int tc_prepare(Operator& op, std::string& err);
 int eval_sin2pi(const float* x, float* lib, float* ref, int64_t n, cudaStream_t s, std::string& err);
+// rows [row0, row0 + nrows) (tree order) of the surface-to-volume matrix, [G][nrows][L] at out (gstride per group)
+int srcop_eval_rows(Operator& op, const int* col_of, int L, int row0, int nrows, float* out, int64_t gstride,
+                    cudaStream_t s, std::string& err);
 int tc_apply(Operator& op, const float* X, float* Y, cudaStream_t s, std::string& err);
 int tc2_prepare(Operator& op, std::string& err);
 int tc2_apply(Operator& op, const float* X, float* Y, cudaStream_t s, std::string& err);
