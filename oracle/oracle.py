@@ -56,9 +56,15 @@ class _Kappa(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("k0", ctypes.c_double), ("amp", ctypes.c_double)]
 
 
+MAX_WALLS = 3
+
+
+class _Plane(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_double * 3), ("n", ctypes.c_double * 3), ("R0", ctypes.c_double)]
+
+
 class _Wall(ctypes.Structure):
-    _fields_ = [("present", ctypes.c_int), ("p", ctypes.c_double * 3), ("n", ctypes.c_double * 3),
-                ("R0", ctypes.c_double)]
+    _fields_ = [("n", ctypes.c_int), ("corner", ctypes.c_int), ("w", _Plane * MAX_WALLS)]
 
 
 _lib = None
@@ -95,19 +101,34 @@ def _kappa_struct(kappa) -> _Kappa:
     return _Kappa(int(kappa.kind), float(kappa.k0), float(kappa.amp))
 
 
-def _wall_struct(wall, R0_override: Optional[float] = None) -> _Wall:
+def problem_walls(prob):
+    """The problem's planar reflective walls (first wall, then any further ones)."""
+    walls = [] if getattr(prob, "wall", None) is None else [prob.wall]
+    return walls + list(getattr(prob, "more_walls", ()) or ())
+
+
+def _wall_struct(walls, R0_override: Optional[float] = None, corner: bool = False) -> _Wall:
+    """walls: None, one wall, or a list of walls (each with p, n, R0)."""
     w = _Wall()
-    if wall is None:
-        w.present = 0
-        return w
-    w.present = 1
-    n = np.asarray(wall.n, dtype=np.float64)
-    n = n / np.linalg.norm(n)
-    for d in range(3):
-        w.p[d] = float(wall.p[d])
-        w.n[d] = float(n[d])
-    w.R0 = float(wall.R0 if R0_override is None else R0_override)
+    if walls is None:
+        walls = []
+    elif not isinstance(walls, (list, tuple)):
+        walls = [walls]
+    assert len(walls) <= MAX_WALLS
+    w.n = len(walls)
+    w.corner = 1 if corner else 0
+    for k, wl in enumerate(walls):
+        n = np.asarray(wl.n, dtype=np.float64)
+        n = n / np.linalg.norm(n)
+        for d in range(3):
+            w.w[k].p[d] = float(wl.p[d])
+            w.w[k].n[d] = float(n[d])
+        w.w[k].R0 = float(wl.R0 if R0_override is None else R0_override)
     return w
+
+
+def _prob_walls(prob, R0_override=None) -> _Wall:
+    return _wall_struct(problem_walls(prob), R0_override, bool(getattr(prob, "corner", False)))
 
 
 # ---------------------------------------------------------------------------
@@ -147,11 +168,12 @@ def optical_depth(kappa, a, b, ngauss: int = 16) -> float:
     return lib().or_optical_depth(ctypes.byref(k), _ptr(a), _ptr(b), ngauss)
 
 
-def kernel_point(kappa, wall, x, y, c, ngauss: int = 16):
-    """(direct[G], reflected[G]) kernel values at the point pair (x, y)."""
+def kernel_point(kappa, wall, x, y, c, ngauss: int = 16, corner: bool = False):
+    """(direct[G], reflected[G]) kernel values at the point pair (x, y); reflected = the sum
+    of every wall's term (and the corner terms).  wall: None, a wall or a list of walls."""
     c = np.ascontiguousarray(c, dtype=np.float64)
     k = _kappa_struct(kappa)
-    w = _wall_struct(wall)
+    w = _wall_struct(wall, corner=corner)
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64)
     d = np.zeros(c.shape[0])
@@ -221,7 +243,7 @@ def G_rows(prob, rows, c=None, ngauss: int = 16, refine: int = 0, R0=None, momen
     out = np.zeros((rows.shape[0], G, N))
     mom = np.zeros((rows.shape[0], G, 4)) if moments else None
     k = _kappa_struct(prob.kappa)
-    w = _wall_struct(prob.wall, R0)
+    w = _prob_walls(prob, R0)
     lib().or_G_rows(N, _ptr(xyz), tet.shape[0], _ptr(tet), ctypes.byref(k), ctypes.byref(w), G, _ptr(c),
                     ngauss, refine, rows.shape[0], _ptr(rows), _ptr(out),
                     _ptr(mom) if moments else None)
@@ -237,7 +259,7 @@ def G_entry(prob, i: int, j: int, c=None, ngauss: int = 16, R0=None):
     tet = np.ascontiguousarray(prob.tet, dtype=np.int32)
     out = np.zeros(c.shape[0])
     k = _kappa_struct(prob.kappa)
-    w = _wall_struct(prob.wall, R0)
+    w = _prob_walls(prob, R0)
     lib().or_G_entry(xyz.shape[0], _ptr(xyz), tet.shape[0], _ptr(tet), ctypes.byref(k), ctypes.byref(w),
                      c.shape[0], _ptr(c), ngauss, int(i), int(j), _ptr(out))
     return out
@@ -254,7 +276,7 @@ def source_geometric(prob, rows=None, c=None, ngauss: int = 16, refine: int = 0,
     rows = np.arange(N, dtype=np.int32) if rows is None else np.ascontiguousarray(rows, dtype=np.int32)
     out = np.zeros((rows.shape[0], c.shape[0]))
     k = _kappa_struct(prob.kappa)
-    w = _wall_struct(prob.wall, R0)
+    w = _prob_walls(prob, R0)
     lib().or_source(N, _ptr(xyz), tri.shape[0], _ptr(tri), ctypes.byref(k), ctypes.byref(w), c.shape[0],
                     _ptr(c), ngauss, refine, rows.shape[0], _ptr(rows), _ptr(out))
     return out
@@ -282,7 +304,7 @@ def source_hat_rows(prob, rows, c=None, ngauss: int = 16, refine: int = 0, R0=No
     L = sv.shape[0]
     out = np.zeros((rows.shape[0], c.shape[0], L))
     k = _kappa_struct(prob.kappa)
-    w = _wall_struct(prob.wall, R0)
+    w = _prob_walls(prob, R0)
     lib().or_source_hat(xyz.shape[0], _ptr(xyz), tri.shape[0], _ptr(tri), _ptr(col), L, ctypes.byref(k),
                         ctypes.byref(w), c.shape[0], _ptr(c), ngauss, refine, rows.shape[0], _ptr(rows), _ptr(out))
     return out

@@ -45,11 +45,23 @@ typedef struct {
     double k0, amp;
 } or_kappa;
 
+/* planar reflective walls: a point p of the plane, the unit OUTWARD normal n,
+ * the reflection coefficient R0.  Each wall contributes the single-reflection
+ * term of Section 2 (one reflection point per wall, Hypothesis H1); with
+ * corner != 0 every pair of perpendicular walls also contributes the path that
+ * reflects on both (the double image of x), which the identity with the
+ * fourfold mirrored domain needs. */
+#define OR_MAX_WALLS 3
 typedef struct {
-    int present;       /* 0: no reflective wall */
-    double p[3];       /* a point of the wall plane */
-    double n[3];       /* unit outward normal of the wall */
-    double R0;         /* reflection coefficient R^0 */
+    double p[3];
+    double n[3];
+    double R0;
+} or_plane;
+
+typedef struct {
+    int n;             /* walls (0 .. OR_MAX_WALLS) */
+    int corner;        /* also the double reflections at perpendicular walls */
+    or_plane w[OR_MAX_WALLS];
 } or_wall;
 
 /* ------------------------------------------------------------------ */
@@ -193,17 +205,22 @@ double or_optical_depth(const or_kappa* k, const double* a, const double* b, int
 /* ------------------------------------------------------------------ */
 /* Wall geometry: mirror image xbar and reflection point x'             */
 /* ------------------------------------------------------------------ */
-static void mirror(const or_wall* W, const double* x, double* xb)
+static void mirror(const or_plane* W, const double* x, double* xb)
 {
     double s = (x[0] - W->p[0]) * W->n[0] + (x[1] - W->p[1]) * W->n[1] + (x[2] - W->p[2]) * W->n[2];
     for (int d = 0; d < 3; ++d) xb[d] = x[d] - 2.0 * s * W->n[d];
 }
 
-/* x' = the point where the segment [xbar, y] meets the wall plane. */
-static void reflection_point(const or_wall* W, const double* xb, const double* y, double* xp)
+/* signed distance of a point from the plane (positive outside) */
+static double side(const or_plane* W, const double* x)
 {
-    double sb = (xb[0] - W->p[0]) * W->n[0] + (xb[1] - W->p[1]) * W->n[1] + (xb[2] - W->p[2]) * W->n[2];
-    double sy = (y[0] - W->p[0]) * W->n[0] + (y[1] - W->p[1]) * W->n[1] + (y[2] - W->p[2]) * W->n[2];
+    return (x[0] - W->p[0]) * W->n[0] + (x[1] - W->p[1]) * W->n[1] + (x[2] - W->p[2]) * W->n[2];
+}
+
+/* x' = the point where the segment [xbar, y] meets the wall plane. */
+static void reflection_point(const or_plane* W, const double* xb, const double* y, double* xp)
+{
+    double sb = side(W, xb), sy = side(W, y);
     /* xbar lies on the outer side (sb >= 0), y on the inner side (sy < 0) */
     double den = sb - sy;
     double t = (den > 0.0) ? sb / den : 0.0;
@@ -216,27 +233,92 @@ static double dist2(const double* a, const double* b)
     return dx * dx + dy * dy + dz * dz;
 }
 
-/* direct kernel without the group scale:  kappa(y) e^{-c tau}/(4 pi r^2),
- * returned per group in out[g]; tau is computed once and scaled by c_g. */
-static void direct_kernel(const or_kappa* k, const double* x, const double* y, const gauss_t* ga,
-                          int G, const double* c, double* out)
+/* The terms of the kernel at a source vertex x: 0 the direct path; then one
+ * reflection on each wall with R0 != 0 (source point = the mirror image of x,
+ * weight R0); then, with corner != 0, one path reflecting on both walls of
+ * every perpendicular pair (source point = the double image, weight
+ * R0_a R0_b).  Returns the number of terms. */
+typedef struct {
+    int kind, a, b;    /* 0 direct, 1 wall a, 2 walls a and b */
+    double src[3];     /* source point of the term */
+    double scale;      /* its weight */
+} or_term;
+
+static int or_terms(const or_wall* W, const double* x, or_term* T)
 {
-    double r2 = dist2(x, y);
-    double tau = optical_depth(k, x, y, ga);
-    double ky = or_kappa_at(k, y);
-    for (int g = 0; g < G; ++g) out[g] = c[g] * ky * exp(-c[g] * tau) / (4.0 * OR_PI * r2);
+    int n = 0;
+    T[n].kind = 0;
+    T[n].a = T[n].b = -1;
+    for (int d = 0; d < 3; ++d) T[n].src[d] = x[d];
+    T[n].scale = 1.0;
+    ++n;
+    if (!W) return n;
+    for (int a = 0; a < W->n; ++a) {
+        if (W->w[a].R0 == 0.0) continue;
+        T[n].kind = 1;
+        T[n].a = a;
+        T[n].b = -1;
+        mirror(&W->w[a], x, T[n].src);
+        T[n].scale = W->w[a].R0;
+        ++n;
+    }
+    if (W->corner)
+        for (int a = 0; a < W->n; ++a)
+            for (int b = a + 1; b < W->n; ++b) {
+                const or_plane *A = &W->w[a], *B = &W->w[b];
+                double dot = A->n[0] * B->n[0] + A->n[1] * B->n[1] + A->n[2] * B->n[2];
+                if (fabs(dot) > 1e-12 || A->R0 == 0.0 || B->R0 == 0.0) continue;
+                double xa[3];
+                mirror(A, x, xa);
+                T[n].kind = 2;
+                T[n].a = a;
+                T[n].b = b;
+                mirror(B, xa, T[n].src);
+                T[n].scale = A->R0 * B->R0;
+                ++n;
+            }
+    return n;
 }
 
-/* reflected kernel: R0 kappa(y) e^{-c (tau(x,x')+tau(x',y))} / (4 pi |xbar-y|^2) */
-static void reflected_kernel(const or_kappa* k, const or_wall* W, const double* x, const double* xb,
-                             const double* y, const gauss_t* ga, int G, const double* c, double* out)
+/* optical depth of the term's physical path from x to y */
+static double term_tau(const or_kappa* k, const or_wall* W, const or_term* T, const double* x, const double* y,
+                       const gauss_t* ga)
 {
-    double xp[3];
-    reflection_point(W, xb, y, xp);
-    double rb2 = dist2(xb, y);
-    double tau = optical_depth(k, x, xp, ga) + optical_depth(k, xp, y, ga);
+    if (T->kind == 0) return optical_depth(k, x, y, ga);
+    if (T->kind == 1) {
+        double xp[3];
+        reflection_point(&W->w[T->a], T->src, y, xp);
+        return optical_depth(k, x, xp, ga) + optical_depth(k, xp, y, ga);
+    }
+    /* two perpendicular walls: the straight line from y to the double image
+     * crosses both planes; the plane crossed first (nearer y) holds the last
+     * reflection point Q, and the crossing of the other plane, mirrored back in
+     * the first one, is the first reflection point P: x -> P -> Q -> y */
+    const or_plane *A = &W->w[T->a], *B = &W->w[T->b];
+    const double* z = T->src;
+    double sya = side(A, y), sza = side(A, z), syb = side(B, y), szb = side(B, z);
+    double ta = sya / (sya - sza), tb = syb / (syb - szb);
+    const or_plane *first = ta <= tb ? A : B, *second = ta <= tb ? B : A;
+    double t1 = ta <= tb ? ta : tb, t2 = ta <= tb ? tb : ta;
+    double Q[3], U[3], P[3];
+    for (int d = 0; d < 3; ++d) {
+        Q[d] = y[d] + t1 * (z[d] - y[d]);
+        U[d] = y[d] + t2 * (z[d] - y[d]);
+    }
+    (void)second;
+    mirror(first, U, P);
+    return optical_depth(k, x, P, ga) + optical_depth(k, P, Q, ga) + optical_depth(k, Q, y, ga);
+}
+
+/* kernel value of one term at (x, y) per group:
+ * scale c_g kappa(y) e^{-c_g tau} / (4 pi |src - y|^2) */
+static void term_kernel(const or_kappa* k, const or_wall* W, const or_term* T, const double* x, const double* y,
+                        const gauss_t* ga, int G, const double* c, double* out)
+{
+    double r2 = dist2(T->src, y);
+    double tau = term_tau(k, W, T, x, y, ga);
     double ky = or_kappa_at(k, y);
-    for (int g = 0; g < G; ++g) out[g] = W->R0 * c[g] * ky * exp(-c[g] * tau) / (4.0 * OR_PI * rb2);
+    for (int g = 0; g < G; ++g) out[g] = T->scale * c[g] * ky * exp(-c[g] * tau) / (4.0 * OR_PI * r2);
 }
 
 /* ------------------------------------------------------------------ */
@@ -338,8 +420,8 @@ void or_G_rows(int nv, const double* xyz, int nt, const int* tet, const or_kappa
 #pragma omp parallel for schedule(dynamic, 1)
     for (int r = 0; r < nrows; ++r) {
         const double* xi = xyz + 3 * (size_t)rows[r];
-        double xb[3] = {0, 0, 0};
-        if (wall && wall->present) mirror(wall, xi, xb);
+        or_term terms[1 + OR_MAX_WALLS + 3];
+        const int nterm = or_terms(wall, xi, terms);
         double* row = out + (size_t)r * G * nv;
         memset(row, 0, sizeof(double) * (size_t)G * nv);
         double* mrow = mom ? mom + (size_t)r * G * 4 : NULL;
@@ -353,9 +435,8 @@ void or_G_rows(int nv, const double* xyz, int nt, const int* tet, const or_kappa
             double cen[3];
             for (int d = 0; d < 3; ++d) cen[d] = 0.25 * (V[0][d] + V[1][d] + V[2][d] + V[3][d]);
             double diam = tet_diam(V);
-            for (int term = 0; term < 2; ++term) {
-                if (term == 1 && !(wall && wall->present && wall->R0 != 0.0)) break;
-                const double* src = term == 0 ? xi : xb;
+            for (int term = 0; term < nterm; ++term) {
+                const double* src = terms[term].src;
                 for (int s = 0; s < nsub; ++s) {
                     const double* P = sub + 16 * s;
                     const double* qb;
@@ -380,10 +461,7 @@ void or_G_rows(int nv, const double* xyz, int nt, const int* tet, const or_kappa
                         double y[3] = {0, 0, 0};
                         for (int d = 0; d < 4; ++d)
                             for (int e = 0; e < 3; ++e) y[e] += lam[d] * V[d][e];
-                        if (term == 0)
-                            direct_kernel(kap, xi, y, &ga, G, c, kv);
-                        else
-                            reflected_kernel(kap, wall, xi, xb, y, &ga, G, c, kv);
+                        term_kernel(kap, wall, &terms[term], xi, y, &ga, G, c, kv);
                         double wq = subvol * qw[q];
                         for (int g = 0; g < G; ++g) {
                             double val = wq * kv[g];
@@ -417,8 +495,8 @@ void or_G_entry(int nv, const double* xyz, int nt, const int* tet, const or_kapp
     or_tet_rule(4, b4, w4);
     or_tet_rule(14, b14, w14);
     const double* xi = xyz + 3 * (size_t)i;
-    double xb[3] = {0, 0, 0};
-    if (wall && wall->present) mirror(wall, xi, xb);
+    or_term terms[1 + OR_MAX_WALLS + 3];
+    const int nterm = or_terms(wall, xi, terms);
     for (int g = 0; g < G; ++g) out[g] = 0.0;
     double kv[64];
     for (int t = 0; t < nt; ++t) {
@@ -433,9 +511,9 @@ void or_G_entry(int nv, const double* xyz, int nt, const int* tet, const or_kapp
         double cen[3];
         for (int d = 0; d < 3; ++d) cen[d] = 0.25 * (V[0][d] + V[1][d] + V[2][d] + V[3][d]);
         double diam = tet_diam(V);
-        /* direct term */
-        {
-            int nearp = sqrt(dist2(xi, cen)) < 2.0 * diam;
+        /* every term: the direct one, then each reflection */
+        for (int term = 0; term < nterm; ++term) {
+            int nearp = sqrt(dist2(terms[term].src, cen)) < 2.0 * diam;
             const double* qb = nearp ? b14 : b4;
             const double* qw = nearp ? w14 : w4;
             int nq = nearp ? 14 : 4;
@@ -443,21 +521,7 @@ void or_G_entry(int nv, const double* xyz, int nt, const int* tet, const or_kapp
                 double y[3] = {0, 0, 0};
                 for (int d = 0; d < 4; ++d)
                     for (int e = 0; e < 3; ++e) y[e] += qb[4 * q + d] * V[d][e];
-                direct_kernel(kap, xi, y, &ga, G, c, kv);
-                for (int g = 0; g < G; ++g) out[g] += vol * qw[q] * kv[g] * qb[4 * q + loc];
-            }
-        }
-        /* reflected term */
-        if (wall && wall->present && wall->R0 != 0.0) {
-            int nearp = sqrt(dist2(xb, cen)) < 2.0 * diam;
-            const double* qb = nearp ? b14 : b4;
-            const double* qw = nearp ? w14 : w4;
-            int nq = nearp ? 14 : 4;
-            for (int q = 0; q < nq; ++q) {
-                double y[3] = {0, 0, 0};
-                for (int d = 0; d < 4; ++d)
-                    for (int e = 0; e < 3; ++e) y[e] += qb[4 * q + d] * V[d][e];
-                reflected_kernel(kap, wall, xi, xb, y, &ga, G, c, kv);
+                term_kernel(kap, wall, &terms[term], xi, y, &ga, G, c, kv);
                 for (int g = 0; g < G; ++g) out[g] += vol * qw[q] * kv[g] * qb[4 * q + loc];
             }
         }
@@ -550,9 +614,8 @@ void or_source(int nv, const double* xyz, int ne, const int* tri, const or_kappa
     for (int r = 0; r < nrows; ++r) {
         int i = rows[r];
         const double* xi = xyz + 3 * (size_t)i;
-        double xb[3] = {0, 0, 0};
-        int has_refl = wall && wall->present && wall->R0 != 0.0;
-        if (wall && wall->present) mirror(wall, xi, xb);
+        or_term terms[1 + OR_MAX_WALLS + 3];
+        const int nterm = or_terms(wall, xi, terms);
         double* o = out + (size_t)r * G;
         for (int g = 0; g < G; ++g) o[g] = 0.0;
         for (int e = 0; e < ne; ++e) {
@@ -574,10 +637,9 @@ void or_source(int nv, const double* xyz, int ne, const int* tri, const or_kappa
                     double dd = sqrt(dist2(V[a], V[b]));
                     if (dd > diam) diam = dd;
                 }
-            for (int term = 0; term < 2; ++term) {
-                if (term == 1 && !has_refl) break;
-                const double* src = term == 0 ? xi : xb;
-                double scale = term == 0 ? 1.0 : wall->R0;
+            for (int term = 0; term < nterm; ++term) {
+                const double* src = terms[term].src;
+                double scale = terms[term].scale;
                 /* is the source point a vertex of the triangle? */
                 int vloc = -1;
                 for (int k = 0; k < 3; ++k)
@@ -614,14 +676,7 @@ void or_source(int nv, const double* xyz, int ne, const int* tri, const or_kappa
                         for (int d = 0; d < 3; ++d)
                             for (int ee = 0; ee < 3; ++ee) y[ee] += lam[d] * V[d][ee];
                         double r2 = dist2(src, y);
-                        double tau;
-                        if (term == 0) {
-                            tau = optical_depth(kap, xi, y, &ga);
-                        } else {
-                            double xp[3];
-                            reflection_point(wall, xb, y, xp);
-                            tau = optical_depth(kap, xi, xp, &ga) + optical_depth(kap, xp, y, &ga);
-                        }
+                        double tau = term_tau(kap, wall, &terms[term], xi, y, &ga);
                         double geo = scale * area / (double)nsub * qw[q] * cm * cm / (r2 * r2) / (4.0 * OR_PI);
                         for (int g = 0; g < G; ++g) o[g] += geo * exp(-c[g] * tau);
                     }
@@ -644,13 +699,14 @@ void or_kernel_point(const or_kappa* kap, const or_wall* wall, const double* x, 
     gauss_t ga;
     ga.n = ngauss;
     or_gauss_legendre(ngauss, ga.t, ga.w);
-    direct_kernel(kap, x, y, &ga, G, c, out_direct);
-    if (wall && wall->present) {
-        double xb[3];
-        mirror(wall, x, xb);
-        reflected_kernel(kap, wall, x, xb, y, &ga, G, c, out_refl);
-    } else {
-        for (int g = 0; g < G; ++g) out_refl[g] = 0.0;
+    or_term terms[1 + OR_MAX_WALLS + 3];
+    const int nterm = or_terms(wall, x, terms);
+    double kv[64];
+    term_kernel(kap, wall, &terms[0], x, y, &ga, G, c, out_direct);
+    for (int g = 0; g < G; ++g) out_refl[g] = 0.0;
+    for (int t = 1; t < nterm; ++t) {
+        term_kernel(kap, wall, &terms[t], x, y, &ga, G, c, kv);
+        for (int g = 0; g < G; ++g) out_refl[g] += kv[g];
     }
 }
 
@@ -714,9 +770,8 @@ void or_source_hat(int nv, const double* xyz, int ne, const int* tri, const int*
     for (int r = 0; r < nrows; ++r) {
         int i = rows[r];
         const double* xi = xyz + 3 * (size_t)i;
-        double xb[3] = {0, 0, 0};
-        int has_refl = wall && wall->present && wall->R0 != 0.0;
-        if (wall && wall->present) mirror(wall, xi, xb);
+        or_term terms[1 + OR_MAX_WALLS + 3];
+        const int nterm = or_terms(wall, xi, terms);
         double* o = out + (size_t)r * G * L;
         for (int k = 0; k < G * L; ++k) o[k] = 0.0;
         for (int e = 0; e < ne; ++e) {
@@ -739,10 +794,9 @@ void or_source_hat(int nv, const double* xyz, int ne, const int* tri, const int*
                     double dd = sqrt(dist2(V[a], V[b]));
                     if (dd > diam) diam = dd;
                 }
-            for (int term = 0; term < 2; ++term) {
-                if (term == 1 && !has_refl) break;
-                const double* src = term == 0 ? xi : xb;
-                double scale = term == 0 ? 1.0 : wall->R0;
+            for (int term = 0; term < nterm; ++term) {
+                const double* src = terms[term].src;
+                double scale = terms[term].scale;
                 int vloc = -1;
                 for (int k = 0; k < 3; ++k)
                     if (dist2(src, V[k]) <= 1e-24) vloc = k;
@@ -777,14 +831,7 @@ void or_source_hat(int nv, const double* xyz, int ne, const int* tri, const int*
                         for (int d = 0; d < 3; ++d)
                             for (int ee = 0; ee < 3; ++ee) y[ee] += lam[d] * V[d][ee];
                         double r2 = dist2(src, y);
-                        double tau;
-                        if (term == 0) {
-                            tau = optical_depth(kap, xi, y, &ga);
-                        } else {
-                            double xp[3];
-                            reflection_point(wall, xb, y, xp);
-                            tau = optical_depth(kap, xi, xp, &ga) + optical_depth(kap, xp, y, &ga);
-                        }
+                        double tau = term_tau(kap, wall, &terms[term], xi, y, &ga);
                         double geo = scale * area / (double)nsub * qw[q] * cm * cm / (r2 * r2) / (4.0 * OR_PI);
                         for (int g = 0; g < G; ++g) {
                             double v = geo * exp(-c[g] * tau);

@@ -512,3 +512,77 @@ def test_surface_to_volume_rows_integrate_a_linear_emitter_coefficient(kind, amp
         ref = SR.emitter_source_reference(p.xyz[v], kind, 1.0, amp, c, R0,
                                           q0=lambda Y: 1.0 + 2.0 * Y[:, 1] - Y[:, 2])
         assert H[r] @ q == pytest.approx(ref, rel=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# several planar walls (Section 2: one reflection point per wall; corner terms)
+# ---------------------------------------------------------------------------
+def _two_wall_problem(n, kap, freqs, R0y, R0z, corner, grey=False):
+    p = W.cube_problem(n, kap, freqs, R0=R0z, grey=grey)
+    p.more_walls = (W.wall_y0(R0y),)
+    p.corner = corner
+    return p
+
+
+def test_two_perpendicular_walls_with_corner_terms_equal_the_fourfold_domain():
+    """Walls y = 0 and z = 0 with R0 = 1 plus the double reflection at their corner are the
+    cube mirrored twice: G_RC S equals G on the fourfold mesh applied to the even extension
+    of S, and the sources agree, to round-off (constant kappa)."""
+    n = 4
+    kap = W.Kappa(W.KAPPA_CONST, 1.1, 0.0)
+    p = _two_wall_problem(n, kap, W.grey_freqs(), 1.0, 1.0, corner=True)
+    qxyz, qtet, img = W.quadrupled_mesh(n)
+    pq = W.Problem(qxyz, qtet, W.quadrupled_emitter(n), kap, None, W.grey_freqs())
+    rows = np.array([0, 5, 21, 42, 63, 30], dtype=np.int32)
+    c = np.array([1.0, 0.6])
+    S = W.rand_vectors(p.N, seed=10)
+    S4 = np.zeros(qxyz.shape[0])
+    for k in range(4):
+        S4[img[k]] = S
+    np.testing.assert_allclose(O.G_rows(p, rows, c=c) @ S, O.G_rows(pq, rows, c=c) @ S4, rtol=1e-12)
+    allr = np.arange(p.N, dtype=np.int32)
+    np.testing.assert_allclose(O.source_geometric(p, allr, c=c), O.source_geometric(pq, allr, c=c),
+                               rtol=1e-12, atol=1e-15)
+    # without the corner term the identity fails: the double reflection carries real weight
+    p.corner = False
+    assert np.abs(O.G_rows(p, rows, c=c) @ S - O.G_rows(pq, rows, c=c) @ S4).max() > 1e-4
+
+
+def _unfolded_tau(x_img, y, k0, amp, npan=64, nq=8):
+    """Line integral of kappa_even(p) = kappa(p_x, |p_y|, |p_z|) on the straight segment from
+    the image point to y (the fourfold domain with kappa extended evenly), composite Gauss."""
+    g, wg = np.polynomial.legendre.leggauss(nq)
+    d = np.asarray(y) - np.asarray(x_img)
+    L = np.linalg.norm(d)
+    # kappa_even has a kink where the line crosses y = 0 or z = 0: panels end there
+    cuts = [-x_img[a] / d[a] for a in (1, 2) if d[a] != 0 and 0 < -x_img[a] / d[a] < 1]
+    knots = np.unique(np.concatenate([[0.0, 1.0], cuts]))
+    edges = np.concatenate([np.linspace(knots[k], knots[k + 1], npan + 1)[:-1] for k in range(len(knots) - 1)] + [[1.0]])
+    t = (0.5 * (edges[:-1, None] + edges[1:, None]) + 0.5 * (edges[1:, None] - edges[:-1, None]) * g).ravel()
+    wt = (0.5 * (edges[1:, None] - edges[:-1, None]) * wg).ravel()
+    P = np.asarray(x_img)[None, :] + t[:, None] * d[None, :]
+    kap = k0 + amp * np.sin(2 * np.pi * P[:, 0]) * np.sin(2 * np.pi * np.abs(P[:, 1])) * np.sin(2 * np.pi * np.abs(P[:, 2]))
+    return L * float((wt * kap).sum())
+
+
+def test_reflected_and_corner_paths_have_the_optical_depth_of_the_unfolded_line():
+    """Each reflected term's optical depth (physical broken path through its reflection
+    points) equals the line integral along the straight line from the image point in the
+    mirrored domain with kappa extended evenly -- for both single reflections and the corner
+    path -- checked through the kernel values at point pairs (sin-product kappa)."""
+    kap = W.sinprod_kappa(0.5)
+    rng = np.random.default_rng(13)
+    c = np.array([0.9, 2.0])
+    for _ in range(20):
+        x, y = rng.uniform(0.05, 0.95, 3), rng.uniform(0.05, 0.95, 3)
+        walls = [W.wall_z0(0.7), W.wall_y0(0.4)]
+        d0, _ = O.kernel_point(kap, None, x, y, c)
+        dk, rk = O.kernel_point(kap, walls, x, y, c, corner=True)
+        np.testing.assert_allclose(dk, d0, rtol=1e-13)
+        want = np.zeros_like(c)
+        ky = 1.0 + 0.5 * np.prod(np.sin(2 * np.pi * y))
+        for img, R in (((x[0], x[1], -x[2]), 0.7), ((x[0], -x[1], x[2]), 0.4), ((x[0], -x[1], -x[2]), 0.28)):
+            tau = _unfolded_tau(img, y, 1.0, 0.5)
+            r2 = float(np.sum((np.asarray(img) - y) ** 2))
+            want += R * c * ky * np.exp(-c * tau) / (4 * math.pi * r2)
+        np.testing.assert_allclose(rk, want, rtol=1e-9)

@@ -96,6 +96,11 @@ def wall_z0(R0: float = 0.5) -> Wall:
     return Wall((0.0, 0.0, 0.0), (0.0, 0.0, -1.0), float(R0))
 
 
+def wall_y0(R0: float = 0.5) -> Wall:
+    """The reflective plane y = 0, outward normal (0, -1, 0)."""
+    return Wall((0.0, 0.0, 0.0), (0.0, -1.0, 0.0), float(R0))
+
+
 @dataclasses.dataclass
 class Kappa:
     """kappa(x) = k0 (+ amp sin(2 pi x) sin(2 pi y) sin(2 pi z) when kind == SINPROD)."""
@@ -152,6 +157,8 @@ class Problem:
     Q0: float = 1.0
     T_emit: float = 1.0
     name: str = ""
+    more_walls: tuple = ()   # further planar reflective walls (each one reflection, Section 2)
+    corner: bool = False     # also the double reflections at perpendicular walls
 
     @property
     def N(self) -> int:
@@ -229,6 +236,60 @@ def serving_requests(count: int, rate_per_s: float = 200.0, seed: int = 0, nmin:
 # ---------------------------------------------------------------------------
 # Test inputs
 # ---------------------------------------------------------------------------
+def quadrupled_mesh(n: int):
+    """The cube mirrored in y = 0 and in z = 0: [0,1] x [-1,1] x [-1,1], four copies of
+    every tetrahedron.  Returns (xyz [M,3], tet [4T,4], image [4][N]) with image[k][v]
+    the id of vertex v mirrored by k = (flip y) + 2 (flip z); vertices on a mirror plane
+    are shared."""
+    xyz, tet = cube_mesh(n)
+    N = xyz.shape[0]
+    pts = [xyz]
+    images = [np.arange(N)]
+    nxt = N
+    for k in (1, 2, 3):
+        fy, fz = k & 1, k >> 1
+        img = np.empty(N, dtype=np.int64)
+        new = []
+        for v in range(N):
+            x = xyz[v].copy()
+            if fy:
+                x[1] = -x[1]
+            if fz:
+                x[2] = -x[2]
+            # shared with an earlier copy when the flipped coordinates are zero
+            same = None
+            if (not fy or xyz[v, 1] == 0.0) and (not fz or xyz[v, 2] == 0.0):
+                same = v
+            elif fy and fz and xyz[v, 1] == 0.0:
+                same = images[2][v]
+            elif fy and fz and xyz[v, 2] == 0.0:
+                same = images[1][v]
+            if same is not None:
+                img[v] = same
+            else:
+                img[v] = nxt
+                new.append(x)
+                nxt += 1
+        images.append(img)
+        if new:
+            pts.append(np.array(new))
+    qxyz = np.concatenate(pts, axis=0)
+    qtet = np.concatenate([images[k][tet] for k in range(4)], axis=0).astype(np.int32)
+    return qxyz, qtet, np.array(images)
+
+
+def quadrupled_emitter(n: int):
+    """Emitter face x = 0 of the quadrupled mesh (outward -x normal in every copy)."""
+    tri = emitter_face_x0(n)
+    _, _, img = quadrupled_mesh(n)
+    out = [tri]
+    for k in (1, 2, 3):
+        t = img[k][tri]
+        # one mirror flips the orientation, two restore it
+        out.append(t[:, [0, 2, 1]] if k in (1, 2) else t)
+    return np.concatenate(out, axis=0).astype(np.int32)
+
+
 def doubled_mesh(n: int):
     """The cube [0,1]^3 together with its mirror image in z = 0 ([0,1]^2 x [-1,1]).
 
