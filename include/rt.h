@@ -88,9 +88,12 @@ typedef struct {
 } rt_kappa;
 
 /* Planar reflective wall (Section 2, planar reflective boundaries): a point
- * p of the plane, the unit OUTWARD normal n, reflection coefficient R0.  The
- * plane's intersection with the (convex) domain is taken as the reflecting
- * face; at most one reflection per ray (Hypothesis 1, M = 1). */
+ * p of the plane, the OUTWARD normal n (any length, normalised by the
+ * library), reflection coefficient R0 in [0, 1].  The plane's intersection
+ * with the (convex) domain is taken as the reflecting face.  Up to
+ * RT_MAX_WALLS walls per problem, each adding one reflected term (its mirror
+ * image of x, weight R0; Hypothesis 1 with one reflection per wall). */
+#define RT_MAX_WALLS 3
 typedef struct {
     double p[3];
     double n[3];
@@ -127,18 +130,25 @@ typedef struct {
  * the mesh, right-hand normal = outward normal) radiating
  * Q_nu = Q0 [omega.n]_- B_nu(T_emit) (Example of Section 1), grey:
  * Q0 sigma T_emit^4.  grey != 0 selects the grey formulation (eq. (grey),
- * Section 3; F must be 1). */
+ * Section 3; F must be 1).
+ * Walls: n_walls in [0, RT_MAX_WALLS] planes in walls[].  corner != 0 adds,
+ * for every pair of perpendicular walls (|n_a . n_b| <= 1e-12 |n_a| |n_b|)
+ * with R0_a, R0_b > 0, the path that reflects on both (source point the
+ * double image of x, weight R0_a R0_b): the second-order term of Section 2's
+ * series of images, which Hypothesis 1 leaves out (corner = 0 is the paper's
+ * model). */
 typedef struct {
     rt_mesh mesh;
     rt_kappa kappa;
-    int n_walls; /* 0 or 1 */
-    const rt_wall* walls;
+    int n_walls;           /* 0 .. RT_MAX_WALLS */
+    const rt_wall* walls;  /* [n_walls] or NULL when n_walls == 0 */
     int64_t n_emit;
     const int32_t* emit_tri;
     double Q0;
     double T_emit;
     int grey;
     rt_freqs freqs;
+    int corner;            /* 0 or 1, see above */
 } rt_problem;
 
 /* Assembly parameters (Section 2 and 2.1). */

@@ -53,7 +53,8 @@ class RtFreqs(ctypes.Structure):
 
 class RtProblem(ctypes.Structure):
     _fields_ = [("mesh", RtMesh), ("kappa", RtKappa), ("n_walls", _c_int), ("walls", _P), ("n_emit", _c_i64),
-                ("emit_tri", _P), ("Q0", _c_dbl), ("T_emit", _c_dbl), ("grey", _c_int), ("freqs", RtFreqs)]
+                ("emit_tri", _P), ("Q0", _c_dbl), ("T_emit", _c_dbl), ("grey", _c_int), ("freqs", RtFreqs),
+                ("corner", _c_int)]
 
 
 class RtHparams(ctypes.Structure):
@@ -234,15 +235,16 @@ class _ProblemArgs:
         self.a = np.ascontiguousarray(fr.albedo, dtype=np.float64)
         grp = getattr(fr, "group", None)
         self.group = None if grp is None else np.ascontiguousarray(grp, dtype=np.int32)
+        walls = ([] if prob.wall is None else [prob.wall]) + list(getattr(prob, "more_walls", ()) or ())
         self.walls = None
-        n_walls = 0
-        if prob.wall is not None:
-            self.walls = (RtWall * 1)()
-            for d in range(3):
-                self.walls[0].p[d] = float(prob.wall.p[d])
-                self.walls[0].n[d] = float(prob.wall.n[d])
-            self.walls[0].R0 = float(prob.wall.R0)
-            n_walls = 1
+        n_walls = len(walls)
+        if n_walls:
+            self.walls = (RtWall * n_walls)()
+            for k, wl in enumerate(walls):
+                for d in range(3):
+                    self.walls[k].p[d] = float(wl.p[d])
+                    self.walls[k].n[d] = float(wl.n[d])
+                self.walls[k].R0 = float(wl.R0)
         self.s = RtProblem()
         self.s.mesh = RtMesh(self.xyz.shape[0], _ptr(self.xyz), self.tet.shape[0], _ptr(self.tet))
         self.s.kappa = RtKappa(int(prob.kappa.kind), float(prob.kappa.k0), float(prob.kappa.amp))
@@ -255,6 +257,7 @@ class _ProblemArgs:
         self.s.grey = 1 if prob.grey else 0
         self.s.freqs = RtFreqs(self.nu.shape[0], _ptr(self.nu), _ptr(self.w), _ptr(self.c), _ptr(self.a),
                                _ptr(self.group) if self.group is not None else None)
+        self.s.corner = 1 if getattr(prob, "corner", False) else 0
 
 
 class Operator:

@@ -153,7 +153,7 @@ __device__ __forceinline__ int find_span(const EntrySpan* sp, int ns, int64_t e)
     return lo;
 }
 
-template <class R, class OUT, int MG>
+template <class R, class OUT, int MG, bool XT = false>
 __global__ void __launch_bounds__(32 * kWarpsPerCta) entries_span_kernel(KernelParams P, const EntrySpan* spans,
                                                                          int nspans, int64_t total, OUT* out)
 {
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) entries_span_kernel(KernelP
         const int64_t loc = e - sp.first;
         const int ii = (int)(loc / sp.nj), jj = (int)(loc % sp.nj);
         R acc[MG];
-        entry_warp<R, MG>(P, sp.i0 + ii, sp.j0 + jj, acc, s_tet[wib], s_cnt[wib], s_pre[wib]);
+        entry_warp<R, MG, XT>(P, sp.i0 + ii, sp.j0 + jj, acc, s_tet[wib], s_cnt[wib], s_pre[wib]);
 #pragma unroll
         for (int g = 0; g < MG; ++g)
             if (g < P.G && lane == (g & 31)) out[sp.base + g * sp.gs + ii * sp.is + jj * sp.js] = (OUT)acc[g];
@@ -195,40 +195,6 @@ __device__ __forceinline__ int find_active(const AcaActive* a, int na, int64_t e
         if (f <= e) lo = mid; else hi = mid - 1;
     }
     return lo;
-}
-
-template <int MG>
-__global__ void __launch_bounds__(32 * kWarpsPerCta) aca_entries_kernel(KernelParams P, const AcaActive* act,
-                                                                        int na, int64_t total, int mode,
-                                                                        const int* istar, const int* jstar,
-                                                                        float* buf)
-{
-    __shared__ int s_tet[kWarpsPerCta][32], s_cnt[kWarpsPerCta][32], s_pre[kWarpsPerCta][33];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t nw = (int64_t)gridDim.x * kWarpsPerCta;
-    for (int64_t e = (int64_t)blockIdx.x * kWarpsPerCta + wib; e < total; e += nw) {
-        const int ai = find_active(act, na, e, mode);
-        const AcaActive a = act[ai];
-        if (mode == 1 && a.skip) continue;
-        int i, j, len;
-        int64_t pos;
-        if (mode == 0) {
-            pos = e - a.first_row;
-            i = a.row0 + istar[a.b];
-            j = a.col0 + (int)pos;
-            len = a.n;
-        } else {
-            pos = e - a.first_col;
-            i = a.row0 + (int)pos;
-            j = a.col0 + jstar[a.b];
-            len = a.m;
-        }
-        float acc[MG];
-        entry_warp<float, MG>(P, i, j, acc, s_tet[wib], s_cnt[wib], s_pre[wib]);
-#pragma unroll
-        for (int g = 0; g < MG; ++g)
-            if (g < P.G && lane == (g & 31)) buf[(mode == 0 ? a.rbuf : a.cbuf) + (int64_t)g * len + pos] = acc[g];
-    }
 }
 
 // ACA pivot columns: G_g[i, j*] for the rows i of an active block.  One CTA of
@@ -276,7 +242,7 @@ __device__ __forceinline__ void count_work(const KernelParams& P, unsigned terms
     }
 }
 
-template <int MG>
+template <int MG, bool XT = false>
 __global__ void __launch_bounds__(kColRows) aca_col_kernel(KernelParams P, const AcaActive* __restrict__ act, int na,
                                                            int64_t nchunks, const int* __restrict__ jstar,
                                                            float* __restrict__ buf)
@@ -353,6 +319,23 @@ __global__ void __launch_bounds__(kColRows) aca_col_kernel(KernelParams P, const
                         const float tau = optical_depth<float>(P, xi, xp) + optical_depth<float>(P, xp, y);
                         row_accumulate<MG>(P, acc, (float)P.R0 * pt.w / dist2<float>(xb, y), tau);
                     }
+                    if constexpr (XT) {   // further walls, corner paths
+                        for (int k = 0; k < P.n_extra; ++k) {
+                            Vec3<float> src;
+                            float sc;
+                            extra_term<float>(P, k, xi, src, sc);
+                            const int nx = dist2<float>(src, cen) < ce.w ? 14 : 4;
+                            n_terms += nx;
+                            n_depths += nx * (P.xkind[k] + 1);
+                            const float4* px = s_pt[t] + (nx == 14 ? 4 : 0);
+                            for (int q = 0; q < nx; ++q) {
+                                const float4 pt = px[q];
+                                const Vec3<float> y = {pt.x, pt.y, pt.z};
+                                row_accumulate<MG>(P, acc, sc * pt.w / dist2<float>(src, y),
+                                                   extra_tau<float>(P, k, xi, src, y));
+                            }
+                        }
+                    }
                 }
             }
         }
@@ -366,7 +349,7 @@ __global__ void __launch_bounds__(kColRows) aca_col_kernel(KernelParams P, const
 }
 
 // Arbitrary (row, col) pairs, internal vertex ids.
-template <class R, int MG>
+template <class R, int MG, bool XT = false>
 __global__ void __launch_bounds__(32 * kWarpsPerCta) entries_pairs_kernel(KernelParams P, int group, int64_t count,
                                                                           const int32_t* rows, const int32_t* cols,
                                                                           const int* iperm, double* out)
@@ -381,7 +364,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) entries_pairs_kernel(Kernel
             j = iperm[j];
         }
         R acc[MG];
-        entry_warp<R, MG>(P, i, j, acc, s_tet[wib], s_cnt[wib], s_pre[wib]);
+        entry_warp<R, MG, XT>(P, i, j, acc, s_tet[wib], s_cnt[wib], s_pre[wib]);
         R v = R(0);
 #pragma unroll
         for (int g = 0; g < MG; ++g)
@@ -401,6 +384,16 @@ static int grid_for(int64_t warps)
 }
 
 // Dispatch on the group count: the accumulator array is sized at compile time.
+// kernels with the further wall and corner terms (XT): 16 or 64 group slots
+#define RT_DISPATCH_MG_XT(G, MACRO) \
+    do {                            \
+        if ((G) <= 16) {            \
+            MACRO(16, true);        \
+        } else {                    \
+            MACRO(64, true);        \
+        }                           \
+    } while (0)
+
 #define RT_DISPATCH_MG(G, MACRO) \
     do {                         \
         if ((G) <= 1) {          \
@@ -434,9 +427,12 @@ static int launch_spans(Operator& op, const std::vector<EntrySpan>& spans_in, OU
     RT_CUDA_TRY(cudaMemcpyAsync(d_sp, spans.data(), spans.size() * sizeof(EntrySpan), cudaMemcpyHostToDevice, s));
     int grid = grid_for(total);
     const int ns = (int)spans.size();
-#define RT_LAUNCH_SPANS(MG) \
-    entries_span_kernel<R, OUT, MG><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, d_sp, ns, total, out)
-    RT_DISPATCH_MG(op.G, RT_LAUNCH_SPANS);
+#define RT_LAUNCH_SPANS(MG, XT) \
+    entries_span_kernel<R, OUT, MG, XT><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, d_sp, ns, total, out)
+#define RT_LAUNCH_SPANS1(MG) RT_LAUNCH_SPANS(MG, false)
+    if (op.kp.n_extra > 0) RT_DISPATCH_MG_XT(op.G, RT_LAUNCH_SPANS);
+    else RT_DISPATCH_MG(op.G, RT_LAUNCH_SPANS1);
+#undef RT_LAUNCH_SPANS1
 #undef RT_LAUNCH_SPANS
     RT_CUDA_TRY(cudaGetLastError());
     RT_CUDA_TRY(cudaFreeAsync(d_sp, s));
@@ -492,14 +488,20 @@ int eval_entries(Operator& op, int group, int64_t count, const int32_t* rows, co
     int grid = grid_for(count);
     const int* ip = op.d_iperm;
     if (op.prec == RT_PREC_F64) {
-#define RT_LAUNCH_PAIRS(MG) \
-    entries_pairs_kernel<double, MG><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, group, count, rows, cols, ip, out)
-        RT_DISPATCH_MG(op.G, RT_LAUNCH_PAIRS);
+#define RT_LAUNCH_PAIRS(MG, XT) \
+    entries_pairs_kernel<double, MG, XT><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, group, count, rows, cols, ip, out)
+#define RT_LAUNCH_PAIRS1(MG) RT_LAUNCH_PAIRS(MG, false)
+        if (op.kp.n_extra > 0) RT_DISPATCH_MG_XT(op.G, RT_LAUNCH_PAIRS);
+        else RT_DISPATCH_MG(op.G, RT_LAUNCH_PAIRS1);
+#undef RT_LAUNCH_PAIRS1
 #undef RT_LAUNCH_PAIRS
     } else {
-#define RT_LAUNCH_PAIRS(MG) \
-    entries_pairs_kernel<float, MG><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, group, count, rows, cols, ip, out)
-        RT_DISPATCH_MG(op.G, RT_LAUNCH_PAIRS);
+#define RT_LAUNCH_PAIRS(MG, XT) \
+    entries_pairs_kernel<float, MG, XT><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, group, count, rows, cols, ip, out)
+#define RT_LAUNCH_PAIRS1(MG) RT_LAUNCH_PAIRS(MG, false)
+        if (op.kp.n_extra > 0) RT_DISPATCH_MG_XT(op.G, RT_LAUNCH_PAIRS);
+        else RT_DISPATCH_MG(op.G, RT_LAUNCH_PAIRS1);
+#undef RT_LAUNCH_PAIRS1
 #undef RT_LAUNCH_PAIRS
     }
     RT_CUDA_TRY(cudaGetLastError());
@@ -549,11 +551,15 @@ __global__ void __launch_bounds__(256) source_kernel(KernelParams P, int n_emit,
             diam2 = fmax(diam2, dist2<R>(V0, V2));
             diam2 = fmax(diam2, dist2<R>(V1, V2));
             int vloc = tv.x == (int)i ? 0 : (tv.y == (int)i ? 1 : (tv.z == (int)i ? 2 : -1));
-            for (int term = 0; term < 2; ++term) {
-                if (term == 1 && !P.has_wall) break;
-                const Vec3<R> src = term == 0 ? xi : xb;
-                const R scale = term == 0 ? R(1) : R(P.R0);
-                if (vloc >= 0 && (term == 0 || on_wall)) {
+            for (int term = 0; term < 2 + P.n_extra; ++term) {
+                if (term == 1 && !P.has_wall) continue;
+                Vec3<R> src;
+                R scale;
+                term_source<R>(P, term, xi, xb, src, scale);
+                // the source point is x itself: always for the direct term, for an
+                // image when x lies on its wall(s)
+                const bool at_x = term == 0 || (term == 1 ? on_wall : dist2<R>(xi, src) <= R(1e-20));
+                if (vloc >= 0 && at_x) {
                     // limit at a vertex of the emitter: angle / (8 pi)
                     const Vec3<R> A = vloc == 0 ? V0 : (vloc == 1 ? V1 : V2);
                     const Vec3<R> B = vloc == 0 ? V1 : (vloc == 1 ? V2 : V0);
@@ -579,13 +585,7 @@ __global__ void __launch_bounds__(256) source_kernel(KernelParams P, int n_emit,
                     const Vec3<R> y = {b0 * V0.x + b1 * V1.x + b2 * V2.x, b0 * V0.y + b1 * V1.y + b2 * V2.y,
                                        b0 * V0.z + b1 * V1.z + b2 * V2.z};
                     const R r2 = dist2<R>(src, y);
-                    R tau;
-                    if (term == 0) {
-                        tau = optical_depth<R>(P, xi, y);
-                    } else {
-                        Vec3<R> xp = wall_point<R>(P, xb, y);
-                        tau = optical_depth<R>(P, xi, xp) + optical_depth<R>(P, xp, y);
-                    }
+                    const R tau = term_depth<R>(P, term, xi, src, y);
                     const R geo = scale * area * R(c_tri_w[q0 + q]) * cm * cm / (r2 * r2) * inv4pi;
 #pragma unroll
                     for (int g = 0; g < MG; ++g)
@@ -669,7 +669,7 @@ struct RowItem {
 // groups): every point is added to shared memory directly.  Tetrahedra are
 // handed out through a shared counter so that the few tetrahedra near x_i
 // (14-point rules) do not hold up a fixed partition.
-template <int MG>
+template <int MG, bool XT = false>
 __global__ void __launch_bounds__(256, MG <= 16 ? 2 : 1) row_cluster_kernel(KernelParams P, const RowItem* __restrict__ items,
                                                           const int* __restrict__ sub_tets,
                                                           const int* __restrict__ istar, float* __restrict__ out)
@@ -770,6 +770,49 @@ __global__ void __launch_bounds__(256, MG <= 16 ? 2 : 1) row_cluster_kernel(Kern
                 }
             }
         }
+        if constexpr (XT) {
+            // further walls and corner paths, each with its own rule; the point
+            // value is split over the vertices as above
+            for (int k = 0; k < P.n_extra; ++k) {
+                Vec3<float> src;
+                float sc;
+                extra_term<float>(P, k, xi, src, sc);
+                const int nx = dist2<float>(src, cen) < lim ? 14 : 4;
+                n_terms += nx;
+                n_depths += nx * (P.xkind[k] + 1);
+                for (int q = 0; q < nx; ++q) {
+                    const int row = (nx == 14 ? 4 : 0) + q;
+                    const float b0 = tet_b<float>(row, 0), b1 = tet_b<float>(row, 1), b2 = tet_b<float>(row, 2),
+                                b3 = tet_b<float>(row, 3);
+                    const Vec3<float> y = {b0 * v0.x + b1 * v1.x + b2 * v2.x + b3 * v3.x,
+                                           b0 * v0.y + b1 * v1.y + b2 * v2.y + b3 * v3.y,
+                                           b0 * v0.z + b1 * v1.z + b2 * v2.z + b3 * v3.z};
+                    const float w = sc * vol * tet_w<float>(row) * kappa_at<float>(P, y.x, y.y, y.z) * inv4pi /
+                                    dist2<float>(src, y);
+                    const float tau = extra_tau<float>(P, k, xi, src, y);
+                    if constexpr (MG > 0) {
+#pragma unroll
+                        for (int g = 0; g < MG; ++g)
+                            if (g < G) {
+                                const float val = w * P.cf[g] * expf(-P.cf[g] * tau);
+                                a0[g] += val * b0;
+                                a1[g] += val * b1;
+                                a2[g] += val * b2;
+                                a3[g] += val * b3;
+                            }
+                    } else {
+                        for (int g = 0; g < G; ++g) {
+                            const float val = w * P.cf[g] * expf(-P.cf[g] * tau);
+                            float* a = acc + g * n;
+                            if (in0) atomicAdd(a + jj[0], val * b0);
+                            if (in1) atomicAdd(a + jj[1], val * b1);
+                            if (in2) atomicAdd(a + jj[2], val * b2);
+                            if (in3) atomicAdd(a + jj[3], val * b3);
+                        }
+                    }
+                }
+            }
+        }
         if constexpr (MG > 0) {
 #pragma unroll
             for (int g = 0; g < MG; ++g)
@@ -861,6 +904,8 @@ int prepare_row_eval(Operator& op, std::string& err)
         RT_CUDA_TRY(cudaFuncSetAttribute(row_cluster_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
         RT_CUDA_TRY(cudaFuncSetAttribute(row_cluster_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
         RT_CUDA_TRY(cudaFuncSetAttribute(row_cluster_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        RT_CUDA_TRY(cudaFuncSetAttribute(row_cluster_kernel<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        RT_CUDA_TRY(cudaFuncSetAttribute(row_cluster_kernel<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
         attr_set[dev] = true;
     }
     return RT_OK;
@@ -879,7 +924,10 @@ static int launch_rows(Operator& op, const std::vector<RowItem>& items, const in
     for (size_t k0 = 0; k0 < items.size(); k0 += (size_t)1 << 30) {
         const int cnt = (int)std::min<size_t>(items.size() - k0, (size_t)1 << 30);
         const int G = op.G;
-        if (G <= 1) row_cluster_kernel<1><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
+        if (op.kp.n_extra > 0) {   // further walls or corner paths
+            if (G <= 16) row_cluster_kernel<16, true><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
+            else row_cluster_kernel<0, true><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
+        } else if (G <= 1) row_cluster_kernel<1><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
         else if (G <= 4) row_cluster_kernel<4><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
         else if (G <= 8) row_cluster_kernel<8><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
         else if (G <= 16) row_cluster_kernel<16><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
@@ -1482,8 +1530,12 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
                 // points tabulated once per chunk
                 {
                     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nchunk, (int64_t)sms * 32));
-#define RT_LAUNCH_ACAC(MG) aca_col_kernel<MG><<<grid, kColRows, 0, s>>>(op.kp, d_act, na, nchunk, D.jstar, colbuf)
-                    RT_DISPATCH_MG(G, RT_LAUNCH_ACAC);
+#define RT_LAUNCH_ACAC(MG, XT) \
+    aca_col_kernel<MG, XT><<<grid, kColRows, 0, s>>>(op.kp, d_act, na, nchunk, D.jstar, colbuf)
+#define RT_LAUNCH_ACAC1(MG) RT_LAUNCH_ACAC(MG, false)
+                    if (op.kp.n_extra > 0) RT_DISPATCH_MG_XT(G, RT_LAUNCH_ACAC);
+                    else RT_DISPATCH_MG(G, RT_LAUNCH_ACAC1);
+#undef RT_LAUNCH_ACAC1
 #undef RT_LAUNCH_ACAC
                     RT_CUDA_TRY(cudaGetLastError());
                 }
@@ -1746,11 +1798,13 @@ __global__ void __launch_bounds__(256) srcop_rows_kernel(KernelParams P, int n_e
             for (int k = 0; k < 3; ++k)
 #pragma unroll
                 for (int g = 0; g < MG; ++g) a[k][g] = 0.f;
-            for (int term = 0; term < 2; ++term) {
-                if (term == 1 && !P.has_wall) break;
-                const Vec3<float> src = term == 0 ? xi : xb;
-                const float scale = term == 0 ? 1.f : (float)P.R0;
-                if (vloc >= 0 && (term == 0 || on_wall)) {
+            for (int term = 0; term < 2 + P.n_extra; ++term) {
+                if (term == 1 && !P.has_wall) continue;
+                Vec3<float> src;
+                float scale;
+                term_source<float>(P, term, xi, xb, src, scale);
+                const bool at_x = term == 0 || (term == 1 ? on_wall : dist2<float>(xi, src) <= 1e-20f);
+                if (vloc >= 0 && at_x) {
                     const Vec3<float> A = vloc == 0 ? V0 : (vloc == 1 ? V1 : V2);
                     const Vec3<float> B = vloc == 0 ? V1 : (vloc == 1 ? V2 : V0);
                     const Vec3<float> Cc = vloc == 0 ? V2 : (vloc == 1 ? V0 : V1);
@@ -1774,13 +1828,7 @@ __global__ void __launch_bounds__(256) srcop_rows_kernel(KernelParams P, int n_e
                     const Vec3<float> y = {b[0] * V0.x + b[1] * V1.x + b[2] * V2.x, b[0] * V0.y + b[1] * V1.y + b[2] * V2.y,
                                            b[0] * V0.z + b[1] * V1.z + b[2] * V2.z};
                     const float r2 = dist2<float>(src, y);
-                    float tau;
-                    if (term == 0) {
-                        tau = optical_depth<float>(P, xi, y);
-                    } else {
-                        const Vec3<float> xp = wall_point<float>(P, xb, y);
-                        tau = optical_depth<float>(P, xi, xp) + optical_depth<float>(P, xp, y);
-                    }
+                    const float tau = term_depth<float>(P, term, xi, src, y);
                     const float geo = scale * area * (float)c_tri_w[q0 + q] * cm * cm / (r2 * r2) * inv4pi;
 #pragma unroll
                     for (int g = 0; g < MG; ++g) {

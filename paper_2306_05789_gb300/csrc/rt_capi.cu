@@ -42,14 +42,17 @@ int validate(const rt_problem* P, const rt_hparams* H)
     if (P->n_emit < 0 || (P->n_emit > 0 && !P->emit_tri)) return fail(RT_EINVAL, "emitter triangles missing");
     for (int64_t k = 0; k < 3 * P->n_emit; ++k)
         if (P->emit_tri[k] < 0 || P->emit_tri[k] >= M.n_vert) return fail(RT_EINVAL, "emitter vertex id out of range");
-    if (P->n_walls < 0 || P->n_walls > 1) return fail(RT_EINVAL, "n_walls must be 0 or 1 (one reflection per ray)");
-    if (P->n_walls == 1) {
-        if (!P->walls) return fail(RT_EINVAL, "walls pointer missing");
-        const double* n = P->walls[0].n;
+    if (P->n_walls < 0 || P->n_walls > RT_MAX_WALLS) return fail(RT_EINVAL, "n_walls must lie in [0, RT_MAX_WALLS]");
+    if (P->n_walls > 0 && !P->walls) return fail(RT_EINVAL, "walls pointer missing");
+    for (int w = 0; w < P->n_walls; ++w) {
+        const double* n = P->walls[w].n;
         const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
         if (!(nn > 0.0) || !std::isfinite(nn)) return fail(RT_EINVAL, "wall normal must be nonzero");
-        if (!(P->walls[0].R0 >= 0.0 && P->walls[0].R0 <= 1.0)) return fail(RT_EINVAL, "R0 must lie in [0, 1]");
+        for (int d = 0; d < 3; ++d)
+            if (!std::isfinite(P->walls[w].p[d])) return fail(RT_EINVAL, "wall point must be finite");
+        if (!(P->walls[w].R0 >= 0.0 && P->walls[w].R0 <= 1.0)) return fail(RT_EINVAL, "R0 must lie in [0, 1]");
     }
+    if (P->corner != 0 && P->corner != 1) return fail(RT_EINVAL, "corner must be 0 or 1");
     if (P->kappa.kind != RT_KAPPA_CONST && P->kappa.kind != RT_KAPPA_SINPROD) return fail(RT_EINVAL, "kappa kind");
     if (!(P->kappa.k0 >= 0.0) || !std::isfinite(P->kappa.k0)) return fail(RT_EINVAL, "kappa: k0 must be >= 0");
     if (P->kappa.kind == RT_KAPPA_SINPROD && !(std::fabs(P->kappa.amp) <= P->kappa.k0))
@@ -325,16 +328,43 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
     kp.amp = P->kappa.kind == RT_KAPPA_SINPROD ? P->kappa.amp : 0.0;
     kp.k0f = (float)kp.k0;
     kp.ampf = (float)kp.amp;
-    kp.has_wall = (P->n_walls == 1 && P->walls[0].R0 > 0.0) ? 1 : 0;
-    if (P->n_walls == 1) {
-        const double* n = P->walls[0].n;
+    // the first wall keeps its own fields (the one-wall kernels' path); the
+    // further walls and the corner paths go to the extra-term list
+    kp.has_wall = (P->n_walls >= 1 && P->walls[0].R0 > 0.0) ? 1 : 0;
+    for (int w = 0; w < P->n_walls; ++w) {
+        const double* n = P->walls[w].n;
         const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
         for (int d = 0; d < 3; ++d) {
-            kp.wp[d] = P->walls[0].p[d];
-            kp.wn[d] = n[d] / nn;
+            kp.wps[w][d] = P->walls[w].p[d];
+            kp.wns[w][d] = n[d] / nn;
         }
-        kp.R0 = P->walls[0].R0;
+        kp.wR[w] = P->walls[w].R0;
     }
+    if (P->n_walls >= 1) {
+        for (int d = 0; d < 3; ++d) {
+            kp.wp[d] = kp.wps[0][d];
+            kp.wn[d] = kp.wns[0][d];
+        }
+        kp.R0 = kp.wR[0];
+    }
+    kp.n_extra = 0;
+    for (int w = 1; w < P->n_walls; ++w)
+        if (kp.wR[w] > 0.0) {
+            kp.xkind[kp.n_extra] = 1;
+            kp.xa[kp.n_extra] = w;
+            kp.xb[kp.n_extra] = -1;
+            ++kp.n_extra;
+        }
+    if (P->corner)
+        for (int a = 0; a < P->n_walls; ++a)
+            for (int b = a + 1; b < P->n_walls; ++b) {
+                const double dot = kp.wns[a][0] * kp.wns[b][0] + kp.wns[a][1] * kp.wns[b][1] + kp.wns[a][2] * kp.wns[b][2];
+                if (std::fabs(dot) > 1e-12 || !(kp.wR[a] > 0.0) || !(kp.wR[b] > 0.0)) continue;
+                kp.xkind[kp.n_extra] = 2;
+                kp.xa[kp.n_extra] = a;
+                kp.xb[kp.n_extra] = b;
+                ++kp.n_extra;
+            }
     kp.G = op.G;
     for (int g = 0; g < op.G; ++g) {
         kp.c[g] = op.gc[g];

@@ -228,10 +228,93 @@ __device__ __forceinline__ Vec3<R> wall_point(const KernelParams& P, const Vec3<
     return {xb.x + t * (y.x - xb.x), xb.y + t * (y.y - xb.y), xb.z + t * (y.z - xb.z)};
 }
 
+// ---- further reflected terms (several walls, corner paths) -------------------
+template <class R>
+__device__ __forceinline__ R wall_side(const KernelParams& P, int w, const Vec3<R>& x)
+{
+    return (x.x - R(P.wps[w][0])) * R(P.wns[w][0]) + (x.y - R(P.wps[w][1])) * R(P.wns[w][1]) +
+           (x.z - R(P.wps[w][2])) * R(P.wns[w][2]);
+}
+
+template <class R>
+__device__ __forceinline__ Vec3<R> mirror_w(const KernelParams& P, int w, const Vec3<R>& x)
+{
+    const R s = wall_side<R>(P, w, x);
+    return {x.x - R(2) * s * R(P.wns[w][0]), x.y - R(2) * s * R(P.wns[w][1]), x.z - R(2) * s * R(P.wns[w][2])};
+}
+
+// source point (the image of x) and weight of extra term k
+template <class R>
+__device__ __forceinline__ void extra_term(const KernelParams& P, int k, const Vec3<R>& x, Vec3<R>& src, R& scale)
+{
+    const int a = P.xa[k];
+    src = mirror_w<R>(P, a, x);
+    scale = R(P.wR[a]);
+    if (P.xkind[k] == 2) {
+        src = mirror_w<R>(P, P.xb[k], src);
+        scale *= R(P.wR[P.xb[k]]);
+    }
+}
+
+// optical depth of extra term k's physical path from x to y (src = its image of x):
+// one wall: x -> x' -> y with x' on [src, y]; two perpendicular walls: the plane
+// that the line from y to src crosses first holds the last reflection point Q, and
+// the crossing of the other plane mirrored back in the first is the first one P
+template <class R>
+__device__ __forceinline__ R extra_tau(const KernelParams& P, int k, const Vec3<R>& x, const Vec3<R>& src,
+                                       const Vec3<R>& y)
+{
+    const int a = P.xa[k];
+    if (P.xkind[k] == 1) {
+        const R sb = wall_side<R>(P, a, src), sy = wall_side<R>(P, a, y);
+        const R den = sb - sy;
+        const R t = den > R(0) ? sb / den : R(0);
+        const Vec3<R> xp = {src.x + t * (y.x - src.x), src.y + t * (y.y - src.y), src.z + t * (y.z - src.z)};
+        return optical_depth<R>(P, x, xp) + optical_depth<R>(P, xp, y);
+    }
+    const int b = P.xb[k];
+    const R sya = wall_side<R>(P, a, y), sza = wall_side<R>(P, a, src);
+    const R syb = wall_side<R>(P, b, y), szb = wall_side<R>(P, b, src);
+    const R ta = sya / (sya - sza), tb = syb / (syb - szb);
+    const bool afirst = ta <= tb;
+    const R t1 = afirst ? ta : tb, t2 = afirst ? tb : ta;
+    const Vec3<R> Q = {y.x + t1 * (src.x - y.x), y.y + t1 * (src.y - y.y), y.z + t1 * (src.z - y.z)};
+    const Vec3<R> U = {y.x + t2 * (src.x - y.x), y.y + t2 * (src.y - y.y), y.z + t2 * (src.z - y.z)};
+    const Vec3<R> Pp = mirror_w<R>(P, afirst ? a : b, U);
+    return optical_depth<R>(P, x, Pp) + optical_depth<R>(P, Pp, Q) + optical_depth<R>(P, Q, y);
+}
+
+// Term t of the kernel at x, t < 2 + P.n_extra: 0 the direct path, 1 the first
+// wall's image (present when P.has_wall), t >= 2 further term t - 2.  Source
+// point and weight, and the optical depth of the term's path to y.
+template <class R>
+__device__ __forceinline__ void term_source(const KernelParams& P, int t, const Vec3<R>& xi, const Vec3<R>& xb,
+                                            Vec3<R>& src, R& scale)
+{
+    if (t < 2) {
+        src = t == 0 ? xi : xb;
+        scale = t == 0 ? R(1) : R(P.R0);
+    } else {
+        extra_term<R>(P, t - 2, xi, src, scale);
+    }
+}
+
+template <class R>
+__device__ __forceinline__ R term_depth(const KernelParams& P, int t, const Vec3<R>& xi, const Vec3<R>& src,
+                                        const Vec3<R>& y)
+{
+    if (t == 0) return optical_depth<R>(P, xi, y);
+    if (t == 1) {
+        const Vec3<R> xp = wall_point<R>(P, src, y);
+        return optical_depth<R>(P, xi, xp) + optical_depth<R>(P, xp, y);
+    }
+    return extra_tau<R>(P, t - 2, xi, src, y);
+}
+
 // Evaluates G_g^{ij} for all groups g < P.G with the whole warp; every lane
 // returns the sums in acc.  s_tet / s_cnt / s_pre: per-warp shared scratch of
 // 32, 32 and 33 ints.
-template <class R, int MG>
+template <class R, int MG, bool XT = false>
 __device__ void entry_warp(const KernelParams& P, int i, int j, R (&acc)[MG], int* s_tet, int* s_cnt, int* s_pre)
 {
     const int lane = threadIdx.x & 31;
@@ -328,6 +411,39 @@ __device__ void entry_warp(const KernelParams& P, int i, int j, R (&acc)[MG], in
             }
         }
         __syncwarp();
+    }
+    // further walls and corner paths (instances with XT): lanes over the
+    // tetrahedra, points in series
+    for (int k = 0; k < (XT ? P.n_extra : 0); ++k) {
+        Vec3<R> src;
+        R scale;
+        extra_term<R>(P, k, xi, src, scale);
+        for (int e = t0 + lane; e < t1; e += 32) {
+            const int packed = P.vt_idx[e];
+            const int tet = packed >> 2, loc = packed & 3;
+            Vec3<R> cen;
+            R diam, vol;
+            load_tgeo<R>(P, tet, cen, diam, vol);
+            const int nq = dist2<R>(src, cen) < R(4) * diam * diam ? 14 : 4;
+            const int4 tv = P.tet[tet];
+            const Vec3<R> v0 = load_xyz<R>(P, tv.x), v1 = load_xyz<R>(P, tv.y), v2 = load_xyz<R>(P, tv.z),
+                          v3 = load_xyz<R>(P, tv.w);
+            for (int q = 0; q < nq; ++q) {
+                const int row = (nq == 14 ? 4 : 0) + q;
+                const R b0 = tet_b<R>(row, 0), b1 = tet_b<R>(row, 1), b2 = tet_b<R>(row, 2), b3 = tet_b<R>(row, 3);
+                const Vec3<R> y = {b0 * v0.x + b1 * v1.x + b2 * v2.x + b3 * v3.x, b0 * v0.y + b1 * v1.y + b2 * v2.y + b3 * v3.y,
+                                   b0 * v0.z + b1 * v1.z + b2 * v2.z + b3 * v3.z};
+                const R lam = loc == 0 ? b0 : (loc == 1 ? b1 : (loc == 2 ? b2 : b3));
+                const R tau = extra_tau<R>(P, k, xi, src, y);
+                const R w = scale * vol * tet_w<R>(row) * lam * kappa_at<R>(P, y.x, y.y, y.z) * inv4pi / dist2<R>(src, y);
+#pragma unroll
+                for (int g = 0; g < MG; ++g)
+                    if (g < P.G) {
+                        const R cg = kp_c<R>(P, g);
+                        acc[g] += w * cg * exp_r(-cg * tau);
+                    }
+            }
+        }
     }
 #pragma unroll
     for (int g = 0; g < MG; ++g) {

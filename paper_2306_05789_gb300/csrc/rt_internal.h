@@ -24,6 +24,8 @@
 namespace rt {
 
 constexpr int kMaxGroups = 64;
+constexpr int kMaxWalls = 3;     // planar reflective walls per problem
+constexpr int kMaxXTerms = 5;    // reflected terms beyond the first wall's: 2 walls + 3 corners
 constexpr int kMaxGauss = 32;
 constexpr int kSubCols = 256;   // columns per sub-cluster in row evaluations
 constexpr double kPi = 3.14159265358979323846;
@@ -43,6 +45,12 @@ struct KernelParams {
     int has_wall;       // R0 != 0 and a wall is present
     double wp[3], wn[3];
     double R0;
+    // further reflected terms (walls beyond the first with R0 != 0, then the corner
+    // paths of perpendicular pairs): kind 1 = one reflection on wall xa, kind 2 =
+    // reflections on walls xa and xb; walls indexed in wps / wns / wR
+    int n_extra;
+    int xkind[kMaxXTerms], xa[kMaxXTerms], xb[kMaxXTerms];
+    double wps[kMaxWalls][3], wns[kMaxWalls][3], wR[kMaxWalls];
     int G;              // groups
     double c[kMaxGroups];
     float cf[kMaxGroups];
