@@ -23,6 +23,11 @@ Readings of the paper taken here:
 * residual: ||J^{k+1} - J^k||_2 / ||J^{k+1}||_2 over all vertices and frequencies.
 * emitter intensity Q_nu = Q0 B_nu(T_emit) (Example of Section 1), grey:
   Q0 sigma T_emit^4.
+* gridded kappa: the value of the grid cell holding the point (values pass
+  through float32, as the library's C ABI takes them); its optical depth is the
+  exact integral along the segment.
+* non-convex domains (Remark 1 after Lemma 1): opaque boxes of the convex hull
+  carry kappa = +infinity; a path crossing one has infinite optical depth.
 
 parity unpinned: nothing in this module is unpinned; the header of
 ``rt_oracle.c`` and the tests name the pin of every function.
@@ -52,8 +57,18 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+MAX_OBST = 4
+MAX_GRID_DIM = 512
+
+
+class _Box(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+
+
 class _Kappa(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int), ("k0", ctypes.c_double), ("amp", ctypes.c_double)]
+    _fields_ = [("kind", ctypes.c_int), ("k0", ctypes.c_double), ("amp", ctypes.c_double),
+                ("grid", ctypes.c_void_p), ("dims", ctypes.c_int * 3), ("glo", ctypes.c_double * 3),
+                ("ghi", ctypes.c_double * 3), ("n_obst", ctypes.c_int), ("obst", _Box * MAX_OBST)]
 
 
 MAX_WALLS = 3
@@ -86,6 +101,8 @@ def lib():
         _lib.or_tri_rule.restype = i
         _lib.or_kappa_at.argtypes = [P, P]
         _lib.or_kappa_at.restype = ctypes.c_double
+        _lib.or_blocked.argtypes = [P, P, P]
+        _lib.or_blocked.restype = i
         _lib.or_optical_depth.argtypes = [P, P, P, i]
         _lib.or_optical_depth.restype = ctypes.c_double
         _lib.or_kernel_point.argtypes = [P, P, P, P, i, P, i, P, P]
@@ -97,8 +114,38 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def _kappa_struct(kappa) -> _Kappa:
-    return _Kappa(int(kappa.kind), float(kappa.k0), float(kappa.amp))
+def _kappa_struct(kappa, obstacles=()) -> _Kappa:
+    """kappa: kind, k0, amp and, for the grid kind, ``grid`` (cell values, array
+    [nz, ny, nx], x fastest) and ``bbox`` (x0, y0, z0, x1, y1, z1).  obstacles:
+    opaque boxes (each with lo, hi), kappa = +infinity inside."""
+    k = _Kappa()
+    k.kind = int(kappa.kind)
+    k.k0 = float(kappa.k0)
+    k.amp = float(kappa.amp)
+    grid = getattr(kappa, "grid", None)
+    if grid is not None:
+        g = np.ascontiguousarray(np.asarray(grid, dtype=np.float32), dtype=np.float64)
+        assert g.ndim == 3 and max(g.shape) <= MAX_GRID_DIM
+        k._grid = g                                # keeps the array alive with the struct
+        k.grid = g.ctypes.data
+        nz, ny, nx = g.shape
+        k.dims[0], k.dims[1], k.dims[2] = nx, ny, nz
+        bb = kappa.bbox
+        for d in range(3):
+            k.glo[d] = float(bb[d])
+            k.ghi[d] = float(bb[3 + d])
+    obstacles = list(obstacles or ())
+    assert len(obstacles) <= MAX_OBST
+    k.n_obst = len(obstacles)
+    for o, b in enumerate(obstacles):
+        for d in range(3):
+            k.obst[o].lo[d] = float(b.lo[d])
+            k.obst[o].hi[d] = float(b.hi[d])
+    return k
+
+
+def _prob_kappa(prob) -> _Kappa:
+    return _kappa_struct(prob.kappa, getattr(prob, "obstacles", ()))
 
 
 def problem_walls(prob):
@@ -161,18 +208,27 @@ def kappa_at(kappa, p) -> float:
     return lib().or_kappa_at(ctypes.byref(k), _ptr(p))
 
 
-def optical_depth(kappa, a, b, ngauss: int = 16) -> float:
-    k = _kappa_struct(kappa)
+def optical_depth(kappa, a, b, ngauss: int = 16, obstacles=()) -> float:
+    k = _kappa_struct(kappa, obstacles)
     a = np.ascontiguousarray(a, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
     return lib().or_optical_depth(ctypes.byref(k), _ptr(a), _ptr(b), ngauss)
 
 
-def kernel_point(kappa, wall, x, y, c, ngauss: int = 16, corner: bool = False):
+def blocked(obstacles, a, b) -> bool:
+    """Does the open segment (a, b) cross the interior of one of the opaque boxes?"""
+    from types import SimpleNamespace
+    k = _kappa_struct(SimpleNamespace(kind=0, k0=0.0, amp=0.0), obstacles)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    return bool(lib().or_blocked(ctypes.byref(k), _ptr(a), _ptr(b)))
+
+
+def kernel_point(kappa, wall, x, y, c, ngauss: int = 16, corner: bool = False, obstacles=()):
     """(direct[G], reflected[G]) kernel values at the point pair (x, y); reflected = the sum
     of every wall's term (and the corner terms).  wall: None, a wall or a list of walls."""
     c = np.ascontiguousarray(c, dtype=np.float64)
-    k = _kappa_struct(kappa)
+    k = _kappa_struct(kappa, obstacles)
     w = _wall_struct(wall, corner=corner)
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64)
@@ -242,7 +298,7 @@ def G_rows(prob, rows, c=None, ngauss: int = 16, refine: int = 0, R0=None, momen
     N = xyz.shape[0]
     out = np.zeros((rows.shape[0], G, N))
     mom = np.zeros((rows.shape[0], G, 4)) if moments else None
-    k = _kappa_struct(prob.kappa)
+    k = _prob_kappa(prob)
     w = _prob_walls(prob, R0)
     lib().or_G_rows(N, _ptr(xyz), tet.shape[0], _ptr(tet), ctypes.byref(k), ctypes.byref(w), G, _ptr(c),
                     ngauss, refine, rows.shape[0], _ptr(rows), _ptr(out),
@@ -258,7 +314,7 @@ def G_entry(prob, i: int, j: int, c=None, ngauss: int = 16, R0=None):
     xyz = np.ascontiguousarray(prob.xyz, dtype=np.float64)
     tet = np.ascontiguousarray(prob.tet, dtype=np.int32)
     out = np.zeros(c.shape[0])
-    k = _kappa_struct(prob.kappa)
+    k = _prob_kappa(prob)
     w = _prob_walls(prob, R0)
     lib().or_G_entry(xyz.shape[0], _ptr(xyz), tet.shape[0], _ptr(tet), ctypes.byref(k), ctypes.byref(w),
                      c.shape[0], _ptr(c), ngauss, int(i), int(j), _ptr(out))
@@ -275,7 +331,7 @@ def source_geometric(prob, rows=None, c=None, ngauss: int = 16, refine: int = 0,
     N = xyz.shape[0]
     rows = np.arange(N, dtype=np.int32) if rows is None else np.ascontiguousarray(rows, dtype=np.int32)
     out = np.zeros((rows.shape[0], c.shape[0]))
-    k = _kappa_struct(prob.kappa)
+    k = _prob_kappa(prob)
     w = _prob_walls(prob, R0)
     lib().or_source(N, _ptr(xyz), tri.shape[0], _ptr(tri), ctypes.byref(k), ctypes.byref(w), c.shape[0],
                     _ptr(c), ngauss, refine, rows.shape[0], _ptr(rows), _ptr(out))
@@ -303,7 +359,7 @@ def source_hat_rows(prob, rows, c=None, ngauss: int = 16, refine: int = 0, R0=No
     rows = np.ascontiguousarray(rows, dtype=np.int32)
     L = sv.shape[0]
     out = np.zeros((rows.shape[0], c.shape[0], L))
-    k = _kappa_struct(prob.kappa)
+    k = _prob_kappa(prob)
     w = _prob_walls(prob, R0)
     lib().or_source_hat(xyz.shape[0], _ptr(xyz), tri.shape[0], _ptr(tri), _ptr(col), L, ctypes.byref(k),
                         ctypes.byref(w), c.shape[0], _ptr(c), ngauss, refine, rows.shape[0], _ptr(rows), _ptr(out))

@@ -10,9 +10,15 @@
  * generator with the CUDA library.
  *
  * What it computes (all in double precision, no blocking or compression):
- *   - kappa(x): constant, or k0 + amp*sin(2 pi x) sin(2 pi y) sin(2 pi z).
+ *   - kappa(x): constant, k0 + amp*sin(2 pi x) sin(2 pi y) sin(2 pi z), or a
+ *     cellwise-constant grid (the value of the grid cell holding x).
  *   - optical depth  int_[a,b] kappa := |b-a| int_0^1 kappa(s b + (1-s) a) ds
- *     (definition under eq. (gen1), Section 1.1), by n-point Gauss-Legendre.
+ *     (definition under eq. (gen1), Section 1.1), by n-point Gauss-Legendre;
+ *     for the grid, exactly: the sum over the pieces of [a,b] cut by the grid
+ *     planes of (value of the piece's cell) x (piece length).
+ *   - non-convex domains (Remark 1 after Lemma 1): opaque boxes in the convex
+ *     hull carry kappa = +infinity, so a path whose open segment crosses the
+ *     interior of a box has infinite optical depth and contributes nothing.
  *   - the volume kernel of the Corollary / Example of Section 1.2 with kappa
  *     folded in as in the FEM matrix G_kappa^{ij} of Section 2:
  *        direct    kappa(y) exp(-tau(x,y)) / (4 pi |x-y|^2)
@@ -40,9 +46,27 @@
 
 #define OR_PI 3.14159265358979323846
 
+#define OR_MAX_OBST 4
+#define OR_MAX_GRID_DIM 512
+/* a path is blocked by a box when its open segment overlaps the open box on a
+ * parameter interval longer than this (relative to the segment) */
+#define OR_BLOCK_EPS 1e-6
+
 typedef struct {
-    int kind;          /* 0: kappa = k0; 1: k0 + amp*sin(2pi x)sin(2pi y)sin(2pi z) */
+    double lo[3], hi[3];
+} or_box;
+
+typedef struct {
+    int kind;          /* 0: kappa = k0; 1: k0 + amp*sin(2pi x)sin(2pi y)sin(2pi z); 2: grid */
     double k0, amp;
+    /* kind 2: dims[0] x dims[1] x dims[2] equal cells of the box [glo, ghi];
+     * cell (i, j, k) holds grid[i + dims[0] * (j + dims[1] * k)]; a point
+     * outside the box takes the value of the nearest cell (clamped indices) */
+    const double* grid;
+    int dims[3];
+    double glo[3], ghi[3];
+    int n_obst;        /* opaque boxes (kappa = +infinity inside) */
+    or_box obst[OR_MAX_OBST];
 } or_kappa;
 
 /* planar reflective walls: a point p of the plane, the unit OUTWARD normal n,
@@ -161,12 +185,89 @@ int or_tri_rule(int which, double* bary, double* w)
 /* ------------------------------------------------------------------ */
 /* kappa and the optical depth                                          */
 /* ------------------------------------------------------------------ */
+static int grid_cell(const or_kappa* k, int d, double x)
+{
+    double u = (x - k->glo[d]) / (k->ghi[d] - k->glo[d]) * k->dims[d];
+    int c = (int)floor(u);
+    if (c < 0) c = 0;
+    if (c > k->dims[d] - 1) c = k->dims[d] - 1;
+    return c;
+}
+
 double or_kappa_at(const or_kappa* k, const double* p)
 {
+    if (k->kind == 2) {
+        int i = grid_cell(k, 0, p[0]), j = grid_cell(k, 1, p[1]), l = grid_cell(k, 2, p[2]);
+        return k->grid[i + k->dims[0] * (j + k->dims[1] * l)];
+    }
     double v = k->k0;
     if (k->kind == 1)
         v += k->amp * sin(2.0 * OR_PI * p[0]) * sin(2.0 * OR_PI * p[1]) * sin(2.0 * OR_PI * p[2]);
     return v;
+}
+
+/* does the open segment (a, b) cross the interior of one of the opaque boxes?
+ * Slab clipping: the parameter interval of the segment inside each open slab
+ * lo_d < x_d < hi_d, intersected over the three axes. */
+int or_blocked(const or_kappa* k, const double* a, const double* b)
+{
+    for (int o = 0; o < k->n_obst; ++o) {
+        const or_box* B = &k->obst[o];
+        double t0 = 0.0, t1 = 1.0;
+        int inside = 1;
+        for (int d = 0; d < 3 && inside; ++d) {
+            double dd = b[d] - a[d];
+            if (dd == 0.0) {
+                if (!(a[d] > B->lo[d] && a[d] < B->hi[d])) inside = 0;
+                continue;
+            }
+            double ta = (B->lo[d] - a[d]) / dd, tb = (B->hi[d] - a[d]) / dd;
+            if (ta > tb) {
+                double tmp = ta;
+                ta = tb;
+                tb = tmp;
+            }
+            if (ta > t0) t0 = ta;
+            if (tb < t1) t1 = tb;
+        }
+        if (inside && t1 - t0 > OR_BLOCK_EPS) return 1;
+    }
+    return 0;
+}
+
+static int cmp_double(const void* x, const void* y)
+{
+    double a = *(const double*)x, b = *(const double*)y;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+/* exact integral of the cellwise-constant grid over [a, b]: cut the segment at
+ * every interior grid plane it crosses, take each piece's cell from the
+ * piece's midpoint */
+static double grid_depth(const or_kappa* k, const double* a, const double* b)
+{
+    double d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    double L = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double ts[3 * OR_MAX_GRID_DIM + 2];
+    int nt = 0;
+    ts[nt++] = 0.0;
+    ts[nt++] = 1.0;
+    for (int ax = 0; ax < 3; ++ax) {
+        if (d[ax] == 0.0) continue;
+        double h = (k->ghi[ax] - k->glo[ax]) / k->dims[ax];
+        for (int m = 1; m < k->dims[ax]; ++m) {
+            double t = (k->glo[ax] + m * h - a[ax]) / d[ax];
+            if (t > 0.0 && t < 1.0) ts[nt++] = t;
+        }
+    }
+    qsort(ts, nt, sizeof(double), cmp_double);
+    double s = 0.0;
+    for (int q = 0; q + 1 < nt; ++q) {
+        double tm = 0.5 * (ts[q] + ts[q + 1]);
+        double p[3] = {a[0] + tm * d[0], a[1] + tm * d[1], a[2] + tm * d[2]};
+        s += or_kappa_at(k, p) * (ts[q + 1] - ts[q]);
+    }
+    return L * s;
 }
 
 typedef struct {
@@ -177,6 +278,8 @@ typedef struct {
 /* int_[a,b] kappa = |b-a| * sum_g (w_g/2) kappa(a + (1+t_g)/2 (b-a)). */
 static double optical_depth(const or_kappa* k, const double* a, const double* b, const gauss_t* g)
 {
+    if (k->n_obst > 0 && or_blocked(k, a, b)) return INFINITY;
+    if (k->kind == 2) return grid_depth(k, a, b);
     double d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
     double L = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     if (k->kind == 0) {

@@ -158,3 +158,36 @@ def emitter_source_reference(x, kappa_kind, k0, amp, c, R0, npan=24, nq=10, q0=N
     t_up = line_tau(Xp, Y) if kappa_kind else k0 * np.linalg.norm(Y - Xp, axis=1)
     refl = (Wq * d * d * np.exp(-c * (t_low + t_up)) / (rb2 * rb2)).sum() / (4 * math.pi)
     return direct + R0 * refl
+
+
+def entry_distance(x, dirs, lo, hi):
+    """Distance from x (outside the box) along each direction to where the ray enters the
+    open box (lo, hi); inf when it misses.  Slab clipping written out per axis."""
+    x = np.asarray(x, dtype=np.float64)
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    t0 = np.zeros(dirs.shape[0])
+    t1 = np.full(dirs.shape[0], np.inf)
+    for d in range(3):
+        v = dirs[:, d]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ta = (lo[d] - x[d]) / v
+            tb = (hi[d] - x[d]) / v
+        par = v == 0
+        inside = (x[d] > lo[d]) & (x[d] < hi[d])
+        ta = np.where(par, np.where(inside, -np.inf, np.inf), ta)
+        tb = np.where(par, np.where(inside, np.inf, -np.inf), tb)
+        t0 = np.maximum(t0, np.minimum(ta, tb))
+        t1 = np.minimum(t1, np.maximum(ta, tb))
+    return np.where(t1 > t0, t0, np.inf)
+
+
+def row_sum_reference_obstacle(x, k0, c, box_lo, box_hi, obst_lo, obst_hi, n_mu=256, n_phi=512):
+    """Lemma 1 with Remark 1 (kappa = +infinity inside an opaque box): the continuous row sum of
+    c*G (constant kappa, no wall) at x is (1/4pi) int_S2 (1 - e^{-c k0 d(omega)}) with d the
+    distance to the first of: leaving the container box, entering the opaque box."""
+    dirs, wts = sphere_rule(n_mu, n_phi)
+    L, _, _ = exit_distance(x, dirs, box_lo, box_hi)
+    E = entry_distance(x, dirs, obst_lo, obst_hi)
+    d = np.minimum(L, E)
+    return (wts * (1 - np.exp(-c * k0 * d))).sum() / (4 * math.pi)

@@ -586,3 +586,135 @@ def test_reflected_and_corner_paths_have_the_optical_depth_of_the_unfolded_line(
             r2 = float(np.sum((np.asarray(img) - y) ** 2))
             want += R * c * ky * np.exp(-c * tau) / (4 * math.pi * r2)
         np.testing.assert_allclose(rk, want, rtol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# cellwise-constant kappa grid and opaque obstacles (non-convex domains,
+# Remark 1 after Lemma 1: kappa = +infinity in the hull outside the domain)
+# ---------------------------------------------------------------------------
+def _grid_kappa(grid, bbox=(0.0, 0.0, 0.0, 1.0, 1.0, 1.0)):
+    return W.Kappa(W.KAPPA_GRID, 0.0, 0.0, np.asarray(grid, dtype=np.float32), bbox)
+
+
+def test_grid_optical_depth_is_the_exact_integral():
+    """Hand values, the constant grid, and brute-force midpoint sums on random segments
+    through a random grid (error bound: one sample interval per plane crossing)."""
+    k = _grid_kappa([[[1.0, 3.0]]])
+    assert O.optical_depth(k, [0.25, 0.5, 0.5], [1.0, 0.5, 0.5]) == pytest.approx(1.75, rel=1e-15)
+    # slanted: from (0, 0, 0) to (1, 1, 0) crosses x = 0.5 at the middle: sqrt(2) (1 + 3) / 2
+    assert O.optical_depth(k, [0, 0, 0], [1, 1, 0]) == pytest.approx(2 * math.sqrt(2), rel=1e-14)
+    assert O.optical_depth(_grid_kappa(np.full((3, 2, 4), 2.5)), [0.1, 0.2, 0.3], [0.9, 0.4, 0.05]) == \
+        pytest.approx(2.5 * np.linalg.norm([0.8, 0.2, -0.25]), rel=1e-14)
+    rng = np.random.default_rng(41)
+    grid = rng.uniform(0.1, 4.0, (5, 3, 4)).astype(np.float32)
+    k = _grid_kappa(grid, (-0.1, 0.0, 0.2, 1.1, 0.9, 1.0))
+    M = 200000
+    for _ in range(12):
+        a, b = rng.uniform(-0.2, 1.2, 3), rng.uniform(-0.2, 1.2, 3)
+        t = (np.arange(M) + 0.5) / M
+        P = a[None, :] + t[:, None] * (b - a)[None, :]
+        lo, hi = np.array([-0.1, 0.0, 0.2]), np.array([1.1, 0.9, 1.0])
+        idx = np.clip(np.floor((P - lo) / (hi - lo) * np.array([4, 3, 5])).astype(int), 0, [3, 2, 4])
+        vals = grid[idx[:, 2], idx[:, 1], idx[:, 0]].astype(np.float64)
+        L = np.linalg.norm(b - a)
+        brute = L * vals.mean()
+        bound = L * 12 * float(grid.max() - grid.min()) / M
+        assert abs(O.optical_depth(k, a, b) - brute) <= bound
+        # kappa_at: the cell of the point, clamped outside the grid's box
+        for p in P[:: M // 7]:
+            i = np.clip(np.floor((p - lo) / (hi - lo) * np.array([4, 3, 5])).astype(int), 0, [3, 2, 4])
+            assert O.kappa_at(k, p) == float(grid[i[2], i[1], i[0]])
+
+
+def test_constant_grid_gives_the_constant_kappa_operator():
+    """A grid holding one value everywhere is kappa = const: rows and source agree with the
+    constant-kappa oracle to rounding (the exact integral against the Gauss sum of a constant;
+    the value is exact in float32, the precision grid values pass through)."""
+    p = W.cube_problem(5, W.Kappa(W.KAPPA_CONST, 1.25, 0.0), W.midpoint_freqs(2), R0=0.5)
+    q = W.cube_problem(5, _grid_kappa(np.full((2, 3, 2), 1.25)), W.midpoint_freqs(2), R0=0.5)
+    rows = np.array([0, 31, 62, 124], dtype=np.int32)
+    np.testing.assert_allclose(O.G_rows(q, rows), O.G_rows(p, rows), rtol=1e-12, atol=1e-300)
+    np.testing.assert_allclose(O.source_geometric(q), O.source_geometric(p), rtol=1e-12, atol=1e-300)
+
+
+def test_blocking_matches_brute_force_segment_sampling():
+    """or_blocked against dense sampling of the open segment, on random segments whose
+    deepest point is clearly inside or clearly outside the box; plus the grazing cases."""
+    B = [W.Box((0.3, 0.35, 0.4), (0.7, 0.6, 0.8))]
+    lo, hi = np.array(B[0].lo), np.array(B[0].hi)
+    rng = np.random.default_rng(42)
+    t = (np.arange(1, 4000) / 4000.0)[:, None]
+    checked = 0
+    for _ in range(400):
+        a, b = rng.uniform(0, 1, 3), rng.uniform(0, 1, 3)
+        P = a + t * (b - a)
+        depth = np.minimum(P - lo, hi - P).min(axis=1).max()   # > 0: some sample inside
+        if abs(depth) < 2e-3:
+            continue
+        assert O.blocked(B, a, b) == (depth > 0)
+        checked += 1
+    assert checked > 300
+    # along a face, ending on a face from outside, through an edge: not blocked
+    assert not O.blocked(B, [0.3, 0.0, 0.5], [0.3, 1.0, 0.5])
+    assert not O.blocked(B, [0.0, 0.5, 0.5], [0.3, 0.5, 0.5])
+    assert not O.blocked(B, [0.2, 0.35, 0.5], [0.4, 0.25, 0.5])
+    # from a face point into the box, and across it
+    assert O.blocked(B, [0.3, 0.5, 0.5], [0.9, 0.5, 0.5])
+    assert O.blocked(B, [0.0, 0.5, 0.6], [1.0, 0.45, 0.6])
+
+
+def _slab_problems(grey=True, R0=0.5):
+    """Unit box of 5^3 cells (h = 0.2) with the slab of cells 0.4 < x < 0.6 removed and, in
+    one problem, an opaque box filling it: the two halves of the domain cannot see each other."""
+    xyz, tet = W.box_mesh((5, 5, 5), 0.2, hole=((2, 0, 0), (3, 5, 5)))
+    emit = W.boundary_faces(xyz, tet, lambda cen: np.abs(cen[:, 0]) < 1e-9)
+    kap = W.Kappa(W.KAPPA_CONST, 0.9, 0.0)
+    fr = W.grey_freqs() if grey else W.midpoint_freqs(2, albedo=0.3)
+    free = W.Problem(xyz, tet, emit, kap, W.wall_z0(R0), fr, grey=grey)
+    shut = W.Problem(xyz, tet, emit, kap, W.wall_z0(R0), fr, grey=grey,
+                     obstacles=(W.Box((0.4, -0.1, -0.1), (0.6, 1.1, 1.1)),))
+    return free, shut
+
+
+def test_an_opaque_slab_separates_the_two_halves_exactly():
+    """Rows and source with an opaque box filling the removed slab: entries between the halves
+    (direct and through the wall) are exactly 0, entries within a half and the source on the
+    emitter's half are those of the same mesh without the box, the far half gets no source."""
+    free, shut = _slab_problems()
+    left = np.where(free.xyz[:, 0] < 0.45)[0]
+    right = np.where(free.xyz[:, 0] > 0.55)[0]
+    rows = np.concatenate([left[::9], right[::9]]).astype(np.int32)
+    Gf, Gs = O.G_rows(free, rows), O.G_rows(shut, rows)
+    for r, i in enumerate(rows):
+        same = left if free.xyz[i, 0] < 0.45 else right
+        other = right if free.xyz[i, 0] < 0.45 else left
+        np.testing.assert_allclose(Gs[r][:, same], Gf[r][:, same], rtol=1e-14, atol=0)
+        assert (Gs[r][:, other] == 0).all()
+        assert (Gf[r][:, other] > 0).all()
+    Sf, Ss = O.source_geometric(free), O.source_geometric(shut)
+    np.testing.assert_allclose(Ss[left], Sf[left], rtol=1e-14, atol=0)
+    assert (Ss[right] == 0).all() and (Sf[right] > 0).all()
+
+
+def test_row_sums_around_an_opaque_cube_converge_to_lemma1_with_remark1():
+    """Lemma 1 on the convex hull with kappa = +infinity in the removed cube: sum_j G^{ij} ->
+    (1/4pi) int_S2 (1 - e^{-c kappa d}) with d the distance to the hull's boundary or to the
+    cube, whichever comes first.  Red refinement and the Richardson value, as for the cube."""
+    xyz, tet = W.box_mesh((6, 6, 6), 1.0 / 6, hole=((2, 2, 2), (4, 4, 4)))
+    kap = W.Kappa(W.KAPPA_CONST, 1.5, 0.0)
+    p = W.Problem(xyz, tet, np.zeros((0, 3), np.int32), kap, None, W.grey_freqs(), grey=True,
+                  obstacles=(W.Box((1 / 3, 1 / 3, 1 / 3), (2 / 3, 2 / 3, 2 / 3)),))
+    targets = np.array([[1 / 6, 1 / 2, 1 / 2], [1 / 3, 1 / 3, 1 / 6], [1 / 2, 1 / 6, 5 / 6]])
+    verts = np.array([np.argmin(np.linalg.norm(xyz - t, axis=1)) for t in targets], dtype=np.int32)
+    c = np.array([1.0])
+    R = [O.G_rows(p, verts, c=c, refine=ref).sum(axis=2)[:, 0] for ref in (0, 1, 2)]
+    for v in range(len(verts)):
+        ref = SR.row_sum_reference_obstacle(xyz[verts[v]], 1.5, 1.0, [0, 0, 0], [1, 1, 1],
+                                            [1 / 3] * 3, [2 / 3] * 3, 192, 384)
+        free = SR.row_sum_reference_obstacle(xyz[verts[v]], 1.5, 1.0, [0, 0, 0], [1, 1, 1],
+                                             [5.0] * 3, [6.0] * 3, 192, 384)
+        assert free - ref > 0.02                      # the cube takes a visible share
+        e0, e2 = R[0][v] / ref - 1, R[2][v] / ref - 1
+        assert abs(e0) < 0.15 and abs(e2) < abs(e0)
+        rich = 2 * R[2][v] - R[1][v]
+        assert abs(rich / ref - 1) < 1e-3

@@ -18,6 +18,15 @@ tetrahedral mesh of the domain, a triangulated boundary):
 * ``doubled_mesh(n)``: the cube and its mirror image in z = 0, i.e. the
   "symmetrised domain" of the academic test (Section 3.2), built by mirroring
   every tetrahedron so the lower half is the exact image of the upper half.
+* ``box_mesh(dims, h, hole)``: the Kuhn mesh of a box of dims[0] x dims[1] x
+  dims[2] cells of size h, with the cells of an index box removed (a
+  non-convex domain, Remark 1 after Lemma 1), and ``boundary_faces`` to pick
+  triangles of its boundary with the outward orientation.
+* ``kobayashi_problem(h)``: the box-minus-cube geometry of the paper's Test 3
+  (Section 4, after Kobayashi's test 1A): container (0, 0.6) x (0, 1) x
+  (0, 0.6), radiating cube [0, 0.1]^3 opaque, its three inner faces emitting,
+  three perfectly reflecting planes through the origin, a low-absorption duct
+  prolonging the cube along y (lengths in metres, kappa per metre).
 """
 from __future__ import annotations
 
@@ -28,6 +37,7 @@ from typing import List
 import numpy as np
 
 KAPPA_CONST = 0
+KAPPA_GRID = 2
 KAPPA_SINPROD = 1
 
 _KUHN_PERMS = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
@@ -103,10 +113,21 @@ def wall_y0(R0: float = 0.5) -> Wall:
 
 @dataclasses.dataclass
 class Kappa:
-    """kappa(x) = k0 (+ amp sin(2 pi x) sin(2 pi y) sin(2 pi z) when kind == SINPROD)."""
+    """kappa(x) = k0 (+ amp sin(2 pi x) sin(2 pi y) sin(2 pi z) when kind == SINPROD);
+    kind == GRID: the value of the cell holding x of a grid of equal cells over
+    bbox = (x0, y0, z0, x1, y1, z1), grid float32 [nz, ny, nx] (x fastest)."""
     kind: int = KAPPA_CONST
     k0: float = 1.0
     amp: float = 0.0
+    grid: np.ndarray | None = None
+    bbox: tuple | None = None
+
+
+@dataclasses.dataclass
+class Box:
+    """Axis-aligned box [lo, hi]; as an obstacle it is opaque (kappa = +infinity inside)."""
+    lo: tuple
+    hi: tuple
 
 
 @dataclasses.dataclass
@@ -159,6 +180,7 @@ class Problem:
     name: str = ""
     more_walls: tuple = ()   # further planar reflective walls (each one reflection, Section 2)
     corner: bool = False     # also the double reflections at perpendicular walls
+    obstacles: tuple = ()    # opaque boxes inside the convex hull (non-convex domain)
 
     @property
     def N(self) -> int:
@@ -337,3 +359,98 @@ def sample_rows(N: int, count: int, seed: int = 0) -> np.ndarray:
 def kuhn_mesh_stats(n: int):
     """(N, T_e) of the cube mesh: N = n^3, T_e = 6 (n-1)^3."""
     return n ** 3, 6 * (n - 1) ** 3
+
+
+# ---------------------------------------------------------------------------
+# Non-convex domains: a box of Kuhn cells with a box of cells removed
+# ---------------------------------------------------------------------------
+def box_mesh(dims, h: float, hole=None):
+    """Kuhn mesh of [0, dims[0] h] x [0, dims[1] h] x [0, dims[2] h] (dims = cells per
+    axis); hole = ((i0, j0, k0), (i1, j1, k1)) removes the cells i0 <= i < i1, ... .
+    Vertices that no tetrahedron uses are dropped; the rest keep the order
+    i + (nx+1) (j + (ny+1) k).  Returns (xyz float64 [N, 3], tet int32 [T, 4])."""
+    nx, ny, nz = (int(d) for d in dims)
+    vx, vy = nx + 1, ny + 1
+    k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    xyz = np.stack([i.ravel() * h, j.ravel() * h, k.ravel() * h], axis=1).astype(np.float64)
+
+    def vid(ii, jj, kk):
+        return ii + vx * (jj + vy * kk)
+
+    ck, cj, ci = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+    if hole is not None:
+        (i0, j0, k0), (i1, j1, k1) = hole
+        keep = ~((ci >= i0) & (ci < i1) & (cj >= j0) & (cj < j1) & (ck >= k0) & (ck < k1))
+        ci, cj, ck = ci[keep], cj[keep], ck[keep]
+    tets = []
+    for p in _KUHN_PERMS:
+        cur = [ci.copy(), cj.copy(), ck.copy()]
+        v0 = vid(*cur)
+        cur[p[0]] += 1
+        v1 = vid(*cur)
+        cur[p[1]] += 1
+        v2 = vid(*cur)
+        v3 = vid(ci + 1, cj + 1, ck + 1)
+        tets.append(np.stack([v0, v1, v2, v3], axis=1))
+    tet = np.stack(tets, axis=1).reshape(-1, 4)
+    used = np.zeros(xyz.shape[0], dtype=bool)
+    used[tet.ravel()] = True
+    new_id = np.cumsum(used) - 1
+    return xyz[used].copy(), new_id[tet].astype(np.int32)
+
+
+def boundary_faces(xyz, tet, select=None):
+    """Boundary triangles of a tetrahedral mesh (faces of exactly one tetrahedron),
+    ordered so that the right-hand normal points out of the domain.  select(centroids)
+    -> bool mask keeps a subset.  int32 [K, 3]."""
+    tet = np.asarray(tet, dtype=np.int64)
+    faces, opp = [], []
+    for a, b, c, d in ((0, 1, 2, 3), (0, 1, 3, 2), (0, 2, 3, 1), (1, 2, 3, 0)):
+        faces.append(tet[:, [a, b, c]])
+        opp.append(tet[:, d])
+    faces = np.concatenate(faces)
+    opp = np.concatenate(opp)
+    key = np.sort(faces, axis=1)
+    _, inv, cnt = np.unique(key, axis=0, return_inverse=True, return_counts=True)
+    inv = inv.ravel()
+    once = cnt[inv] == 1
+    faces, opp = faces[once], opp[once]
+    P = xyz[faces]
+    nrm = np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0])
+    inward = np.einsum("ij,ij->i", nrm, xyz[opp] - P[:, 0]) > 0
+    faces[inward] = faces[inward][:, [0, 2, 1]]
+    if select is not None:
+        faces = faces[np.asarray(select(xyz[faces].mean(axis=1)), dtype=bool)]
+    return faces.astype(np.int32)
+
+
+def kobayashi_problem(h: float = 0.05, freqs: Freqs | None = None, corner: bool = True) -> Problem:
+    """Box-minus-cube geometry of the paper's Test 3 (Section 4, after Kobayashi's test 1A),
+    lengths in metres: container D = (0, 0.6) x (0, 1) x (0, 0.6), opaque radiating cube
+    C = [0, 0.1]^3 removed from the mesh (kappa = +infinity there), its three faces inside D
+    emitting with Q0 = 0.1, perfectly reflecting planes x = 0, y = 0, z = 0 (R0 = 1, one
+    reflection per wall, corner paths optional), kappa = 10 / m except 0.01 / m in the duct
+    (0, 0.1) x (0.1, 1) x (0, 0.1) prolonging the cube, as a 6 x 10 x 6 grid of 0.1 m cells.
+    h must divide 0.1."""
+    m = int(round(0.1 / h))
+    assert m >= 1 and abs(m * h - 0.1) < 1e-12
+    xyz, tet = box_mesh((6 * m, 10 * m, 6 * m), h, hole=((0, 0, 0), (m, m, m)))
+    eps = 1e-9
+
+    def on_cube(cen):
+        on_face = ((np.abs(cen[:, 0] - 0.1) < eps) | (np.abs(cen[:, 1] - 0.1) < eps) |
+                   (np.abs(cen[:, 2] - 0.1) < eps))
+        inside = (cen <= 0.1 + eps).all(axis=1)
+        return on_face & inside
+
+    emit = boundary_faces(xyz, tet, on_cube)
+    grid = np.full((6, 10, 6), 10.0, dtype=np.float32)   # [z, y, x]
+    grid[0, 1:, 0] = 0.01
+    kap = Kappa(KAPPA_GRID, 0.0, 0.0, grid, (0.0, 0.0, 0.0, 0.6, 1.0, 0.6))
+    walls = (Wall((0.0, 0.0, 0.0), (-1.0, 0.0, 0.0), 1.0), Wall((0.0, 0.0, 0.0), (0.0, -1.0, 0.0), 1.0),
+             Wall((0.0, 0.0, 0.0), (0.0, 0.0, -1.0), 1.0))
+    fr = grey_freqs() if freqs is None else freqs
+    return Problem(xyz, tet, emit, kap, walls[0], fr, grey=freqs is None, Q0=0.1, T_emit=1.0,
+                   name=f"kobayashi_h{h:g}", more_walls=walls[1:], corner=corner,
+                   obstacles=(Box((0.0, 0.0, 0.0), (0.1, 0.1, 0.1)),))
