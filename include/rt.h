@@ -50,6 +50,9 @@ extern "C" {
 /* kappa(x) descriptors (kappa_nu = c_nu * kappa(x)) */
 #define RT_KAPPA_CONST 0   /* kappa = k0 */
 #define RT_KAPPA_SINPROD 1 /* kappa = k0 + amp sin(2 pi x) sin(2 pi y) sin(2 pi z) */
+#define RT_KAPPA_GRID 2    /* cellwise-constant grid, see rt_kappa */
+#define RT_MAX_GRID_DIM 512
+#define RT_MAX_OBSTACLES 4
 
 /* operator storage modes and precisions */
 #define RT_MODE_DENSE 0   /* every entry of G stored (FP64 or FP32) */
@@ -81,11 +84,31 @@ typedef struct {
     const int32_t* tet;
 } rt_mesh;
 
+/* Absorption kappa(x) (kappa_nu = c_nu kappa(x), Section 1.1).  RT_KAPPA_GRID:
+ * dims[0] x dims[1] x dims[2] equal cells of the box bbox = (x0, y0, z0, x1,
+ * y1, z1); cell (i, j, k) holds grid[i + dims[0] (j + dims[1] k)] >= 0 (host
+ * array, copied during the build); a point outside the box takes the value of
+ * the nearest cell.  The optical depth int_[a,b] kappa of a grid is computed
+ * exactly (the segment cut at the grid planes, each piece times its cell's
+ * value); the analytic kinds use the Gauss-Legendre rule of rt_hparams. */
 typedef struct {
     int kind;  /* RT_KAPPA_* */
     double k0; /* constant part */
     double amp;
+    const float* grid;  /* RT_KAPPA_GRID only, else NULL */
+    int dims[3];        /* cells per axis, 1 .. RT_MAX_GRID_DIM */
+    double bbox[6];
 } rt_kappa;
+
+/* Opaque axis-aligned box [lo, hi] inside the convex hull of a non-convex
+ * domain (Remark 1 after Lemma 1: kappa = +infinity in the hull outside the
+ * domain).  A path whose open segment overlaps the open box on a parameter
+ * interval longer than 1e-6 of the segment has infinite optical depth and
+ * contributes nothing.  No tetrahedron may lie inside a box (RT_EINVAL). */
+typedef struct {
+    double lo[3];
+    double hi[3];
+} rt_box;
 
 /* Planar reflective wall (Section 2, planar reflective boundaries): a point
  * p of the plane, the OUTWARD normal n (any length, normalised by the
@@ -149,6 +172,8 @@ typedef struct {
     int grey;
     rt_freqs freqs;
     int corner;            /* 0 or 1, see above */
+    int n_obstacles;       /* 0 .. RT_MAX_OBSTACLES opaque boxes */
+    const rt_box* obstacles;
 } rt_problem;
 
 /* Assembly parameters (Section 2 and 2.1). */

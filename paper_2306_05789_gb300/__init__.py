@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librt.so")
 
 RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOCONV, RT_ETIMEOUT, RT_EAGAIN = 0, -1, -2, -3, -4, -5, -6
-RT_KAPPA_CONST, RT_KAPPA_SINPROD = 0, 1
+RT_KAPPA_CONST, RT_KAPPA_SINPROD, RT_KAPPA_GRID = 0, 1, 2
 RT_MODE_DENSE, RT_MODE_HMATRIX = 0, 1
 RT_PREC_F64, RT_PREC_F32, RT_PREC_BF16, RT_PREC_F16 = 0, 1, 2, 3
 RT_ADM_GAP, RT_ADM_CENTER = 0, 1
@@ -40,7 +40,12 @@ class RtMesh(ctypes.Structure):
 
 
 class RtKappa(ctypes.Structure):
-    _fields_ = [("kind", _c_int), ("k0", _c_dbl), ("amp", _c_dbl)]
+    _fields_ = [("kind", _c_int), ("k0", _c_dbl), ("amp", _c_dbl), ("grid", _P), ("dims", _c_int * 3),
+                ("bbox", _c_dbl * 6)]
+
+
+class RtBox(ctypes.Structure):
+    _fields_ = [("lo", _c_dbl * 3), ("hi", _c_dbl * 3)]
 
 
 class RtWall(ctypes.Structure):
@@ -54,7 +59,7 @@ class RtFreqs(ctypes.Structure):
 class RtProblem(ctypes.Structure):
     _fields_ = [("mesh", RtMesh), ("kappa", RtKappa), ("n_walls", _c_int), ("walls", _P), ("n_emit", _c_i64),
                 ("emit_tri", _P), ("Q0", _c_dbl), ("T_emit", _c_dbl), ("grey", _c_int), ("freqs", RtFreqs),
-                ("corner", _c_int)]
+                ("corner", _c_int), ("n_obstacles", _c_int), ("obstacles", _P)]
 
 
 class RtHparams(ctypes.Structure):
@@ -247,7 +252,27 @@ class _ProblemArgs:
                 self.walls[k].R0 = float(wl.R0)
         self.s = RtProblem()
         self.s.mesh = RtMesh(self.xyz.shape[0], _ptr(self.xyz), self.tet.shape[0], _ptr(self.tet))
-        self.s.kappa = RtKappa(int(prob.kappa.kind), float(prob.kappa.k0), float(prob.kappa.amp))
+        kap = prob.kappa
+        self.s.kappa = RtKappa(int(kap.kind), float(kap.k0), float(kap.amp))
+        grid = getattr(kap, "grid", None)
+        self.grid = None
+        if grid is not None:
+            self.grid = np.ascontiguousarray(grid, dtype=np.float32)   # [nz, ny, nx], x fastest
+            nz, ny, nx = self.grid.shape
+            self.s.kappa.grid = _ptr(self.grid)
+            self.s.kappa.dims[0], self.s.kappa.dims[1], self.s.kappa.dims[2] = nx, ny, nz
+            for d in range(6):
+                self.s.kappa.bbox[d] = float(kap.bbox[d])
+        obst = list(getattr(prob, "obstacles", ()) or ())
+        self.obst = None
+        if obst:
+            self.obst = (RtBox * len(obst))()
+            for o, b in enumerate(obst):
+                for d in range(3):
+                    self.obst[o].lo[d] = float(b.lo[d])
+                    self.obst[o].hi[d] = float(b.hi[d])
+            self.s.n_obstacles = len(obst)
+            self.s.obstacles = ctypes.cast(self.obst, _P)
         self.s.n_walls = n_walls
         self.s.walls = ctypes.cast(self.walls, _P) if self.walls is not None else None
         self.s.n_emit = self.tri.shape[0]

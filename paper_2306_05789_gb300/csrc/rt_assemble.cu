@@ -209,9 +209,12 @@ constexpr int kColTets = 32;
 
 // acc[g] += w c_g exp(-c_g tau) over the groups (Eq. 5 with the group scale
 // c_g of the multi-frequency operator); exp recurrence when c_g is arithmetic.
-template <int MG>
+template <int MG, bool XT = false>
 __device__ __forceinline__ void row_accumulate(const KernelParams& P, float (&acc)[MG], float w, float tau)
 {
+    if constexpr (XT) {
+        if (!(tau < INFINITY)) return;   // path through an opaque box
+    }
     if (P.c_arith) {
         float E = expf(-P.c0f * tau);
         const float D = expf(-P.dcf * tau);
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(kColRows) aca_col_kernel(KernelParams P, const
                 y.y = b0w * v0.y + b1 * v1.y + b2 * v2.y + b3 * v3.y;
                 y.z = b0w * v0.z + b1 * v1.z + b2 * v2.z + b3 * v3.z;
                 const float lam = loc == 0 ? b0w : (loc == 1 ? b1 : (loc == 2 ? b2 : b3));
-                const float w = P.tvol32[tet] * tet_w<float>(q) * lam * kappa_at<float>(P, y.x, y.y, y.z) * inv4pi;
+                const float w = P.tvol32[tet] * tet_w<float>(q) * lam * kappa_at<float, XT>(P, y.x, y.y, y.z) * inv4pi;
                 s_pt[t][q] = make_float4(y.x, y.y, y.z, w);
                 if (q == 0) {
                     Vec3<float> cen;
@@ -309,15 +312,15 @@ __global__ void __launch_bounds__(kColRows) aca_col_kernel(KernelParams P, const
                     for (int q = 0; q < nd; ++q) {
                         const float4 pt = pd[q];
                         const Vec3<float> y = {pt.x, pt.y, pt.z};
-                        row_accumulate<MG>(P, acc, pt.w / dist2<float>(xi, y), optical_depth<float>(P, xi, y));
+                        row_accumulate<MG, XT>(P, acc, pt.w / dist2<float>(xi, y), optical_depth<float, XT>(P, xi, y));
                     }
                     const float4* pr = s_pt[t] + (nr == 14 ? 4 : 0);
                     for (int q = 0; q < nr; ++q) {
                         const float4 pt = pr[q];
                         const Vec3<float> y = {pt.x, pt.y, pt.z};
                         const Vec3<float> xp = wall_point<float>(P, xb, y);
-                        const float tau = optical_depth<float>(P, xi, xp) + optical_depth<float>(P, xp, y);
-                        row_accumulate<MG>(P, acc, (float)P.R0 * pt.w / dist2<float>(xb, y), tau);
+                        const float tau = optical_depth<float, XT>(P, xi, xp) + optical_depth<float, XT>(P, xp, y);
+                        row_accumulate<MG, XT>(P, acc, (float)P.R0 * pt.w / dist2<float>(xb, y), tau);
                     }
                     if constexpr (XT) {   // further walls, corner paths
                         for (int k = 0; k < P.n_extra; ++k) {
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(kColRows) aca_col_kernel(KernelParams P, const
                             for (int q = 0; q < nx; ++q) {
                                 const float4 pt = px[q];
                                 const Vec3<float> y = {pt.x, pt.y, pt.z};
-                                row_accumulate<MG>(P, acc, sc * pt.w / dist2<float>(src, y),
+                                row_accumulate<MG, XT>(P, acc, sc * pt.w / dist2<float>(src, y),
                                                    extra_tau<float>(P, k, xi, src, y));
                             }
                         }
@@ -384,7 +387,8 @@ static int grid_for(int64_t warps)
 }
 
 // Dispatch on the group count: the accumulator array is sized at compile time.
-// kernels with the further wall and corner terms (XT): 16 or 64 group slots
+// general kernels (XT: further walls and corner terms, a kappa grid, opaque
+// boxes): 16 or 64 group slots
 #define RT_DISPATCH_MG_XT(G, MACRO) \
     do {                            \
         if ((G) <= 16) {            \
@@ -430,7 +434,7 @@ static int launch_spans(Operator& op, const std::vector<EntrySpan>& spans_in, OU
 #define RT_LAUNCH_SPANS(MG, XT) \
     entries_span_kernel<R, OUT, MG, XT><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, d_sp, ns, total, out)
 #define RT_LAUNCH_SPANS1(MG) RT_LAUNCH_SPANS(MG, false)
-    if (op.kp.n_extra > 0) RT_DISPATCH_MG_XT(op.G, RT_LAUNCH_SPANS);
+    if (op.kp.ext) RT_DISPATCH_MG_XT(op.G, RT_LAUNCH_SPANS);
     else RT_DISPATCH_MG(op.G, RT_LAUNCH_SPANS1);
 #undef RT_LAUNCH_SPANS1
 #undef RT_LAUNCH_SPANS
@@ -491,7 +495,7 @@ int eval_entries(Operator& op, int group, int64_t count, const int32_t* rows, co
 #define RT_LAUNCH_PAIRS(MG, XT) \
     entries_pairs_kernel<double, MG, XT><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, group, count, rows, cols, ip, out)
 #define RT_LAUNCH_PAIRS1(MG) RT_LAUNCH_PAIRS(MG, false)
-        if (op.kp.n_extra > 0) RT_DISPATCH_MG_XT(op.G, RT_LAUNCH_PAIRS);
+        if (op.kp.ext) RT_DISPATCH_MG_XT(op.G, RT_LAUNCH_PAIRS);
         else RT_DISPATCH_MG(op.G, RT_LAUNCH_PAIRS1);
 #undef RT_LAUNCH_PAIRS1
 #undef RT_LAUNCH_PAIRS
@@ -499,7 +503,7 @@ int eval_entries(Operator& op, int group, int64_t count, const int32_t* rows, co
 #define RT_LAUNCH_PAIRS(MG, XT) \
     entries_pairs_kernel<float, MG, XT><<<grid, 32 * kWarpsPerCta, 0, s>>>(op.kp, group, count, rows, cols, ip, out)
 #define RT_LAUNCH_PAIRS1(MG) RT_LAUNCH_PAIRS(MG, false)
-        if (op.kp.n_extra > 0) RT_DISPATCH_MG_XT(op.G, RT_LAUNCH_PAIRS);
+        if (op.kp.ext) RT_DISPATCH_MG_XT(op.G, RT_LAUNCH_PAIRS);
         else RT_DISPATCH_MG(op.G, RT_LAUNCH_PAIRS1);
 #undef RT_LAUNCH_PAIRS1
 #undef RT_LAUNCH_PAIRS
@@ -670,7 +674,7 @@ struct RowItem {
 // handed out through a shared counter so that the few tetrahedra near x_i
 // (14-point rules) do not hold up a fixed partition.
 template <int MG, bool XT = false>
-__global__ void __launch_bounds__(256, MG <= 16 ? 2 : 1) row_cluster_kernel(KernelParams P, const RowItem* __restrict__ items,
+__global__ void __launch_bounds__(256, MG <= 16 && !XT ? 2 : 1) row_cluster_kernel(KernelParams P, const RowItem* __restrict__ items,
                                                           const int* __restrict__ sub_tets,
                                                           const int* __restrict__ istar, float* __restrict__ out)
 {
@@ -726,8 +730,11 @@ __global__ void __launch_bounds__(256, MG <= 16 ? 2 : 1) row_cluster_kernel(Kern
                 y.x = b0 * v0.x + b1 * v1.x + b2 * v2.x + b3 * v3.x;
                 y.y = b0 * v0.y + b1 * v1.y + b2 * v2.y + b3 * v3.y;
                 y.z = b0 * v0.z + b1 * v1.z + b2 * v2.z + b3 * v3.z;
-                const float wq = vol * tet_w<float>(row) * kappa_at<float>(P, y.x, y.y, y.z) * inv4pi;
+                const float wq = vol * tet_w<float>(row) * kappa_at<float, XT>(P, y.x, y.y, y.z) * inv4pi;
                 auto accumulate = [&](float w, float tau) {
+                    if constexpr (XT) {
+                        if (!(tau < INFINITY)) return;   // path through an opaque box
+                    }
                     if constexpr (MG > 0) {
                         auto add = [&](int g, float eg) {
                             const float val = w * P.cf[g] * eg;
@@ -762,10 +769,10 @@ __global__ void __launch_bounds__(256, MG <= 16 ? 2 : 1) row_cluster_kernel(Kern
                         }
                     }
                 };
-                if (pass == 0) accumulate(wq / dist2<float>(xi, y), optical_depth<float>(P, xi, y));
+                if (pass == 0) accumulate(wq / dist2<float>(xi, y), optical_depth<float, XT>(P, xi, y));
                 if (pass == 1 || share) {
                     const Vec3<float> xp = wall_point<float>(P, xb, y);
-                    const float tau = optical_depth<float>(P, xi, xp) + optical_depth<float>(P, xp, y);
+                    const float tau = optical_depth<float, XT>(P, xi, xp) + optical_depth<float, XT>(P, xp, y);
                     accumulate((float)P.R0 * wq / dist2<float>(xb, y), tau);
                 }
             }
@@ -787,7 +794,7 @@ __global__ void __launch_bounds__(256, MG <= 16 ? 2 : 1) row_cluster_kernel(Kern
                     const Vec3<float> y = {b0 * v0.x + b1 * v1.x + b2 * v2.x + b3 * v3.x,
                                            b0 * v0.y + b1 * v1.y + b2 * v2.y + b3 * v3.y,
                                            b0 * v0.z + b1 * v1.z + b2 * v2.z + b3 * v3.z};
-                    const float w = sc * vol * tet_w<float>(row) * kappa_at<float>(P, y.x, y.y, y.z) * inv4pi /
+                    const float w = sc * vol * tet_w<float>(row) * kappa_at<float, XT>(P, y.x, y.y, y.z) * inv4pi /
                                     dist2<float>(src, y);
                     const float tau = extra_tau<float>(P, k, xi, src, y);
                     if constexpr (MG > 0) {
@@ -924,7 +931,7 @@ static int launch_rows(Operator& op, const std::vector<RowItem>& items, const in
     for (size_t k0 = 0; k0 < items.size(); k0 += (size_t)1 << 30) {
         const int cnt = (int)std::min<size_t>(items.size() - k0, (size_t)1 << 30);
         const int G = op.G;
-        if (op.kp.n_extra > 0) {   // further walls or corner paths
+        if (op.kp.ext) {   // further walls, corner paths, a kappa grid or opaque boxes
             if (G <= 16) row_cluster_kernel<16, true><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
             else row_cluster_kernel<0, true><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
         } else if (G <= 1) row_cluster_kernel<1><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
@@ -1533,7 +1540,7 @@ int assemble_hmatrix(Operator& op, cudaStream_t s, std::string& err)
 #define RT_LAUNCH_ACAC(MG, XT) \
     aca_col_kernel<MG, XT><<<grid, kColRows, 0, s>>>(op.kp, d_act, na, nchunk, D.jstar, colbuf)
 #define RT_LAUNCH_ACAC1(MG) RT_LAUNCH_ACAC(MG, false)
-                    if (op.kp.n_extra > 0) RT_DISPATCH_MG_XT(G, RT_LAUNCH_ACAC);
+                    if (op.kp.ext) RT_DISPATCH_MG_XT(G, RT_LAUNCH_ACAC);
                     else RT_DISPATCH_MG(G, RT_LAUNCH_ACAC1);
 #undef RT_LAUNCH_ACAC1
 #undef RT_LAUNCH_ACAC

@@ -53,10 +53,47 @@ int validate(const rt_problem* P, const rt_hparams* H)
         if (!(P->walls[w].R0 >= 0.0 && P->walls[w].R0 <= 1.0)) return fail(RT_EINVAL, "R0 must lie in [0, 1]");
     }
     if (P->corner != 0 && P->corner != 1) return fail(RT_EINVAL, "corner must be 0 or 1");
-    if (P->kappa.kind != RT_KAPPA_CONST && P->kappa.kind != RT_KAPPA_SINPROD) return fail(RT_EINVAL, "kappa kind");
-    if (!(P->kappa.k0 >= 0.0) || !std::isfinite(P->kappa.k0)) return fail(RT_EINVAL, "kappa: k0 must be >= 0");
-    if (P->kappa.kind == RT_KAPPA_SINPROD && !(std::fabs(P->kappa.amp) <= P->kappa.k0))
-        return fail(RT_EINVAL, "kappa must stay nonnegative (|amp| <= k0)");
+    const rt_kappa& K = P->kappa;
+    if (K.kind != RT_KAPPA_CONST && K.kind != RT_KAPPA_SINPROD && K.kind != RT_KAPPA_GRID)
+        return fail(RT_EINVAL, "kappa kind");
+    if (K.kind == RT_KAPPA_GRID) {
+        if (!K.grid) return fail(RT_EINVAL, "kappa grid values missing");
+        int64_t cells = 1;
+        for (int d = 0; d < 3; ++d) {
+            if (K.dims[d] < 1 || K.dims[d] > RT_MAX_GRID_DIM) return fail(RT_EINVAL, "kappa grid dims must lie in [1, 512]");
+            if (!std::isfinite(K.bbox[d]) || !std::isfinite(K.bbox[3 + d]) || !(K.bbox[3 + d] > K.bbox[d]))
+                return fail(RT_EINVAL, "kappa grid box must be finite with x1 > x0");
+            cells *= K.dims[d];
+        }
+        for (int64_t c = 0; c < cells; ++c)
+            if (!(K.grid[c] >= 0.0f) || !std::isfinite(K.grid[c])) return fail(RT_EINVAL, "kappa grid values must be finite and >= 0");
+    } else {
+        if (!(K.k0 >= 0.0) || !std::isfinite(K.k0)) return fail(RT_EINVAL, "kappa: k0 must be >= 0");
+        if (K.kind == RT_KAPPA_SINPROD && !(std::fabs(K.amp) <= K.k0))
+            return fail(RT_EINVAL, "kappa must stay nonnegative (|amp| <= k0)");
+    }
+    if (P->n_obstacles < 0 || P->n_obstacles > RT_MAX_OBSTACLES) return fail(RT_EINVAL, "n_obstacles must lie in [0, 4]");
+    if (P->n_obstacles > 0 && !P->obstacles) return fail(RT_EINVAL, "obstacles pointer missing");
+    for (int o = 0; o < P->n_obstacles; ++o)
+        for (int d = 0; d < 3; ++d)
+            if (!std::isfinite(P->obstacles[o].lo[d]) || !std::isfinite(P->obstacles[o].hi[d]) ||
+                !(P->obstacles[o].hi[d] > P->obstacles[o].lo[d]))
+                return fail(RT_EINVAL, "obstacle box must be finite with hi > lo");
+    if (P->n_obstacles > 0) {
+        // Remark 1: the boxes are the hull's part outside the domain, so no
+        // tetrahedron may lie inside one (its centroid is a strict interior point)
+        for (int64_t t = 0; t < M.n_tet; ++t) {
+            double c[3] = {0, 0, 0};
+            for (int k = 0; k < 4; ++k)
+                for (int d = 0; d < 3; ++d) c[d] += 0.25 * M.xyz[3 * (int64_t)M.tet[4 * t + k] + d];
+            for (int o = 0; o < P->n_obstacles; ++o) {
+                const rt_box& B = P->obstacles[o];
+                if (c[0] > B.lo[0] && c[0] < B.hi[0] && c[1] > B.lo[1] && c[1] < B.hi[1] && c[2] > B.lo[2] &&
+                    c[2] < B.hi[2])
+                    return fail(RT_EINVAL, "a tetrahedron lies inside an opaque box");
+            }
+        }
+    }
     const rt_freqs& Fq = P->freqs;
     if (Fq.F < 1 || Fq.F > 4096) return fail(RT_EINVAL, "frequency count must be in [1, 4096]");
     if (!Fq.nu || !Fq.w || !Fq.c || !Fq.albedo) return fail(RT_EINVAL, "frequency arrays missing");
@@ -326,6 +363,29 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
     kp.kappa_kind = P->kappa.kind;
     kp.k0 = P->kappa.k0;
     kp.amp = P->kappa.kind == RT_KAPPA_SINPROD ? P->kappa.amp : 0.0;
+    if (P->kappa.kind == RT_KAPPA_GRID) {
+        kp.k0 = kp.amp = 0.0;
+        const int64_t cells = (int64_t)P->kappa.dims[0] * P->kappa.dims[1] * P->kappa.dims[2];
+        std::vector<float> g32(P->kappa.grid, P->kappa.grid + cells);
+        std::vector<double> g64(g32.begin(), g32.end());
+        float* d32 = nullptr;
+        double* d64 = nullptr;
+        if ((rc = upload(op, &d32, g32, err))) return rc;
+        if ((rc = upload(op, &d64, g64, err))) return rc;
+        kp.kgrid32 = d32;
+        kp.kgrid64 = d64;
+        for (int d = 0; d < 3; ++d) {
+            kp.gdims[d] = P->kappa.dims[d];
+            kp.glo[d] = P->kappa.bbox[d];
+            kp.ghi[d] = P->kappa.bbox[3 + d];
+        }
+    }
+    kp.n_obst = P->n_obstacles;
+    for (int o = 0; o < P->n_obstacles; ++o)
+        for (int d = 0; d < 3; ++d) {
+            kp.olo[o][d] = P->obstacles[o].lo[d];
+            kp.ohi[o][d] = P->obstacles[o].hi[d];
+        }
     kp.k0f = (float)kp.k0;
     kp.ampf = (float)kp.amp;
     // the first wall keeps its own fields (the one-wall kernels' path); the
@@ -365,6 +425,7 @@ int build(rt::Operator& op, const rt_problem* P, const rt_hparams* H, cudaStream
                 kp.xb[kp.n_extra] = b;
                 ++kp.n_extra;
             }
+    kp.ext = (kp.n_extra > 0 || kp.n_obst > 0 || kp.kappa_kind == RT_KAPPA_GRID) ? 1 : 0;
     kp.G = op.G;
     for (int g = 0; g < op.G; ++g) {
         kp.c[g] = op.gc[g];

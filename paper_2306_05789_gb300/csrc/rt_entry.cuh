@@ -153,9 +153,37 @@ __device__ __forceinline__ R dist2(const Vec3<R>& a, const Vec3<R>& b)
     return dx * dx + dy * dy + dz * dz;
 }
 
+// ---- cellwise-constant grid (RT_KAPPA_GRID), general instances only ---------
 template <class R>
+__device__ __forceinline__ R grid_value(const KernelParams& P, int idx);
+template <>
+__device__ __forceinline__ float grid_value<float>(const KernelParams& P, int idx) { return __ldg(P.kgrid32 + idx); }
+template <>
+__device__ __forceinline__ double grid_value<double>(const KernelParams& P, int idx) { return __ldg(P.kgrid64 + idx); }
+
+// cell index along axis d of coordinate x, clamped to the grid
+template <class R>
+__device__ __forceinline__ int grid_cell(const KernelParams& P, int d, R x)
+{
+    R u = (x - R(P.glo[d])) / (R(P.ghi[d]) - R(P.glo[d])) * R(P.gdims[d]);
+    u = u < R(0) ? R(0) : (u > R(P.gdims[d]) - R(0.5) ? R(P.gdims[d]) - R(0.5) : u);
+    return (int)floor(u);
+}
+
+template <class R>
+__device__ __forceinline__ R grid_kappa(const KernelParams& P, R x, R y, R z)
+{
+    const int i = grid_cell<R>(P, 0, x), j = grid_cell<R>(P, 1, y), k = grid_cell<R>(P, 2, z);
+    return grid_value<R>(P, i + P.gdims[0] * (j + P.gdims[1] * k));
+}
+
+// XT: the general instances, which also know the grid
+template <class R, bool XT = false>
 __device__ __forceinline__ R kappa_at(const KernelParams& P, R x, R y, R z)
 {
+    if constexpr (XT) {
+        if (P.kappa_kind == RT_KAPPA_GRID) return grid_kappa<R>(P, x, y, z);
+    }
     R k = kp_k0<R>(P);
     if (P.kappa_kind == RT_KAPPA_SINPROD)
         k += kp_amp<R>(P) * sin2pi(x) * sin2pi(y) * sin2pi(z);
@@ -191,11 +219,104 @@ __device__ __forceinline__ float gauss_sum_sinprod(const KernelParams& P, const 
     return P.k0f + 0.25f * P.ampf * S;
 }
 
-// int_[a,b] kappa = |b-a| sum_g (w_g/2) kappa(a + u_g (b-a)).  For constant
-// kappa the Gauss sum equals kappa |b-a| exactly (weights sum to 1).
+// Exact int_[a,b] kappa for the cellwise-constant grid: walk the grid planes
+// the segment crosses in order of the segment parameter t (one next crossing
+// per axis, the smallest first); each piece [t0, t1] adds the value of the
+// cell holding its midpoint times its length.  Planes are x = glo + m h,
+// m = 1 .. dims-1; a crossing counts when 0 < t < 1.
 template <class R>
+__device__ R grid_depth(const KernelParams& P, const Vec3<R>& a, const Vec3<R>& b)
+{
+    const R A[3] = {a.x, a.y, a.z};
+    const R D[3] = {b.x - a.x, b.y - a.y, b.z - a.z};
+    const R L = sqrt_r(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+    R tn[3], h[3];
+    int m[3], st[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        h[d] = (R(P.ghi[d]) - R(P.glo[d])) / R(P.gdims[d]);
+        st[d] = D[d] > R(0) ? 1 : -1;
+        tn[d] = R(2);
+        m[d] = 0;
+        if (D[d] != R(0)) {
+            const R u = (A[d] - R(P.glo[d])) / h[d];
+            const R uc = u < R(-1) ? R(-1) : (u > R(P.gdims[d] + 1) ? R(P.gdims[d] + 1) : u);
+            m[d] = D[d] > R(0) ? max((int)floor(uc) + 1, 1) : min((int)ceil(uc) - 1, P.gdims[d] - 1);
+            // first plane strictly ahead of a (rounding may put the first guess behind)
+            for (int it = 0; it < 3; ++it) {
+                if (m[d] < 1 || m[d] > P.gdims[d] - 1) break;
+                const R t = (R(P.glo[d]) + R(m[d]) * h[d] - A[d]) / D[d];
+                if (t > R(0)) break;
+                m[d] += st[d];
+            }
+            if (m[d] >= 1 && m[d] <= P.gdims[d] - 1) tn[d] = (R(P.glo[d]) + R(m[d]) * h[d] - A[d]) / D[d];
+        }
+    }
+    R s = R(0), t0 = R(0);
+    const int max_steps = P.gdims[0] + P.gdims[1] + P.gdims[2] + 4;
+    for (int step = 0; step < max_steps; ++step) {
+        R t1 = tn[0] < tn[1] ? tn[0] : tn[1];
+        t1 = t1 < tn[2] ? t1 : tn[2];
+        t1 = t1 < R(1) ? t1 : R(1);
+        if (t1 > t0) {
+            const R tm = R(0.5) * (t0 + t1);
+            s += grid_kappa<R>(P, A[0] + tm * D[0], A[1] + tm * D[1], A[2] + tm * D[2]) * (t1 - t0);
+            t0 = t1;
+        }
+        if (t1 >= R(1)) break;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (tn[d] == t1) {
+                m[d] += st[d];
+                tn[d] = (m[d] >= 1 && m[d] <= P.gdims[d] - 1) ? (R(P.glo[d]) + R(m[d]) * h[d] - A[d]) / D[d] : R(2);
+            }
+    }
+    return L * s;
+}
+
+// Does the open segment (a, b) cross the interior of an opaque box?  Slab
+// clipping of the parameter interval per axis; blocked when what is left is
+// longer than 1e-6 (in units of the segment).
+template <class R>
+__device__ bool path_blocked(const KernelParams& P, const Vec3<R>& a, const Vec3<R>& b)
+{
+    const R A[3] = {a.x, a.y, a.z};
+    const R D[3] = {b.x - a.x, b.y - a.y, b.z - a.z};
+    for (int o = 0; o < P.n_obst; ++o) {
+        R t0 = R(0), t1 = R(1);
+        bool inside = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const R lo = R(P.olo[o][d]), hi = R(P.ohi[o][d]);
+            if (D[d] == R(0)) {
+                if (!(A[d] > lo && A[d] < hi)) inside = false;
+                continue;
+            }
+            R ta = (lo - A[d]) / D[d], tb = (hi - A[d]) / D[d];
+            if (ta > tb) {
+                const R tmp = ta;
+                ta = tb;
+                tb = tmp;
+            }
+            t0 = ta > t0 ? ta : t0;
+            t1 = tb < t1 ? tb : t1;
+        }
+        if (inside && t1 - t0 > R(1e-6)) return true;
+    }
+    return false;
+}
+
+// int_[a,b] kappa = |b-a| sum_g (w_g/2) kappa(a + u_g (b-a)).  For constant
+// kappa the Gauss sum equals kappa |b-a| exactly (weights sum to 1).  The
+// general instances (XT) also handle the opaque boxes (+infinity) and the
+// grid (exact integral).
+template <class R, bool XT = false>
 __device__ __forceinline__ R optical_depth(const KernelParams& P, const Vec3<R>& a, const Vec3<R>& b)
 {
+    if constexpr (XT) {
+        if (P.n_obst > 0 && path_blocked<R>(P, a, b)) return R(INFINITY);
+        if (P.kappa_kind == RT_KAPPA_GRID) return grid_depth<R>(P, a, b);
+    }
     R dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
     R L = sqrt_r(dx * dx + dy * dy + dz * dz);
     if (P.kappa_kind != RT_KAPPA_SINPROD) return kp_k0<R>(P) * L;
@@ -270,7 +391,7 @@ __device__ __forceinline__ R extra_tau(const KernelParams& P, int k, const Vec3<
         const R den = sb - sy;
         const R t = den > R(0) ? sb / den : R(0);
         const Vec3<R> xp = {src.x + t * (y.x - src.x), src.y + t * (y.y - src.y), src.z + t * (y.z - src.z)};
-        return optical_depth<R>(P, x, xp) + optical_depth<R>(P, xp, y);
+        return optical_depth<R, true>(P, x, xp) + optical_depth<R, true>(P, xp, y);
     }
     const int b = P.xb[k];
     const R sya = wall_side<R>(P, a, y), sza = wall_side<R>(P, a, src);
@@ -281,7 +402,7 @@ __device__ __forceinline__ R extra_tau(const KernelParams& P, int k, const Vec3<
     const Vec3<R> Q = {y.x + t1 * (src.x - y.x), y.y + t1 * (src.y - y.y), y.z + t1 * (src.z - y.z)};
     const Vec3<R> U = {y.x + t2 * (src.x - y.x), y.y + t2 * (src.y - y.y), y.z + t2 * (src.z - y.z)};
     const Vec3<R> Pp = mirror_w<R>(P, afirst ? a : b, U);
-    return optical_depth<R>(P, x, Pp) + optical_depth<R>(P, Pp, Q) + optical_depth<R>(P, Q, y);
+    return optical_depth<R, true>(P, x, Pp) + optical_depth<R, true>(P, Pp, Q) + optical_depth<R, true>(P, Q, y);
 }
 
 // Term t of the kernel at x, t < 2 + P.n_extra: 0 the direct path, 1 the first
@@ -303,10 +424,10 @@ template <class R>
 __device__ __forceinline__ R term_depth(const KernelParams& P, int t, const Vec3<R>& xi, const Vec3<R>& src,
                                         const Vec3<R>& y)
 {
-    if (t == 0) return optical_depth<R>(P, xi, y);
+    if (t == 0) return optical_depth<R, true>(P, xi, y);
     if (t == 1) {
         const Vec3<R> xp = wall_point<R>(P, src, y);
-        return optical_depth<R>(P, xi, xp) + optical_depth<R>(P, xp, y);
+        return optical_depth<R, true>(P, xi, xp) + optical_depth<R, true>(P, xp, y);
     }
     return extra_tau<R>(P, t - 2, xi, src, y);
 }
@@ -379,13 +500,16 @@ __device__ void entry_warp(const KernelParams& P, int i, int j, R (&acc)[MG], in
             R r2, tau;
             if (!refl) {
                 r2 = dist2<R>(xi, y);
-                tau = optical_depth<R>(P, xi, y);
+                tau = optical_depth<R, XT>(P, xi, y);
             } else {
                 Vec3<R> xp = wall_point<R>(P, xb, y);
                 r2 = dist2<R>(xb, y);
-                tau = optical_depth<R>(P, xi, xp) + optical_depth<R>(P, xp, y);
+                tau = optical_depth<R, XT>(P, xi, xp) + optical_depth<R, XT>(P, xp, y);
             }
-            R w = vol * tet_w<R>(row) * lam * kappa_at<R>(P, y.x, y.y, y.z) * inv4pi / r2;
+            if constexpr (XT) {
+                if (!(tau < R(INFINITY))) continue;   // path through an opaque box
+            }
+            R w = vol * tet_w<R>(row) * lam * kappa_at<R, XT>(P, y.x, y.y, y.z) * inv4pi / r2;
             if (refl) w *= R(P.R0);
             bool done = false;
             if constexpr (sizeof(R) == 4) {
@@ -435,7 +559,7 @@ __device__ void entry_warp(const KernelParams& P, int i, int j, R (&acc)[MG], in
                                    b0 * v0.z + b1 * v1.z + b2 * v2.z + b3 * v3.z};
                 const R lam = loc == 0 ? b0 : (loc == 1 ? b1 : (loc == 2 ? b2 : b3));
                 const R tau = extra_tau<R>(P, k, xi, src, y);
-                const R w = scale * vol * tet_w<R>(row) * lam * kappa_at<R>(P, y.x, y.y, y.z) * inv4pi / dist2<R>(src, y);
+                const R w = scale * vol * tet_w<R>(row) * lam * kappa_at<R, true>(P, y.x, y.y, y.z) * inv4pi / dist2<R>(src, y);
 #pragma unroll
                 for (int g = 0; g < MG; ++g)
                     if (g < P.G) {

@@ -26,6 +26,7 @@ namespace rt {
 constexpr int kMaxGroups = 64;
 constexpr int kMaxWalls = 3;     // planar reflective walls per problem
 constexpr int kMaxXTerms = 5;    // reflected terms beyond the first wall's: 2 walls + 3 corners
+constexpr int kMaxObst = 4;      // opaque boxes per problem
 constexpr int kMaxGauss = 32;
 constexpr int kSubCols = 256;   // columns per sub-cluster in row evaluations
 constexpr double kPi = 3.14159265358979323846;
@@ -51,6 +52,17 @@ struct KernelParams {
     int n_extra;
     int xkind[kMaxXTerms], xa[kMaxXTerms], xb[kMaxXTerms];
     double wps[kMaxWalls][3], wns[kMaxWalls][3], wR[kMaxWalls];
+    // cellwise-constant kappa (kappa_kind == RT_KAPPA_GRID): gdims cells of the
+    // box [glo, ghi], values in kgrid32 / kgrid64
+    const float* kgrid32;
+    const double* kgrid64;
+    int gdims[3];
+    double glo[3], ghi[3];
+    // opaque boxes (kappa = +infinity inside)
+    int n_obst;
+    double olo[kMaxObst][3], ohi[kMaxObst][3];
+    // the instance needs the general kernels (further walls, grid or obstacles)
+    int ext;
     int G;              // groups
     double c[kMaxGroups];
     float cf[kMaxGroups];

@@ -40,6 +40,8 @@ struct Request {
     std::vector<double> xyz;
     std::vector<int32_t> tet, emit;
     std::vector<rt_wall> walls;
+    std::vector<float> kgrid;
+    std::vector<rt_box> obstacles;
     std::vector<double> nu, w, c, albedo;
     std::vector<int32_t> group;
     Plan plan;
@@ -292,6 +294,9 @@ int rt_submit(rt_server* h, const rt_problem* P, int64_t* id)
         r->tet.assign(P->mesh.tet, P->mesh.tet + 4 * T);
         if (P->n_emit > 0) r->emit.assign(P->emit_tri, P->emit_tri + 3 * P->n_emit);
         if (P->n_walls > 0) r->walls.assign(P->walls, P->walls + P->n_walls);
+        if (P->kappa.kind == RT_KAPPA_GRID)
+            r->kgrid.assign(P->kappa.grid, P->kappa.grid + (int64_t)P->kappa.dims[0] * P->kappa.dims[1] * P->kappa.dims[2]);
+        if (P->n_obstacles > 0) r->obstacles.assign(P->obstacles, P->obstacles + P->n_obstacles);
         r->nu.assign(P->freqs.nu, P->freqs.nu + F);
         r->w.assign(P->freqs.w, P->freqs.w + F);
         r->c.assign(P->freqs.c, P->freqs.c + F);
@@ -302,6 +307,8 @@ int rt_submit(rt_server* h, const rt_problem* P, int64_t* id)
         r->prob.mesh.tet = r->tet.data();
         r->prob.emit_tri = r->emit.empty() ? nullptr : r->emit.data();
         r->prob.walls = r->walls.empty() ? nullptr : r->walls.data();
+        r->prob.kappa.grid = r->kgrid.empty() ? nullptr : r->kgrid.data();
+        r->prob.obstacles = r->obstacles.empty() ? nullptr : r->obstacles.data();
         r->prob.freqs.nu = r->nu.data();
         r->prob.freqs.w = r->w.data();
         r->prob.freqs.c = r->c.data();
