@@ -181,7 +181,7 @@ def run_batch(args):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        b = rt.rt_build_batch(probs, hp, threads=8, tune=args.tune, stream=stream)
+        b = rt.rt_build_batch(probs, hp, threads=args.build_threads, tune=args.tune, stream=stream)
         J = torch.zeros(int(b.vec_off[-1]), dtype=torch.float32, device=dev)
         T = torch.zeros(int(b.vert_off[-1]), dtype=torch.float64, device=dev)
         iters, st = b.solve(J, T, tol=args.tol, max_iter=300, check_every=4, stream=stream)
@@ -250,7 +250,7 @@ def run_batch(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "instances": n, "instances_per_rank": n, "parallelism": f"shards{world}",
                    "n_range": [8, 24], "F_range": [1, 8],
-                   "amp_range": [0.0, 0.8], "tol": args.tol, "autotune": bool(args.tune),
+                   "amp_range": [0.0, 0.8], "tol": args.tol, "autotune": bool(args.tune), "build_threads": args.build_threads,
                    "l2": "batch operators larger than L2"},
         "roofline": {"bound": "hbm", "kernel": "batch_apply_kernel (persistent, all instances)", "achieved": gbs,
                      "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
@@ -861,7 +861,10 @@ def main():
     ap.add_argument("--compare-f32", action="store_true", help="also time one plain FP32 solve of the workload")
     ap.add_argument("--residual-rows", type=int, default=32, help="oracle rows of the one-step residual")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-tune", dest="tune", action="store_false")
+    ap.add_argument("--tune", dest="tune", action="store_true",
+                    help="batch: time candidate work-item and grid sizes during the build (default: the library's "
+                         "defaults, measured on GB300)")
+    ap.add_argument("--build-threads", type=int, default=16, help="batch: host threads building the operators")
     ap.add_argument("--requests", type=int, default=24, help="serve: requests in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (1/s)")
     ap.add_argument("--seed", type=int, default=0, help="serve: request stream seed")

@@ -65,7 +65,7 @@ struct Batch {
     int64_t* d_voff = nullptr;
     int64_t* d_toff = nullptr;
     int ctas = 0;
-    int p1_bytes = 48 << 10, ctas_per_sm = 4;
+    int p1_bytes = 64 << 10, ctas_per_sm = 8;   // the autotuner's pick for 256 mixed instances on GB300
     long long spin_cycles = 0;   // wait budget of the phase-2 items (0: kSpinCycles)
     int spin_extra = 0;          // diagnostic: completed phase-1 items a wait needs beyond all of them
     double tune_ms = 0.0, build_ms = 0.0;
