@@ -207,8 +207,9 @@ __device__ __forceinline__ int find_active(const AcaActive* a, int na, int64_t e
 constexpr int kColRows = 64;
 constexpr int kColTets = 32;
 
-// acc[g] += w c_g exp(-c_g tau) over the groups (Eq. 5 with the group scale
-// c_g of the multi-frequency operator); exp recurrence when c_g is arithmetic.
+// acc[g] += w exp(-c_g tau) over the groups; the factor c_g of Eq. 5 (the
+// group scale of the multi-frequency operator) multiplies the finished sums.
+// exp recurrence when c_g is arithmetic.
 template <int MG, bool XT = false>
 __device__ __forceinline__ void row_accumulate(const KernelParams& P, float (&acc)[MG], float w, float tau)
 {
@@ -220,13 +221,13 @@ __device__ __forceinline__ void row_accumulate(const KernelParams& P, float (&ac
         const float D = expf(-P.dcf * tau);
 #pragma unroll
         for (int g = 0; g < MG; ++g) {
-            if (g < P.G) acc[g] += w * P.cf[g] * E;
+            if (g < P.G) acc[g] += w * E;
             E *= D;
         }
     } else {
 #pragma unroll
         for (int g = 0; g < MG; ++g)
-            if (g < P.G) acc[g] += w * P.cf[g] * expf(-P.cf[g] * tau);
+            if (g < P.G) acc[g] += w * expf(-P.cf[g] * tau);
     }
 }
 
@@ -345,7 +346,7 @@ __global__ void __launch_bounds__(kColRows) aca_col_kernel(KernelParams P, const
         if (row_ok) {
 #pragma unroll
             for (int g = 0; g < MG; ++g)
-                if (g < P.G) buf[a.cbuf + (int64_t)g * a.m + pos] = acc[g];
+                if (g < P.G) buf[a.cbuf + (int64_t)g * a.m + pos] = acc[g] * P.cf[g];
         }
         count_work(P, n_terms, n_depths);
     }
@@ -736,12 +737,13 @@ __global__ void __launch_bounds__(256, MG <= 16 && !XT ? 2 : 1) row_cluster_kern
                         if (!(tau < INFINITY)) return;   // path through an opaque box
                     }
                     if constexpr (MG > 0) {
+                        // c_g multiplies the sums when they are flushed
+                        const float w0 = w * b0, w1 = w * b1, w2 = w * b2, w3 = w * b3;
                         auto add = [&](int g, float eg) {
-                            const float val = w * P.cf[g] * eg;
-                            a0[g] += val * b0;
-                            a1[g] += val * b1;
-                            a2[g] += val * b2;
-                            a3[g] += val * b3;
+                            a0[g] += w0 * eg;
+                            a1[g] += w1 * eg;
+                            a2[g] += w2 * eg;
+                            a3[g] += w3 * eg;
                         };
                         if (P.c_arith) {
                             // exp(-c_g tau) as exp(-c_0 tau) exp(-dc tau)^g: two SFU exponentials per point
@@ -801,7 +803,7 @@ __global__ void __launch_bounds__(256, MG <= 16 && !XT ? 2 : 1) row_cluster_kern
 #pragma unroll
                         for (int g = 0; g < MG; ++g)
                             if (g < G) {
-                                const float val = w * P.cf[g] * expf(-P.cf[g] * tau);
+                                const float val = w * expf(-P.cf[g] * tau);   // c_g at the flush
                                 a0[g] += val * b0;
                                 a1[g] += val * b1;
                                 a2[g] += val * b2;
@@ -825,10 +827,11 @@ __global__ void __launch_bounds__(256, MG <= 16 && !XT ? 2 : 1) row_cluster_kern
             for (int g = 0; g < MG; ++g)
                 if (g < G) {
                     float* a = acc + g * n;
-                    if (in0) atomicAdd(a + jj[0], a0[g]);
-                    if (in1) atomicAdd(a + jj[1], a1[g]);
-                    if (in2) atomicAdd(a + jj[2], a2[g]);
-                    if (in3) atomicAdd(a + jj[3], a3[g]);
+                    const float cg = P.cf[g];
+                    if (in0) atomicAdd(a + jj[0], a0[g] * cg);
+                    if (in1) atomicAdd(a + jj[1], a1[g] * cg);
+                    if (in2) atomicAdd(a + jj[2], a2[g] * cg);
+                    if (in3) atomicAdd(a + jj[3], a3[g] * cg);
                 }
         }
     }
