@@ -87,6 +87,19 @@ __device__ __forceinline__ float sin2pi(float x)
     return (((int)n) & 1) ? -v : v;
 }
 __device__ __forceinline__ double sin2pi(double x) { return sinpi(2.0 * x); }
+
+// sin(2 pi x) on the special-function unit, for values that enter only through
+// products of magnitude <= 1 (the sines of the sin-product kappa and of the
+// midpoints in its line integral): sin has period 1 in x, so x - rint(x) in
+// [-1/2, 1/2] keeps the argument of __sinf in [-pi, pi], where its absolute
+// error stays below 4e-7.  The sinc quotients keep the polynomial sin2pi,
+// whose relative accuracy near zero they need.
+__device__ __forceinline__ float sin2pi_sfu(float x)
+{
+    const float t = x - rintf(x);
+    return __sinf(6.28318530717958647692f * t);
+}
+__device__ __forceinline__ double sin2pi_sfu(double x) { return sin2pi(x); }
 __device__ __forceinline__ float exp_r(float x) { return expf(x); }
 __device__ __forceinline__ double exp_r(double x) { return exp(x); }
 __device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
@@ -186,7 +199,7 @@ __device__ __forceinline__ R kappa_at(const KernelParams& P, R x, R y, R z)
     }
     R k = kp_k0<R>(P);
     if (P.kappa_kind == RT_KAPPA_SINPROD)
-        k += kp_amp<R>(P) * sin2pi(x) * sin2pi(y) * sin2pi(z);
+        k += kp_amp<R>(P) * sin2pi_sfu(x) * sin2pi_sfu(y) * sin2pi_sfu(z);
     return k;
 }
 
@@ -214,8 +227,8 @@ __device__ __forceinline__ float gauss_sum_sinprod(const KernelParams& P, const 
                                                    float dz)
 {
     const float mx = a.x + 0.5f * dx, my = a.y + 0.5f * dy, mz = a.z + 0.5f * dz;
-    const float S = sin2pi(mx + my - mz) * sinc_pi(dx + dy - dz) + sin2pi(-mx + my + mz) * sinc_pi(-dx + dy + dz) +
-                    sin2pi(mx - my + mz) * sinc_pi(dx - dy + dz) - sin2pi(mx + my + mz) * sinc_pi(dx + dy + dz);
+    const float S = sin2pi_sfu(mx + my - mz) * sinc_pi(dx + dy - dz) + sin2pi_sfu(-mx + my + mz) * sinc_pi(-dx + dy + dz) +
+                    sin2pi_sfu(mx - my + mz) * sinc_pi(dx - dy + dz) - sin2pi_sfu(mx + my + mz) * sinc_pi(dx + dy + dz);
     return P.k0f + 0.25f * P.ampf * S;
 }
 
