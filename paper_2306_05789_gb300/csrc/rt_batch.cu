@@ -25,6 +25,7 @@
 
 #include "rt_hmv_dev.cuh"
 #include "rt_internal.h"
+#include "rt_newton.cuh"
 
 namespace rt {
 
@@ -65,6 +66,7 @@ struct Batch {
     int64_t* d_voff = nullptr;
     int64_t* d_toff = nullptr;
     int ctas = 0;
+    int maxF = 1;                          // largest frequency count of the instances
     int p1_bytes = 64 << 10, ctas_per_sm = 8;   // the autotuner's pick for 256 mixed instances on GB300
     long long spin_cycles = 0;   // wait budget of the phase-2 items (0: kSpinCycles)
     int spin_extra = 0;          // diagnostic: completed phase-1 items a wait needs beyond all of them
@@ -261,85 +263,44 @@ __global__ void __launch_bounds__(256) batch_update(const BatchInst* __restrict_
     }
 }
 
-__device__ __forceinline__ void planck_sum_b(const double* __restrict__ fq, int F, double t, int lane, double& g,
-                                             double& dg)
-{
-    g = 0.0;
-    dg = 0.0;
-    if (t > 0.0) {
-        for (int f = lane; f < F; f += 32) {
-            const double nu = fq[4 * f], wt = fq[4 * f + 1];
-            const double x = nu / t;
-            if (x < 700.0) {
-                const double em = expm1(x);
-                const double B = nu * nu * nu / em;
-                g += wt * B;
-                dg += wt * B * (x / t) * (1.0 + 1.0 / em);
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        g += __shfl_xor_sync(0xffffffffu, g, o);
-        dg += __shfl_xor_sync(0xffffffffu, dg, o);
-    }
-}
-
-// warp per vertex, same safeguarded FP64 Newton as the single-instance solver
+// LPV lanes per vertex (the power of two >= the batch's largest F), the same
+// temperature solve as the single-instance solver (rt_newton.cuh)
+template <int LPV>
 __global__ void __launch_bounds__(256) batch_newton(const BatchInst* __restrict__ insts,
                                                     const int64_t* __restrict__ toff, int n, int64_t total,
                                                     const float* __restrict__ J, double* __restrict__ T,
                                                     const int* __restrict__ active, int* __restrict__ fail)
 {
-    const int lane = threadIdx.x & 31;
+    constexpr int VPW = 32 / LPV;
+    const int lane = threadIdx.x & 31, sl = lane & (LPV - 1);
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t v = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < total; v += nw) {
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * VPW; base < total;
+         base += nw * VPW) {
+        const int64_t v = base + lane / LPV;
+        if (v >= total) continue;   // whole vertex segments drop out together
         const int b = find_seg(toff, n, v);
         if (!active[b]) continue;
         const BatchInst I = insts[b];
         const int i = (int)(v - I.toff);
         if (I.grey) {
-            if (lane == 0) {
+            if (sl == 0) {
                 const double j = (double)J[I.voff + i];
                 T[v] = j > 0.0 ? sqrt(sqrt(j / kSigmaB)) : 0.0;
             }
             continue;
         }
+        const unsigned m = seg_mask<LPV>(lane);
         double rhs = 0.0;
-        for (int f = lane; f < I.F; f += 32) rhs += I.fq[4 * f + 1] * (double)J[I.voff + (int64_t)f * I.N + i];
+        for (int f = sl; f < I.F; f += LPV) rhs += I.fq[4 * f + 1] * (double)J[I.voff + (int64_t)f * I.N + i];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) rhs += __shfl_xor_sync(0xffffffffu, rhs, o);
+        for (int o = LPV >> 1; o > 0; o >>= 1) rhs += __shfl_xor_sync(m, rhs, o);
         if (!(rhs > 0.0)) {
-            if (lane == 0) T[v] = 0.0;
+            if (sl == 0) T[v] = 0.0;
             continue;
         }
-        const double tp = T[v];
-        double lo = 0.0, hi = fmax(1.0, 2.0 * tp), g, dg;
-        planck_sum_b(I.fq, I.F, hi, lane, g, dg);
-        int guard = 0;
-        while (g < rhs && guard < 200) {
-            lo = hi;
-            hi *= 2.0;
-            planck_sum_b(I.fq, I.F, hi, lane, g, dg);
-            ++guard;
-        }
-        double t = (tp > lo && tp < hi) ? tp : 0.5 * (lo + hi);
-        bool ok = false;
-        for (int it = 0; it < 100; ++it) {
-            planck_sum_b(I.fq, I.F, t, lane, g, dg);
-            const double fv = g - rhs;
-            if (fv < 0.0) lo = t;
-            if (fv > 0.0) hi = t;
-            double tn = dg > 0.0 ? t - fv / dg : 0.5 * (lo + hi);
-            if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
-            const bool done = fabs(tn - t) <= 1e-14 * fabs(tn);
-            t = tn;
-            if (done || fv == 0.0) {
-                ok = true;
-                break;
-            }
-        }
-        if (lane == 0) {
+        double t = 0.0;
+        const bool ok = solve_temperature<LPV>(I.fq, I.F, rhs, lane, T[v], t);
+        if (sl == 0) {
             if (!ok) atomicOr(fail, 1);
             T[v] = t;
         }
@@ -596,6 +557,7 @@ int rt_build_batch(const rt_problem* probs, int64_t count, const rt_hparams* hp,
             return bfail(RT_EINVAL, "batch instances must have at most 16 kappa groups");
         }
         B.voff[k + 1] = B.voff[k] + (int64_t)op.F * op.N;
+        B.maxF = std::max(B.maxF, op.F);
         B.toff[k + 1] = B.toff[k] + op.N;
     }
     B.total_vec = B.voff[count];
@@ -703,8 +665,20 @@ int rt_solve_batch(rt_batch* h, const rt_solve_opts* o, float* J, double* T, int
         int rc = launch_apply(B, B.d_S, B.d_Y, B.d_active, cs, err);
         if (rc) return rc;
         batch_update<<<B.n, 256, 0, cs>>>(B.d_inst, B.d_J, B.d_Y, B.d_SE, B.d_active, B.d_done_now, o->tol);
-        const int gn = (int)std::max<int64_t>(1, std::min<int64_t>((B.total_vert + 7) / 8, 152 * 32));
-        batch_newton<<<gn, 256, 0, cs>>>(B.d_inst, B.d_toff, B.n, B.total_vert, B.d_J, B.d_T, B.d_active, d_fail);
+        const int lpv = B.maxF <= 1 ? 1 : B.maxF <= 2 ? 2 : B.maxF <= 4 ? 4 : B.maxF <= 8 ? 8 : B.maxF <= 16 ? 16 : 32;
+        const int64_t warps = (B.total_vert * lpv + 31) / 32;
+        const int gn = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, 152 * 32));
+#define RT_BNEWTON(L) \
+    batch_newton<L><<<gn, 256, 0, cs>>>(B.d_inst, B.d_toff, B.n, B.total_vert, B.d_J, B.d_T, B.d_active, d_fail)
+        switch (lpv) {
+            case 1: RT_BNEWTON(1); break;
+            case 2: RT_BNEWTON(2); break;
+            case 4: RT_BNEWTON(4); break;
+            case 8: RT_BNEWTON(8); break;
+            case 16: RT_BNEWTON(16); break;
+            default: RT_BNEWTON(32); break;
+        }
+#undef RT_BNEWTON
         batch_flags<<<1, 256, 0, cs>>>(B.d_active, B.d_done_now, B.d_iters, B.n, B.d_nactive);
         return cudaGetLastError() == cudaSuccess ? RT_OK : RT_ECUDA;
     };

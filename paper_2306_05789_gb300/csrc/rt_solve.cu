@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "rt_internal.h"
+#include "rt_newton.cuh"
 
 namespace rt {
 
@@ -120,84 +121,37 @@ __global__ void fp_reduce(const double* __restrict__ part, int nparts, double* r
     }
 }
 
-// temperature from the Planck balance: one warp per vertex, lanes over the
-// frequencies; B_nu and dB_nu/dT share one expm1 per frequency and Newton step:
-//   B = nu^3 / em,  dB/dT = B (x / T) (1 + 1/em),  em = expm1(x),  x = nu / T.
-__device__ __forceinline__ void planck_sum(const double* __restrict__ fq, int F, double t, int lane, double& g,
-                                           double& dg)
-{
-    g = 0.0;
-    dg = 0.0;
-    if (t > 0.0) {
-        for (int f = lane; f < F; f += 32) {
-            const double nu = fq[4 * f], wt = fq[4 * f + 1];
-            const double x = nu / t;
-            if (x < 700.0) {
-                const double em = expm1(x);
-                const double B = nu * nu * nu / em;
-                g += wt * B;
-                dg += wt * B * (x / t) * (1.0 + 1.0 / em);
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        g += __shfl_xor_sync(0xffffffffu, g, o);
-        dg += __shfl_xor_sync(0xffffffffu, dg, o);
-    }
-}
-
-template <class V>
+template <class V, int LPV>
 __global__ void __launch_bounds__(256) fp_newton(const V* __restrict__ J, double* __restrict__ T,
                                                  const double* __restrict__ fq, int N, int F, int grey,
                                                  int* __restrict__ fail)
 {
-    const int lane = threadIdx.x & 31;
+    constexpr int VPW = 32 / LPV;
+    const int lane = threadIdx.x & 31, sl = lane & (LPV - 1);
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += nw) {
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * VPW; base < N;
+         base += nw * VPW) {
+        const int64_t i = base + lane / LPV;
+        if (i >= N) continue;   // whole vertex segments drop out together
         if (grey) {
-            if (lane == 0) {
+            if (sl == 0) {
                 const double j = (double)J[i];
                 T[i] = j > 0.0 ? sqrt(sqrt(j / kSigma)) : 0.0;
             }
             continue;
         }
+        const unsigned m = seg_mask<LPV>(lane);
         double rhs = 0.0;
-        for (int f = lane; f < F; f += 32) rhs += fq[4 * f + 1] * (double)J[(int64_t)f * N + i];
+        for (int f = sl; f < F; f += LPV) rhs += fq[4 * f + 1] * (double)J[(int64_t)f * N + i];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) rhs += __shfl_xor_sync(0xffffffffu, rhs, o);
+        for (int o = LPV >> 1; o > 0; o >>= 1) rhs += __shfl_xor_sync(m, rhs, o);
         if (!(rhs > 0.0)) {
-            if (lane == 0) T[i] = 0.0;
+            if (sl == 0) T[i] = 0.0;
             continue;
         }
-        const double tp = T[i];
-        double lo = 0.0, hi = fmax(1.0, 2.0 * tp);
-        double g, dg;
-        planck_sum(fq, F, hi, lane, g, dg);
-        int guard = 0;
-        while (g < rhs && guard < 200) {
-            lo = hi;
-            hi *= 2.0;
-            planck_sum(fq, F, hi, lane, g, dg);
-            ++guard;
-        }
-        double t = (tp > lo && tp < hi) ? tp : 0.5 * (lo + hi);
-        bool ok = false;
-        for (int it = 0; it < 100; ++it) {
-            planck_sum(fq, F, t, lane, g, dg);
-            const double fv = g - rhs;
-            if (fv < 0.0) lo = t;
-            if (fv > 0.0) hi = t;
-            double tn = dg > 0.0 ? t - fv / dg : 0.5 * (lo + hi);
-            if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
-            const bool done = fabs(tn - t) <= 1e-14 * fabs(tn);
-            t = tn;
-            if (done || fv == 0.0) {
-                ok = true;
-                break;
-            }
-        }
-        if (lane == 0) {
+        double t = 0.0;
+        const bool ok = solve_temperature<LPV>(fq, F, rhs, lane, T[i], t);
+        if (sl == 0) {
             if (!ok) atomicOr(fail, 1);
             T[i] = t;
         }
@@ -222,8 +176,21 @@ static int one_iteration(Operator& op, cudaStream_t s, int grey, int* d_counter,
     if (rc) return rc;
     fp_update<V><<<op.n_part, kRedThreads, 0, s>>>((V*)op.d_J, (const V*)op.d_Y, (const V*)op.d_SE, tot, op.d_part);
     fp_reduce<<<1, 256, 0, s>>>(op.d_part, op.n_part, op.d_res, d_counter, cap);
-    fp_newton<V><<<(int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)N + 7) / 8, 152 * 32)), 256, 0, s>>>(
-        (const V*)op.d_J, op.d_T, op.d_fq, N, F, grey, d_fail);
+    // LPV lanes per vertex: the power of two >= F (1 for the grey closed form)
+    const int lpv = grey ? 1 : (F <= 1 ? 1 : F <= 2 ? 2 : F <= 4 ? 4 : F <= 8 ? 8 : F <= 16 ? 16 : 32);
+    const int64_t warps = ((int64_t)N * lpv + 31) / 32;
+    const int gn = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, 152 * 32));
+#define RT_NEWTON(L) \
+    fp_newton<V, L><<<gn, 256, 0, s>>>((const V*)op.d_J, op.d_T, op.d_fq, N, F, grey, d_fail)
+    switch (lpv) {
+        case 1: RT_NEWTON(1); break;
+        case 2: RT_NEWTON(2); break;
+        case 4: RT_NEWTON(4); break;
+        case 8: RT_NEWTON(8); break;
+        case 16: RT_NEWTON(16); break;
+        default: RT_NEWTON(32); break;
+    }
+#undef RT_NEWTON
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
 }
