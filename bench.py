@@ -608,7 +608,7 @@ def run_gpu(args):
                      "entries_evaluated": info["entries_evaluated"], "compression": info["compression"],
                      "rank_max": info["rank_max"], "n_far": info["n_far"],
                      "n_dense_fallback": info["n_dense_fallback"]},
-        "assembly_roofline": assembly_roofline(info),
+        "assembly_roofline": assembly_roofline(info, info["G"]),
         "solve": {"iters_mean": statistics.mean(iters), "ms_solve_mean": statistics.mean(s["ms_total"] for s in stats)},
         "e2e": {"value": world / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": int(prob.xyz.nbytes + prob.tet.nbytes
                                                                                       + prob.emit_tri.nbytes),
@@ -626,14 +626,15 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def assembly_roofline(info):
+def assembly_roofline(info, groups):
     """Entry evaluation (ACA rows and columns, near blocks) is bound by instruction issue
     (FP32 pipe and SFU), not memory.  Work units counted on the device: kernel terms (one
     direct or reflected value of the kernel at a point pair, every group at once) and
     optical depths (16-point Gauss line integrals, evaluated in closed form).  The peak is
     the FP32 issue rate, 152 SMs x 128 FP32 lanes x the maximum SM clock of
     MEASURED_PEAKS.json, with thread instructions per kernel term taken from the committed
-    ncu instruction counts of the two assembly kernels (profiles/assembly_*.md)."""
+    ncu instruction counts of the two assembly kernels for the same group count
+    (profiles/assembly_instructions.json; absent for group counts it does not list)."""
     ms = info["ms_aca"] + info["ms_near"]
     terms, depths = info.get("assembly_terms", 0), info.get("assembly_depths", 0)
     if ms <= 0 or terms <= 0:
@@ -652,11 +653,13 @@ def assembly_roofline(info):
     try:
         with open(os.path.join(ROOT, "profiles", "assembly_instructions.json")) as f:
             c = json.load(f)
+        # the counts of the instance this build ran (16 or 1 kappa groups); none for others
+        c = c["by_groups"][str(int(groups))]
         ipt, xpt = float(c["thread_inst_per_term"]), float(c["sfu_thread_inst_per_term"])
-        out.update({"thread_inst_per_term": ipt, "sfu_inst_per_term": xpt,
+        out.update({"thread_inst_per_term": ipt, "sfu_inst_per_term": xpt, "counts_from": c["workload"],
                     "achieved_lane_inst_per_s": out["terms_per_s"] * ipt,
                     "frac_fp32_issue": out["terms_per_s"] * ipt / lanes_peak,
-                    "frac_sfu": out["terms_per_s"] * xpt / sfu_peak, "per_term_counts": c.get("how")})
+                    "frac_sfu": out["terms_per_s"] * xpt / sfu_peak})
     except Exception:
         pass
     return out
