@@ -1006,6 +1006,10 @@ __global__ void aca_row_residual(AcaDev D, const AcaActive* act, int na, int64_t
         const AcaActive a = act[ai];
         const int jj = (int)(e - a.first_row);
         const int b = a.b, r = D.rank[b], is = D.istar[b];
+        // lanes of this warp on the same block combine their row maxima first:
+        // one atomic per block and group per warp instead of one per lane
+        const unsigned peers = __match_any_sync(__activemask(), b);
+        const bool leader = (threadIdx.x & 31) == __ffs(peers) - 1;
         float score = 0.0f;
         for (int g = 0; g < D.G; ++g) {
             float v = buf[a.rbuf + (int64_t)g * a.n + jj];
@@ -1016,7 +1020,8 @@ __global__ void aca_row_residual(AcaDev D, const AcaActive* act, int na, int64_t
             }
             buf[a.rbuf + (int64_t)g * a.n + jj] = v;
             score += fabsf(v) * D.wscale[(int64_t)b * D.G + g];
-            if (isfinite(v)) atomicMax(&D.rowmax[(int64_t)b * D.G + g], __float_as_uint(fabsf(v)));
+            const unsigned mx = __reduce_max_sync(peers, isfinite(v) ? __float_as_uint(fabsf(v)) : 0u);
+            if (leader && mx) atomicMax(&D.rowmax[(int64_t)b * D.G + g], mx);
         }
         atomicMax(&D.key[b], score_key(score, jj));
     }
@@ -1132,7 +1137,10 @@ __global__ void __launch_bounds__(256) aca_dots(AcaDev D, const AcaActive* act, 
                 const float* U1 = D.pool + a.uoff + (int64_t)g * a.m;
                 const float* V0 = D.pool + vl + (int64_t)g * a.n;
                 const float* V1 = D.pool + a.voff + (int64_t)g * a.n;
+                // unrolled so that several loads per lane are in flight
+#pragma unroll 4
                 for (int i = sl; i < a.m; i += L) pu += U0[i] * U1[i];
+#pragma unroll 4
                 for (int j = sl; j < a.n; j += L) pv += V0[j] * V1[j];
             }
             double su = pu, sv = pv;
