@@ -84,10 +84,14 @@ def measured_traffic(workload_name, kind):
 def workload(name, seed=0):
     if name.startswith("batch"):
         return W.batch_instances(count=int(name[5:] or 256), seed=seed)
-    if name == "cube32_F16":
+    if name in ("cube32_F16", "srcop32"):
         return W.multifreq_32()
     if name == "cube12_grey":
         return W.plain_grey_12()
+    if name == "kobayashi":
+        # box minus the opaque radiating cube, three R0 = 1 planes with corner paths,
+        # the duct in a kappa grid (the paper's Test-3 geometry), h = 2.5 cm
+        return W.kobayashi_problem(0.025)
     if name.startswith("cube") and name.endswith("s") and "_F" in name:
         # one operator shared by all frequencies (kappa_nu = kappa(x))
         n, F = name[4:-1].split("_F")
@@ -433,6 +437,89 @@ def run_serve(args):
     }))
 
 
+def run_srcop(args):
+    """The surface-to-volume matrix Sbar^E_{i,l} (Section 2, last paragraph) as a
+    compressed operator, on the 32^3 16-group workload: each step builds it from
+    the volume operator (entry evaluation + ACA), then rt_apply_source is timed
+    live with CUDA events against its algorithmic bytes; sampled rows of the
+    result are checked against the FP64 oracle's rows of the same matrix."""
+    import torch
+
+    import paper_2306_05789_gb300 as rt
+    rt.lib()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    prob = W.multifreq_32()
+    op = rt.rt_build_operator(prob, rt.hparams(), stream)
+    for _ in range(args.warmup):
+        rt.rt_build_source_operator(op, stream).free()
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sop = None
+    for k in range(args.steps):
+        if sop is not None:
+            sop.free()
+        sop = rt.rt_build_source_operator(op, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    info = sop.info()
+    L, F, N = info["L"], prob.freqs.F, prob.N
+    q = np.random.default_rng(0).uniform(0.2, 1.5, L)
+    Q = torch.tensor(q, dtype=torch.float32, device=dev)
+    out = torch.zeros(F, N, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        sop.apply(Q, out, stream)
+    n_apply = 20
+    l2_flush = info["apply_bytes"] < 2 * L2_BYTES
+    junk = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev) if l2_flush else None
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_tot = 0.0
+    for _ in range(n_apply):
+        if junk is not None:
+            junk.fill_(1.0)
+        a0.record(stream)
+        sop.apply(Q, out, stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        t_tot += a0.elapsed_time(a1)
+    t_apply = t_tot / n_apply / 1e3
+    clk = clocks.stop()
+    y = out.double().cpu().numpy()
+    sop.free()
+    op.free()
+    from oracle import oracle as O
+    O.build()
+    rows = W.sample_rows(N, args.residual_rows, seed=3)
+    t0 = time.perf_counter()
+    H = O.source_hat_rows(prob, rows)
+    _, gidx = O.groups_of(prob.freqs)
+    Bv = O.emitter_intensity(prob) / prob.Q0
+    ref = np.stack([Bv[f] * (H[:, gidx[f], :] @ q) for f in range(F)])
+    err = float(np.linalg.norm(y[:, rows] - ref) / np.linalg.norm(ref))
+    hbm, _, peak_kind = peaks()
+    gbs = info["apply_bytes"] / t_apply / 1e9
+    print(json.dumps({
+        "metric": "builds/s", "value": 1e3 / ms, "unit": "builds/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "srcop32", "N": N, "L": L, "G": info["G"], "aca_eps": 1e-4,
+                   "what": "surface-to-volume operator of the 32^3, 16-group workload; a step is one build"},
+        "source_operator": {k: info[k] for k in ("n_blocks", "n_far", "n_dense", "rank_max", "stored_entries",
+                                                 "compression", "apply_bytes", "device_bytes", "ms_eval", "ms_aca")},
+        "roofline": {"bound": "hbm", "kernel": "so_phase1 + so_phase2 (rt_apply_source)", "achieved": gbs,
+                     "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "peak_kind": peak_kind,
+                     "ms": t_apply * 1e3, "l2_flush": l2_flush},
+        "err_vs_oracle": {"rel_l2": err, "rows": int(len(rows)), "oracle_s": time.perf_counter() - t0,
+                          "what": "rt_apply_source of per-vertex coefficients U[0.2, 1.5] against dense FP64 oracle "
+                                  "rows of the surface-to-volume matrix"},
+        "gpu_launches": None, "clocks": clk,
+    }))
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -608,7 +695,8 @@ def run_gpu(args):
                      "entries_evaluated": info["entries_evaluated"], "compression": info["compression"],
                      "rank_max": info["rank_max"], "n_far": info["n_far"],
                      "n_dense_fallback": info["n_dense_fallback"]},
-        "assembly_roofline": assembly_roofline(info, info["G"]),
+        # the committed instruction counts are for the analytic-kappa, one-wall kernels
+        "assembly_roofline": assembly_roofline(info, None if args.workload == "kobayashi" else info["G"]),
         "solve": {"iters_mean": statistics.mean(iters), "ms_solve_mean": statistics.mean(s["ms_total"] for s in stats)},
         "e2e": {"value": world / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": int(prob.xyz.nbytes + prob.tet.nbytes
                                                                                       + prob.emit_tri.nbytes),
@@ -654,7 +742,7 @@ def assembly_roofline(info, groups):
         with open(os.path.join(ROOT, "profiles", "assembly_instructions.json")) as f:
             c = json.load(f)
         # the counts of the instance this build ran (16 or 1 kappa groups); none for others
-        c = c["by_groups"][str(int(groups))]
+        c = c["by_groups"][str(int(groups))] if groups is not None else None
         ipt, xpt = float(c["thread_inst_per_term"]), float(c["sfu_thread_inst_per_term"])
         out.update({"thread_inst_per_term": ipt, "sfu_inst_per_term": xpt, "counts_from": c["workload"],
                     "achieved_lane_inst_per_s": out["terms_per_s"] * ipt,
@@ -902,6 +990,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "srcop32":
+        run_srcop(args)
     elif args.workload == "serve":
         if args.far_prec == "f32" and "--far-prec" not in sys.argv:
             args.far_prec = "bf16"
