@@ -90,8 +90,8 @@ def workload(name, seed=0):
         return W.plain_grey_12()
     if name == "kobayashi":
         # box minus the opaque radiating cube, three R0 = 1 planes with corner paths,
-        # the duct in a kappa grid (the paper's Test-3 geometry), h = 2.5 cm
-        return W.kobayashi_problem(0.025)
+        # the duct in a kappa grid (the paper's Test-3 geometry), h = 1/30 m
+        return W.kobayashi_problem(1.0 / 30.0)
     if name.startswith("cube") and name.endswith("s") and "_F" in name:
         # one operator shared by all frequencies (kappa_nu = kappa(x))
         n, F = name[4:-1].split("_F")
@@ -680,7 +680,10 @@ def run_gpu(args):
                    "refine": bool(refine_tol > 0),
                    "albedo": 0.0 if dense else 0.3, "tol": args.tol, "far_prec": args.far_prec,
                    "parallelism": f"replicas{world}",
-                   "l2": "L2 flushed before each timed apply" if l2_flush else "operator larger than L2 (no flush needed)"},
+                   "l2": "L2 flushed before each timed apply" if l2_flush else "operator larger than L2 (no flush needed)",
+                   **({"kappa": "grid 6x10x6 cells: 10 /m, 0.01 /m in the duct", "R0": 1.0, "albedo": 0.0,
+                       "walls": "x = 0, y = 0, z = 0 with corner paths", "obstacles": "opaque cube [0, 0.1]^3",
+                       "grey": True} if args.workload == "kobayashi" else {})},
         "roofline": {"bound": "hbm",
                      "kernel": ("dense_apply" if dense else
                                 ("t2_xsplit+t2_phase1+t2_phase2 (streamed tcgen05, rt_apply)" if info["apply_tensor_cores"]
