@@ -218,8 +218,9 @@ __device__ __forceinline__ bool hs_fill(const HsRing& R, int s, uint32_t u, cons
     return true;
 }
 
-// after a producer timeout: wait (bounded) for the slot's last copies, so that
-// none is in flight when the CTA exits
+// wait (bounded) for the slot's last copies, so that none is in flight when
+// the CTA exits: when a producer leaves normally, and after its own timeout (a
+// consumer that gives up can then leave at once)
 __device__ __forceinline__ void hs_drain(const HsRing& R, int s, uint32_t uses)
 {
     if ((threadIdx.x & 31) == 0 && uses > 0) bulk::wait(R.full(s), (uses - 1) & 1u);
@@ -245,7 +246,8 @@ __global__ void __launch_bounds__(hs::kThreads) hmv_s1(const HsLoad* __restrict_
         int64_t j = blockIdx.x + (int64_t)s * gridDim.x;
         HsRec nxt;
         if (j < total) hs_fetch(nxt, loads + j / F, (int)(j % F), fgroup);
-        for (uint32_t u = 0; j < total; j += step, ++u) {
+        uint32_t u = 0;
+        for (; j < total; j += step, ++u) {
             const HsRec cur = nxt;
             if (j + step < total) hs_fetch(nxt, loads + (j + step) / F, (int)((j + step) % F), fgroup);
             if (!hs_fill<T>(R, s, u, cur, far, nullptr, X, nullptr, N, false)) {
@@ -254,6 +256,7 @@ __global__ void __launch_bounds__(hs::kThreads) hmv_s1(const HsLoad* __restrict_
                 return;
             }
         }
+        hs_drain(R, s, u);   // the last copies have landed before this warp leaves
         return;
     }
     constexpr int VW = VecW<T>::n;
@@ -425,7 +428,8 @@ __global__ void __launch_bounds__(hs::kThreads) hmv_s2(const HsLoad* __restrict_
         for (int k = 0; k < s && j < nitems; ++k) next();
         HsRec nxt;
         if (j < nitems) hs_fetch(nxt, loads + ld, it.y, fgroup);
-        for (uint32_t u = 0; j < nitems; ++u) {
+        uint32_t u = 0;
+        for (; j < nitems; ++u) {
             const HsRec cur = nxt;
             for (int k = 0; k < hs::kStages && j < nitems; ++k) next();
             if (j < nitems) hs_fetch(nxt, loads + ld, it.y, fgroup);
@@ -435,6 +439,7 @@ __global__ void __launch_bounds__(hs::kThreads) hmv_s2(const HsLoad* __restrict_
                 return;
             }
         }
+        hs_drain(R, s, u);   // the last copies have landed before this warp leaves
         return;
     }
     const int tid = threadIdx.x;   // consumer thread 0 .. kConsumers - 1
