@@ -660,6 +660,11 @@ int assemble_source(Operator& op, cudaStream_t s, std::string& err)
 // One CTA per (row, sub-cluster); the row segment accumulates in shared
 // memory [G][n] (float atomics, so the summation order is not fixed).
 // ---------------------------------------------------------------------------
+// threads of one row-over-cluster CTA: a (row, sub-cluster) item has a few
+// hundred tetrahedra, so 128 threads keep each thread busy on several of them
+// and let four CTAs per SM hide one another's end-of-item barrier
+constexpr int kRowThreads = 128;
+
 struct RowItem {
     int b;            // ACA block (row = i + istar[b]) or -1 (row = i)
     int i;
@@ -675,7 +680,7 @@ struct RowItem {
 // handed out through a shared counter so that the few tetrahedra near x_i
 // (14-point rules) do not hold up a fixed partition.
 template <int MG, bool XT = false>
-__global__ void __launch_bounds__(256, MG <= 16 && !XT ? 2 : 1) row_cluster_kernel(KernelParams P, const RowItem* __restrict__ items,
+__global__ void __launch_bounds__(kRowThreads, MG <= 16 && !XT ? 4 : 2) row_cluster_kernel(KernelParams P, const RowItem* __restrict__ items,
                                                           const int* __restrict__ sub_tets,
                                                           const int* __restrict__ istar, float* __restrict__ out)
 {
@@ -935,14 +940,14 @@ static int launch_rows(Operator& op, const std::vector<RowItem>& items, const in
         const int cnt = (int)std::min<size_t>(items.size() - k0, (size_t)1 << 30);
         const int G = op.G;
         if (op.kp.ext) {   // further walls, corner paths, a kappa grid or opaque boxes
-            if (G <= 16) row_cluster_kernel<16, true><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
-            else row_cluster_kernel<0, true><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
-        } else if (G <= 1) row_cluster_kernel<1><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
-        else if (G <= 4) row_cluster_kernel<4><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
-        else if (G <= 8) row_cluster_kernel<8><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
-        else if (G <= 16) row_cluster_kernel<16><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
-        else if (G <= 32) row_cluster_kernel<32><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
-        else row_cluster_kernel<0><<<cnt, 256, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
+            if (G <= 16) row_cluster_kernel<16, true><<<cnt, kRowThreads, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
+            else row_cluster_kernel<0, true><<<cnt, kRowThreads, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
+        } else if (G <= 1) row_cluster_kernel<1><<<cnt, kRowThreads, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
+        else if (G <= 4) row_cluster_kernel<4><<<cnt, kRowThreads, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
+        else if (G <= 8) row_cluster_kernel<8><<<cnt, kRowThreads, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
+        else if (G <= 16) row_cluster_kernel<16><<<cnt, kRowThreads, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
+        else if (G <= 32) row_cluster_kernel<32><<<cnt, kRowThreads, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
+        else row_cluster_kernel<0><<<cnt, kRowThreads, smem, s>>>(op.kp, d + k0, op.d_sub_tets, istar, out);
     }
     RT_CUDA_TRY(cudaGetLastError());
     RT_CUDA_TRY(cudaFreeAsync(d, s));
