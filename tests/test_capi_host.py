@@ -1,6 +1,8 @@
 """C-ABI checks that need no GPU: the library loads, exports every symbol that
-include/rt.h declares, and the host-side cluster/block tree (Section 2.1)
-satisfies its invariants."""
+include/rt.h declares, the host-side cluster/block tree (Section 2.1)
+satisfies its invariants, and rt_build_operator rejects invalid walls, kappa
+grids, opaque boxes and binning parameters on the host (RT_EINVAL) before any
+device call."""
 from __future__ import annotations
 
 import os
@@ -103,3 +105,74 @@ def test_tree_order_keeps_leaves_spatially_compact():
         p = xyz[perm[r0:r0 + m]]
         ext = p.max(axis=0) - p.min(axis=0)
         assert ext.max() <= 4.0 / 15 + 1e-12
+
+
+# ---------------------------------------------------------------------------
+# input validation runs on the host before any device call (rt_build_operator
+# rejects a bad problem with RT_EINVAL and a message, GPU or not)
+# ---------------------------------------------------------------------------
+def _rejected(prob, hp=None, fix=None):
+    import ctypes
+    args = rt._ProblemArgs(prob)
+    if fix is not None:
+        fix(args.s)
+    out = ctypes.c_void_p()
+    hp = hp or rt.hparams()
+    rc = rt.lib().rt_build_operator(ctypes.byref(args.s), ctypes.byref(hp), None, ctypes.byref(out))
+    return rc, rt.lib().rt_last_error().decode()
+
+
+def _cube():
+    return W.cube_problem(4, W.sinprod_kappa(0.5), W.midpoint_freqs(2), R0=0.5)
+
+
+def test_more_than_three_walls_are_rejected():
+    p = _cube()
+    p.more_walls = (W.wall_y0(0.5), W.Wall((0, 1, 0), (0, 1, 0), 0.5), W.Wall((1, 0, 0), (1, 0, 0), 0.5))
+    rc, msg = _rejected(p)
+    assert rc == rt.RT_EINVAL and "n_walls" in msg
+
+
+@pytest.mark.parametrize("wall,what", [(W.Wall((0, 0, 0), (0, 0, 0), 0.5), "normal"),
+                                       (W.Wall((0, 0, 0), (0, -1, 0), 1.5), "R0")])
+def test_bad_walls_are_rejected(wall, what):
+    p = _cube()
+    p.more_walls = (wall,)
+    rc, msg = _rejected(p)
+    assert rc == rt.RT_EINVAL and what in msg
+
+
+def test_corner_flag_must_be_zero_or_one():
+    def bad(s):
+        s.corner = 2
+    rc, msg = _rejected(_cube(), fix=bad)
+    assert rc == rt.RT_EINVAL and "corner" in msg
+
+
+@pytest.mark.parametrize("grid,bbox,what", [
+    (-np.ones((2, 2, 2)), (0, 0, 0, 1, 1, 1), "values"),
+    (np.ones((2, 2, 2)), (0, 0, 0, 1, 0, 1), "box"),
+    (np.ones((1, 1, 600)), (0, 0, 0, 1, 1, 1), "dims")])
+def test_bad_kappa_grids_are_rejected(grid, bbox, what):
+    p = _cube()
+    p.kappa = W.Kappa(W.KAPPA_GRID, 0.0, 0.0, np.asarray(grid, dtype=np.float32), bbox)
+    rc, msg = _rejected(p)
+    assert rc == rt.RT_EINVAL and what in msg
+
+
+def test_bad_opaque_boxes_are_rejected():
+    p = _cube()
+    p.obstacles = (W.Box((0.5, 0.5, 0.5), (0.4, 0.6, 0.6)),)
+    rc, msg = _rejected(p)
+    assert rc == rt.RT_EINVAL and "hi > lo" in msg
+    p.obstacles = (W.Box((0.2, 0.2, 0.2), (0.8, 0.8, 0.8)),)   # the mesh fills it
+    rc, msg = _rejected(p)
+    assert rc == rt.RT_EINVAL and "inside an opaque box" in msg
+    p.obstacles = tuple(W.Box((2.0 + k, 0, 0), (2.5 + k, 1, 1)) for k in range(5))
+    rc, msg = _rejected(p)
+    assert rc == rt.RT_EINVAL and "n_obstacles" in msg
+
+
+def test_kappa_bins_out_of_range_are_rejected():
+    rc, msg = _rejected(_cube(), hp=rt.hparams(kappa_bins=65))
+    assert rc == rt.RT_EINVAL and "kappa_bins" in msg
