@@ -237,9 +237,12 @@ __device__ __forceinline__ float gauss_sum_sinprod(const KernelParams& P, const 
 
 // Exact int_[a,b] kappa for the cellwise-constant grid: walk the grid planes
 // the segment crosses in order of the segment parameter t (one next crossing
-// per axis, the smallest first); each piece [t0, t1] adds the value of the
-// cell holding its midpoint times its length.  Planes are x = glo + m h,
-// m = 1 .. dims-1; a crossing counts when 0 < t < 1.
+// per axis, the smallest first); each piece [t0, t1] adds the value of its
+// cell times its length.  Planes are x = glo + m h, m = 1 .. dims-1; a crossing
+// counts when 0 < t < 1.  The cell of a piece is tracked by the walk itself
+// (the cell ahead of a, then one step per plane crossed), which is the cell
+// holding the piece's midpoint; a point outside the grid's box belongs to the
+// nearest cell.
 template <class R>
 __device__ R grid_depth(const KernelParams& P, const Vec3<R>& a, const Vec3<R>& b)
 {
@@ -247,13 +250,12 @@ __device__ R grid_depth(const KernelParams& P, const Vec3<R>& a, const Vec3<R>& 
     const R D[3] = {b.x - a.x, b.y - a.y, b.z - a.z};
     const R L = sqrt_r(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
     R tn[3], h[3];
-    int m[3], st[3];
+    int m[3], st[3], cell[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         h[d] = (R(P.ghi[d]) - R(P.glo[d])) / R(P.gdims[d]);
         st[d] = D[d] > R(0) ? 1 : -1;
         tn[d] = R(2);
-        m[d] = 0;
         if (D[d] != R(0)) {
             const R u = (A[d] - R(P.glo[d])) / h[d];
             const R uc = u < R(-1) ? R(-1) : (u > R(P.gdims[d] + 1) ? R(P.gdims[d] + 1) : u);
@@ -266,6 +268,12 @@ __device__ R grid_depth(const KernelParams& P, const Vec3<R>& a, const Vec3<R>& 
                 m[d] += st[d];
             }
             if (m[d] >= 1 && m[d] <= P.gdims[d] - 1) tn[d] = (R(P.glo[d]) + R(m[d]) * h[d] - A[d]) / D[d];
+            // the cell between the last plane behind and the next one ahead
+            const int c = D[d] > R(0) ? m[d] - 1 : m[d];
+            cell[d] = c < 0 ? 0 : (c > P.gdims[d] - 1 ? P.gdims[d] - 1 : c);
+        } else {
+            m[d] = 0;
+            cell[d] = grid_cell<R>(P, d, A[d]);
         }
     }
     R s = R(0), t0 = R(0);
@@ -275,8 +283,7 @@ __device__ R grid_depth(const KernelParams& P, const Vec3<R>& a, const Vec3<R>& 
         t1 = t1 < tn[2] ? t1 : tn[2];
         t1 = t1 < R(1) ? t1 : R(1);
         if (t1 > t0) {
-            const R tm = R(0.5) * (t0 + t1);
-            s += grid_kappa<R>(P, A[0] + tm * D[0], A[1] + tm * D[1], A[2] + tm * D[2]) * (t1 - t0);
+            s += grid_value<R>(P, cell[0] + P.gdims[0] * (cell[1] + P.gdims[1] * cell[2])) * (t1 - t0);
             t0 = t1;
         }
         if (t1 >= R(1)) break;
@@ -284,6 +291,7 @@ __device__ R grid_depth(const KernelParams& P, const Vec3<R>& a, const Vec3<R>& 
         for (int d = 0; d < 3; ++d)
             if (tn[d] == t1) {
                 m[d] += st[d];
+                cell[d] += st[d];
                 tn[d] = (m[d] >= 1 && m[d] <= P.gdims[d] - 1) ? (R(P.glo[d]) + R(m[d]) * h[d] - A[d]) / D[d] : R(2);
             }
     }
