@@ -10,6 +10,15 @@
 // (x_i for the direct term, xbar_i for the reflected one) lies within two
 // diameters of the tetrahedron's centroid, 4-point degree-2 rule otherwise.
 //
+// Further reflected terms (the general instances, XT): each further wall adds
+// its own single-reflection term (image of x in that plane, weight R0, broken
+// path through the reflection point; Section 2 with one reflection per wall),
+// and each pair of perpendicular walls the path reflecting on both (double
+// image, weight R0_a R0_b).  tau may also be the exact integral of a
+// cellwise-constant kappa grid, or +infinity when a path segment crosses an
+// opaque box of a non-convex domain (Remark 1 after Lemma 1: kappa = +infinity
+// in the convex hull outside the domain); such a term contributes nothing.
+//
 // One warp evaluates one entry: the (tetrahedron, quadrature point, term)
 // items of the entry are distributed over the lanes through a warp prefix sum,
 // each lane accumulates all groups, and a butterfly reduction leaves the sums
