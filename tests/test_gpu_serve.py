@@ -119,3 +119,37 @@ def test_request_errors_do_not_stop_the_server():
     srv.free()
     res, _ = serve([p], rt.hparams(leaf=32), slots=1)
     assert res[0][2]["status"] == 0
+
+
+def test_served_requests_with_walls_grids_and_opaque_boxes():
+    """The server copies everything a request points to (further walls, the kappa
+    grid, the opaque boxes) at submission: a mix of a Test-3 geometry request, a
+    two-wall request with its corner path and a plain one, submitted from arrays
+    that are released right after submission, gives the results of direct solves;
+    the Test-3 request also matches the FP64 oracle's one-step residual."""
+    koba = W.kobayashi_problem(0.05)
+    walls = W.cube_problem(8, W.sinprod_kappa(0.5), W.midpoint_freqs(2, albedo=0.3), R0=0.5)
+    walls.more_walls = (W.wall_y0(0.4),)
+    walls.corner = True
+    plain = small_requests()[0]
+    probs = [koba, walls, plain]
+    hp = rt.hparams(leaf=32)
+    srv = rt.Server(hp, slots=3, tol=1e-7)
+    ids = []
+    for p in probs:
+        ids.append(srv.submit(p))   # the marshalled arrays die with the call's temporaries
+    res = [srv.poll(i, wait_ms=-1) for i in ids]
+    srv.free()
+    dev = torch.device("cuda:0")
+    for p, (J, T, info) in zip(probs, res):
+        op = rt.rt_build_operator(p, hp)
+        Jd = torch.zeros(p.freqs.F, p.N, dtype=torch.float32, device=dev)
+        Td = torch.zeros(p.N, dtype=torch.float64, device=dev)
+        op.solve_fixed_point(Jd, Td, tol=1e-7, max_iter=400, check_every=4)
+        op.free()
+        assert rel_l2(T, Td.cpu().numpy()) < 1e-5, p.name
+        assert rel_l2(J, Jd.cpu().numpy()) < 1e-5, p.name
+    J, T, _ = res[0]
+    rows = W.sample_rows(koba.N, 24, seed=61)
+    r = O.one_step_residual(koba, rows, J.astype(np.float64), T)
+    assert np.linalg.norm(r) / np.linalg.norm(J[:, rows]) < 1e-5

@@ -110,3 +110,27 @@ def test_dense_operator_is_rejected():
         assert e.value.code == rt.RT_EINVAL
     finally:
         op.free()
+
+
+def test_binned_channels_use_their_group_rows():
+    """With kappa binning (2 bins for 5 channels) the operator has one N x L matrix per
+    bin, built with the bin's midpoint scale; channel f applies its bin's matrix times
+    its own intensity: against the oracle's rows at the bins' scales."""
+    F = 5
+    p = W.cube_problem(12, W.sinprod_kappa(0.5), W.midpoint_freqs(F, albedo=0.3), R0=0.5)
+    op = rt.rt_build_operator(p, rt.hparams(kappa_bins=2))
+    sop = rt.rt_build_source_operator(op)
+    try:
+        info = sop.info()
+        assert info["G"] == 2
+        q = np.random.default_rng(26).uniform(0.2, 1.5, info["L"])
+        y = run(sop, q, F, p.N)
+        rows = W.sample_rows(p.N, 80, seed=27)
+        cg, gidx = O.groups_of(p.freqs, bins=2)
+        H = O.source_hat_rows(p, rows, c=cg)
+        Bv = O.emitter_intensity(p) / p.Q0
+        ref = np.stack([Bv[f] * (H[:, gidx[f], :] @ q) for f in range(F)])
+        assert rel_l2(y[:, rows], ref) < 1e-4
+    finally:
+        sop.free()
+        op.free()
