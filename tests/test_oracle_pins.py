@@ -748,3 +748,48 @@ def test_grid_kappa_wall_equals_the_doubled_domain_with_the_mirrored_grid():
     kapw = W.Kappa(W.KAPPA_GRID, 0.0, 0.0, np.concatenate([g, g], axis=0), (0.0, 0.0, -1.0, 1.0, 1.0, 1.0))
     pw = W.Problem(dxyz, dtet, W.doubled_emitter(n), kapw, None, W.grey_freqs())
     assert np.abs(O.G_rows(p, rows, c=c) @ S - O.G_rows(pw, rows, c=c) @ S_even).max() > 1e-4
+
+
+def _mirror_z(xyz, tet, tri):
+    """The mesh and its mirror image in z = 0 (vertices on the plane shared), the
+    emitter triangles mirrored with their orientation kept outward."""
+    N = xyz.shape[0]
+    on = xyz[:, 2] == 0.0
+    low = np.full(N, -1, dtype=np.int64)
+    low[on] = np.nonzero(on)[0]
+    extra = np.nonzero(~on)[0]
+    low[extra] = N + np.arange(extra.size)
+    lxyz = xyz[extra].copy()
+    lxyz[:, 2] = -lxyz[:, 2]
+    dxyz = np.concatenate([xyz, lxyz])
+    dtet = np.concatenate([tet, low[tet]]).astype(np.int32)
+    dtri = np.concatenate([tri, low[tri][:, [0, 2, 1]]]).astype(np.int32)
+    return dxyz, dtet, dtri, np.arange(N), low
+
+
+def test_opaque_box_by_a_wall_equals_the_doubled_domain_with_the_box_mirrored():
+    """The doubled-domain identity with an opaque box: R0 = 1 on z = 0 beside a box
+    removed from the mesh is the mirrored mesh with the box and its image opaque and no
+    wall -- a reflected path is blocked exactly when its unfolded straight line crosses
+    a box.  Rows and source to rounding, and the box does block some paths."""
+    xyz, tet = W.box_mesh((4, 4, 4), 0.25, hole=((1, 1, 1), (3, 3, 2)))
+    emit = W.boundary_faces(xyz, tet, lambda cen: np.abs(cen[:, 0]) < 1e-9)
+    box = W.Box((0.25, 0.25, 0.25), (0.75, 0.75, 0.5))
+    kap = W.Kappa(W.KAPPA_CONST, 1.1, 0.0)
+    p = W.Problem(xyz, tet, emit, kap, W.wall_z0(1.0), W.grey_freqs(), grey=True, obstacles=(box,))
+    dxyz, dtet, dtri, up, low = _mirror_z(xyz, tet, emit)
+    boxd = W.Box((0.25, 0.25, -0.5), (0.75, 0.75, -0.25))
+    pd = W.Problem(dxyz, dtet, dtri, kap, None, W.grey_freqs(), grey=True, obstacles=(box, boxd))
+    rows = np.unique(np.concatenate([W.sample_rows(p.N, 10, seed=64), [0, p.N - 1]])).astype(np.int32)
+    c = np.array([1.0, 0.6])
+    S = W.rand_vectors(p.N, seed=65)
+    S_even = np.zeros(dxyz.shape[0])
+    S_even[up] = S
+    S_even[low] = S
+    A = O.G_rows(p, rows, c=c)
+    np.testing.assert_allclose(A @ S, O.G_rows(pd, rows, c=c) @ S_even, rtol=1e-12)
+    allr = np.arange(p.N, dtype=np.int32)
+    np.testing.assert_allclose(O.source_geometric(p, allr, c=c), O.source_geometric(pd, allr, c=c),
+                               rtol=1e-12, atol=1e-15)
+    free = W.Problem(xyz, tet, emit, kap, W.wall_z0(1.0), W.grey_freqs(), grey=True)
+    assert np.abs(O.G_rows(free, rows, c=c) @ S - A @ S).max() > 1e-3 * np.abs(A @ S).max()
