@@ -793,3 +793,20 @@ def test_opaque_box_by_a_wall_equals_the_doubled_domain_with_the_box_mirrored():
                                rtol=1e-12, atol=1e-15)
     free = W.Problem(xyz, tet, emit, kap, W.wall_z0(1.0), W.grey_freqs(), grey=True)
     assert np.abs(O.G_rows(free, rows, c=c) @ S - A @ S).max() > 1e-3 * np.abs(A @ S).max()
+
+
+def test_surface_to_volume_rows_sum_to_the_source_with_walls_grids_and_boxes():
+    """The partition of unity of the surface hat functions holds for every term: with two
+    walls and their corner path over a kappa grid, and in the Test-3 geometry (three walls,
+    corner paths, opaque cube, duct), sum_l Sbar^E_{i,l} is the source (pinned above by the
+    doubled-domain identities), emitter vertices included."""
+    g = np.random.default_rng(66).uniform(0.5, 1.5, (2, 3, 2)).astype(np.float32)
+    p = W.cube_problem(6, W.Kappa(W.KAPPA_GRID, 0.0, 0.0, g, (0, 0, 0, 1, 1, 1)), W.midpoint_freqs(2), R0=0.5)
+    p.more_walls = (W.wall_y0(0.4),)
+    p.corner = True
+    q = W.kobayashi_problem(0.05)
+    for prob in (p, q):
+        rows = np.unique(np.concatenate([W.sample_rows(prob.N, 40, seed=67), O.emitter_vertices(prob)[::3]]))
+        rows = rows.astype(np.int32)
+        H = O.source_hat_rows(prob, rows)
+        np.testing.assert_allclose(H.sum(axis=2), O.source_geometric(prob, rows), rtol=1e-12, atol=1e-16)
