@@ -1,8 +1,8 @@
 """FP64 CPU oracle for the integral-form RTE with a reflective wall (arXiv 2306.05789).
 
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
-and the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py``, never by
-the product package.  It shares no code with the CUDA library.
+and the ``cpu_baseline`` / ``err_vs_oracle`` / ``--impl reference`` legs of
+``bench.py``, never by the product package.  It shares no code with the CUDA library.
 
 Layers:
 
@@ -29,8 +29,8 @@ Readings of the paper taken here:
 * non-convex domains (Remark 1 after Lemma 1): opaque boxes of the convex hull
   carry kappa = +infinity; a path crossing one has infinite optical depth.
 
-parity unpinned: nothing in this module is unpinned; the header of
-``rt_oracle.c`` and the tests name the pin of every function.
+Every function here is pinned (no part is "parity unpinned"): the header of
+``rt_oracle.c`` and ``tests/test_oracle_pins.py`` name the pin of each one.
 """
 from __future__ import annotations
 

@@ -1,13 +1,13 @@
 /*
  * rt_oracle.c -- plain, slow FP64 CPU oracle for the integral-form radiative
- * transfer operator with one planar reflective wall (Pironneau & Tournier,
+ * transfer operator with planar reflective walls (Pironneau & Tournier,
  * "Reflective Conditions for Radiative Transfer in Integral Form with
  * H-Matrices", arXiv 2306.05789).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
- * load this file; only the test suite, the smoke check and the CPU-baseline
- * leg of the benchmark do.  It shares no code, header, table or constant
- * generator with the CUDA library.
+ * load this file; only the test suite, the smoke check and the oracle legs of
+ * the benchmark (CPU baseline, sampled error, reference arm) do.  It shares
+ * no code, header, table or constant generator with the CUDA library.
  *
  * What it computes (all in double precision, no blocking or compression):
  *   - kappa(x): constant, k0 + amp*sin(2 pi x) sin(2 pi y) sin(2 pi z), or a
@@ -39,6 +39,32 @@
  * Frequencies enter only through kappa_nu = c_g * kappa(x): each "group" g
  * is one distinct scale c_g, and the oracle returns one matrix row per group.
  * The fixed point and the Newton temperature solve live in oracle.py.
+ *
+ * Pins (tests/test_oracle_pins.py; each compares with something other than
+ * this file):
+ *   or_gauss_legendre    exact on monomials to degree 31
+ *   or_tet_rule          exact on monomials to degree 2 (4 points) and 5
+ *                          (14 points), and not to one degree more
+ *   or_tri_rule          exact to degree 2 (3 points) and 5 (7 points)
+ *   or_optical_depth     kappa |b - a| for constant kappa; the closed form of
+ *                          the sin-product integral; the grid's exact piecewise
+ *                          sum against hand values and brute-force sampling
+ *   or_kappa_at          a constant grid gives the constant-kappa operator
+ *   or_blocked           dense segment sampling, grazing and corner cases; an
+ *                          opaque slab separates the two halves exactly
+ *   or_kernel_point      the mirror-image closed form (constant kappa); every
+ *                          reflected and corner path has the optical depth of
+ *                          the straight line through the unfolded domain
+ *   or_G_rows,           P1 reproduction of linear functions; entry = row;
+ *   or_G_entry             Lemma 1 row sums (with and without an opaque cube);
+ *                          the doubled and fourfold domains for R0 = 1 walls,
+ *                          also over a mirrored kappa grid and a mirrored box
+ *   or_source            the kappa = 0 view factor in closed form; limit
+ *                          values on the emitter; the absorbing source against
+ *                          an independent face integral; the doubled and
+ *                          fourfold domains
+ *   or_source_hat        rows sum to or_source (partition of unity) and
+ *                          integrate a linear emitter coefficient exactly
  */
 #include <math.h>
 #include <stdlib.h>
