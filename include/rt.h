@@ -451,7 +451,11 @@ const char* rt_last_error(void);
  * d = |c_t - c_s| (adm = RT_ADM_CENTER).  perm (may be NULL): [n] tree order -> vertex id.  blocks (may
  * be NULL): [cap][5] rows (row0, m, col0, n, kind: 0 dense leaf, 1
  * admissible) in tree order.  counts: [0] = leaves, [1] = dense blocks,
- * [2] = admissible blocks. */
+ * [2] = admissible blocks.
+ * Point sets of at least 32768 points are planned on several host threads
+ * (environment variable RT_PLAN_THREADS, default the hardware threads, at
+ * most 16); the plan does not depend on the thread count, bit for bit.  The
+ * operator builds and rt_submit plan the same way. */
 int rt_plan(const double* xyz, int64_t n, int leaf, double eta, int adm, int32_t* perm, int32_t* blocks,
             int64_t cap, int64_t* counts);
 

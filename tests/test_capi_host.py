@@ -97,6 +97,32 @@ def test_gap_admissibility_keeps_touching_clusters_dense():
     assert fr[1] < fr[0] < 0.25
 
 
+@pytest.mark.parametrize("kind,leaf,adm", [("cube", 64, rt.RT_ADM_GAP), ("ties", 20, rt.RT_ADM_CENTER)])
+def test_plan_is_the_same_on_one_and_on_many_host_threads(monkeypatch, kind, leaf, adm):
+    """Point sets of >= 32768 points build the trees on several host threads; the
+    permutation and every block must equal the one-thread build exactly (large random
+    sets with repeated coordinates exercise the tie-breaking by vertex id)."""
+    if kind == "cube":
+        xyz = W.cube_mesh(40)[0]
+    else:
+        rng = np.random.default_rng(8)
+        xyz = rng.uniform(0.0, 1.0, (50001, 3))
+        xyz[:, 0] = np.floor(xyz[:, 0] * 20) / 20
+        xyz[::5, 2] = 0.5
+    plans = []
+    for threads in ("1", "3", "16"):
+        monkeypatch.setenv("RT_PLAN_THREADS", threads)
+        plans.append(rt.rt_plan(xyz, leaf, 2.0, adm))
+    for perm, blocks, counts in plans[1:]:
+        np.testing.assert_array_equal(perm, plans[0][0])
+        np.testing.assert_array_equal(blocks, plans[0][1])
+        assert counts == plans[0][2]
+    perm, blocks, _ = plans[0]
+    assert sorted(perm.tolist()) == list(range(xyz.shape[0]))
+    # the blocks tile the matrix: their areas add up to N^2
+    assert int((blocks[:, 1].astype(np.int64) * blocks[:, 3]).sum()) == xyz.shape[0] ** 2
+
+
 def test_tree_order_keeps_leaves_spatially_compact():
     xyz, _ = W.cube_mesh(16)
     perm, blocks, _ = rt.rt_plan(xyz, 64, 2.0)
