@@ -314,6 +314,36 @@ def test_newton_matches_bisection_and_closed_forms():
     np.testing.assert_allclose(O.temperature_grey(Jg) ** 4 * (math.pi ** 4 / 15), Jg, rtol=1e-13)
 
 
+def test_temperature_balance_weights_each_channel_by_its_absorbed_share():
+    """Properties of the balance sum_nu w c (1 - a) (J_nu - B_nu(T)) = 0 (Section 1,
+    (RTb) with kappa_nu = c_nu kappa(x); kappa(x) cancels): a purely scattering channel
+    (a = 1) or one with c = 0 has no say in T; scaling every c, or every w, by one factor
+    leaves T unchanged; raising J of an absorbing channel raises T.  A swapped albedo
+    factor, a dropped c or w, or a wrong sign fails one of these."""
+    rng = np.random.default_rng(61)
+    nu = np.array([0.4, 0.9, 1.6])
+    fr = W.Freqs(nu, np.array([0.3, 0.5, 0.2]), np.array([0.7, 1.2, 2.0]), np.array([0.3, 1.0, 0.0]))
+    J = rng.uniform(0.05, 2.0, size=(3, 40))
+    T = O.temperature_newton(J, fr)
+    assert (T > 0).all()
+    J2 = J.copy()
+    J2[1] = rng.uniform(0.0, 50.0, 40)                     # the a = 1 channel
+    np.testing.assert_array_equal(O.temperature_newton(J2, fr), T)
+    for scale_c, scale_w in ((3.7, 1.0), (1.0, 0.25)):
+        f2 = W.Freqs(nu, fr.w * scale_w, fr.c * scale_c, fr.albedo)
+        np.testing.assert_allclose(O.temperature_newton(J, f2), T, rtol=1e-13)
+    f0 = W.Freqs(nu, fr.w, np.array([0.7, 1.2, 0.0]), fr.albedo)
+    fdrop = W.Freqs(nu[:2], fr.w[:2], fr.c[:2], fr.albedo[:2])
+    np.testing.assert_allclose(O.temperature_newton(J, f0), O.temperature_newton(J[:2], fdrop), rtol=1e-13)
+    J3 = J.copy()
+    J3[2] *= 1.5                                           # an absorbing channel
+    assert (O.temperature_newton(J3, fr) > T).all()
+    # the balance itself holds at the returned T (residual relative to the absorbed power)
+    wt = (fr.w * fr.c * (1 - fr.albedo))[:, None]
+    bal = (wt * (J - O.planck(nu[:, None], T[None, :]))).sum(axis=0)
+    assert np.abs(bal).max() <= 1e-12 * (wt * J).sum(axis=0).max()
+
+
 def test_planck_integrates_to_stefan_boltzmann():
     """int_0^inf nu^3/(e^{nu/T}-1) d nu = (pi^4/15) T^4 (the relation used by the grey model)."""
     nu = np.linspace(1e-6, 60, 400001)
