@@ -362,6 +362,36 @@ def test_grey_fixed_point_equals_direct_linear_solve():
     assert res["residual"] <= 1e-13
 
 
+def test_pure_scattering_fixed_point_is_the_direct_linear_solve():
+    """Albedo 1 (Section 1.3 with a_nu = 1): the balance gives T no weight, S = J, and
+    each channel's fixed point solves (I - (c_f/c_g) G_g) J_f = Sbar^E_f -- checked against
+    a direct dense solve, so a swapped albedo factor in the source update (S = B(T) = 0)
+    or in the balance fails."""
+    p = W.cube_problem(5, W.sinprod_kappa(0.5), W.midpoint_freqs(2, albedo=1.0), R0=0.5)
+    op = O.DenseOperator(p)
+    res = O.fixed_point(p, op, tol=1e-14, max_iter=2000)
+    assert (res["T"] == 0).all()
+    for f in range(p.freqs.F):
+        A = np.eye(p.N) - op.scale[f] * op.G[op.gidx[f]]
+        np.testing.assert_allclose(res["J"][f], np.linalg.solve(A, op.SE[f]), rtol=1e-11)
+
+
+def test_grey_fixed_point_does_not_depend_on_the_albedo():
+    """Grey model (Section 3): T = (J/sigma)^(1/4) makes sigma T^4 = J, so
+    S = a J + (1 - a) sigma T^4 = J for every albedo and the fixed point is the same
+    linear solve whatever a is."""
+    base = None
+    for a in (0.0, 0.4, 0.9):
+        p = W.cube_problem(5, W.Kappa(W.KAPPA_CONST, 1.0, 0.0), W.grey_freqs(albedo=a), R0=0.5, grey=True)
+        op = O.DenseOperator(p)
+        res = O.fixed_point(p, op, tol=1e-14, max_iter=2000)
+        if base is None:
+            base = res["J"][0]
+            np.testing.assert_allclose(base, np.linalg.solve(np.eye(p.N) - op.G[0], op.SE[0]), rtol=1e-11)
+        else:
+            np.testing.assert_allclose(res["J"][0], base, rtol=1e-11)
+
+
 def test_fixed_point_monotone_increasing_from_zero():
     """Proposition of Section 1.3: T^0 = 0, J^0 = 0 gives T^k increasing at every vertex."""
     p = W.cube_problem(5, W.sinprod_kappa(0.5), W.midpoint_freqs(3, albedo=0.3), R0=0.5)
