@@ -299,8 +299,9 @@ def batch_cpu_baseline(probs, iters, rows):
         est.append(p.N * t_row + float(iters[int(b)]) * 2.0 * p.freqs.F * p.N * p.N / rate)
     t_batch = statistics.mean(est) * len(probs)
     return {"value": len(probs) / t_batch, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{len(pick)} of {len(probs)} instances, {rows} dense FP64 rows each, extrapolated to "
-                      f"N rows + the GPU's iteration count of dense applies, scaled to all instances"}
+            "sample": f"{len(pick)} of {len(probs)} instances (N = {', '.join(str(probs[int(b)].N) for b in pick)}), "
+                      f"{rows} dense FP64 rows each, extrapolated to N rows + the GPU's iteration count of dense "
+                      f"applies, scaled to all instances"}
 
 
 def serve_stream(rt, reqs, hp, args, refine_tol):
@@ -404,6 +405,10 @@ def run_serve(args):
             res = O.one_step_residual(p, rows, J.astype(np.float64), T)
             errs[name].append(float(np.linalg.norm(res) / np.linalg.norm(J[:, rows])))
     oracle_s = time.perf_counter() - t0
+    # the oracle's rate on the same stream: sampled requests, each with the FP32 run's
+    # iteration count, extrapolated to every request
+    cpu = None if args.no_cpu_baseline else batch_cpu_baseline(
+        [p for _, p in reqs], [r[2]["iters"] for r in res_hi["f32"]], args.cpu_rows)
 
     h2d = sum(p.xyz.nbytes + p.tet.nbytes + p.emit_tri.nbytes for _, p in reqs)
     d2h = sum(p.freqs.F * p.N * 4 + p.N * 8 for _, p in reqs)
@@ -433,6 +438,7 @@ def run_serve(args):
         "e2e": {"value": head["served"], "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h),
                 "note": "the served rate is itself end to end: host inputs in, host results out"},
+        "cpu_baseline": cpu,
         "clocks": clk,
     }))
 
