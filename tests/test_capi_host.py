@@ -123,6 +123,26 @@ def test_plan_is_the_same_on_one_and_on_many_host_threads(monkeypatch, kind, lea
     assert int((blocks[:, 1].astype(np.int64) * blocks[:, 3]).sum()) == xyz.shape[0] ** 2
 
 
+@pytest.mark.parametrize("n,leaf", [(1, 64), (2, 1), (300, 16), (40000, 64)])
+def test_plan_of_coincident_points_is_all_dense(monkeypatch, n, leaf):
+    """Degenerate point sets: one point, and many copies of one point (zero radius and
+    zero distance: no pair is admissible, d > 0 fails).  Every block is a dense leaf
+    block, the blocks tile the matrix once, leaves hold at most `leaf` points, and the
+    large case plans the same on one and on many host threads."""
+    xyz = np.tile(np.array([[0.3, 0.2, 0.9]]), (n, 1))
+    monkeypatch.setenv("RT_PLAN_THREADS", "1")
+    perm, blocks, (nleaf, ndense, nfar) = rt.rt_plan(xyz, leaf, 2.0)
+    assert nfar == 0 and ndense == blocks.shape[0] == nleaf ** 2
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    assert (blocks[:, 4] == 0).all() and blocks[:, 1].max() <= leaf and blocks[:, 3].max() <= leaf
+    assert int((blocks[:, 1].astype(np.int64) * blocks[:, 3]).sum()) == n * n
+    if n >= 32768:
+        monkeypatch.setenv("RT_PLAN_THREADS", "16")
+        perm2, blocks2, _ = rt.rt_plan(xyz, leaf, 2.0)
+        np.testing.assert_array_equal(perm2, perm)
+        np.testing.assert_array_equal(blocks2, blocks)
+
+
 def test_tree_order_keeps_leaves_spatially_compact():
     xyz, _ = W.cube_mesh(16)
     perm, blocks, _ = rt.rt_plan(xyz, 64, 2.0)
